@@ -1,0 +1,156 @@
+/*
+ * libhfx -- Gamma-point Hartree-Fock exact exchange (E_x and V_x phi) on one GB300 GPU.
+ *
+ * What one call computes (paper Sec. 2.1, Eqs. "vx", "vij" and "HFX"), for real occupied
+ * orbitals phi_i sampled on an n1 x n2 x n3 grid of a periodic cell (volume Omega, N points):
+ *
+ *   rho_ij(r)   = phi_i(r) phi_j(r)                                   (pair density)
+ *   F_ij(G)     = sum_r rho_ij(r) exp(-i G.r)                          (forward 3D FFT)
+ *   v(G)        = 4 pi / |G|^2, v(0) = 0                               (Coulomb kernel)
+ *   v_ij(r)     = (1/N) sum_G v(G) F_ij(G) exp(i G.r)                  (Eq. vij, Poisson solve)
+ *   E_x         = -(alpha/2) (Omega/N^2) sum_{(i,j) ordered} sum_G v(G) |F_ij(G)|^2   (Eq. HFX)
+ *   (V_x phi)_i = -alpha sum_j v_ij(r) phi_j(r)                          (Eq. vx)
+ *
+ * over a list of unordered pairs i <= j: an off-diagonal entry stands for (i,j) and (j,i)
+ * (energy weight 2, and it adds to both V_i and V_j because v_ij = v_ji), a diagonal entry
+ * for itself (weight 1).  The cost is N_orb^2 N log N per call (Sec. 1), which is why
+ * the paper's multiple-time-step scheme evaluates it only on its slow (outer) steps.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Grid data is row-major [n_orb][n1][n2][n3], the last index (n3) contiguous; point
+ *   (p1,p2,p3) sits at r = a1 p1/n1 + a2 p2/n2 + a3 p3/n3 for lattice rows a_k.
+ * - Device pointers must be 16-byte aligned.  The library never frees caller memory.
+ * - Every call that takes a cuda_stream (a cudaStream_t passed as void*, NULL = legacy
+ *   default stream) only enqueues work on it: no host synchronisation, no allocation
+ *   (except the first hfx_apply for a new n_orb, which uploads a small schedule table
+ *   and must therefore come before any stream capture).
+ * - Errors are returned before anything is enqueued when they can be seen on the host;
+ *   the library never aborts.  hfx_last_error() gives the calling thread's last message.
+ */
+#ifndef HFX_H_
+#define HFX_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hfx_ctx hfx_ctx;
+
+typedef enum {
+  HFX_OK = 0,
+  HFX_ERR_INVALID_ARG = -1,      /* null pointer, bad size, misaligned pointer, bad flag   */
+  HFX_ERR_UNSUPPORTED_GRID = -2, /* an edge is not {2,3,5}-smooth, or a plane exceeds the
+                                    on-chip capacity of the chosen precision              */
+  HFX_ERR_OOM = -3,              /* a table allocation failed, or the workspace is short  */
+  HFX_ERR_CUDA = -4,             /* a CUDA runtime call or a kernel launch failed         */
+  HFX_ERR_BAD_PAIR_LIST = -5,    /* (device-detected) an entry outside 0 <= i <= j < n_orb
+                                    or more copies of a pair than fit; those entries were
+                                    skipped                                               */
+  HFX_ERR_TIMEOUT = -6           /* (device-detected) a bounded device-side wait gave up  */
+} hfx_status;
+
+typedef enum {
+  HFX_KERNEL_COULOMB = 0,        /* v = 4 pi/|G|^2 on the whole grid, v(0) = 0 (default)   */
+  HFX_KERNEL_COULOMB_SPHERE = 1  /* also v = 0 where |G|^2/2 >= 4 ecut (pair-density sphere) */
+} hfx_kernel;
+
+typedef enum {
+  HFX_PREC_FP64 = 0,  /* all arithmetic in FP64                                          */
+  HFX_PREC_FP32 = 1   /* pair products and FFTs in FP32; energy sums and the V_x phi
+                         accumulation in FP64                                              */
+} hfx_precision;
+
+/* flags for hfx_apply */
+#define HFX_ENERGY_ONLY   0x1u  /* compute E_x only; vxphi is not touched (may be NULL)    */
+#define HFX_ACCUMULATE    0x2u  /* add to *ex_dev and vxphi instead of overwriting them      */
+#define HFX_ORBITALS_F32  0x4u  /* orbitals are FP32 (HFX_PREC_FP32 only); default FP64     */
+
+typedef struct {
+  double lattice[3][3]; /* rows are the cell vectors a1, a2, a3 in bohr; cubic = diag(L,L,L) */
+} hfx_box;
+
+/* hfx_create -- build a context for one cell and grid (Sec. 2.1; the grid holds the
+ * Gamma-point orbitals whose pair potentials are solved by FFT, Sec. 2.2).
+ *   box    : cell vectors (bohr); must have a non-zero volume.
+ *   grid   : n1, n2, n3; each {2,3,5}-smooth, 2 <= n <= 256; a plane of n2*n3 (and n1*n3)
+ *            complex values must fit in shared memory (FP32: n2*n3 <= 24576; FP64: <= 12288).
+ *   ecut   : wavefunction cutoff in Ha, used only by HFX_KERNEL_COULOMB_SPHERE (> 0 then).
+ *   kernel : hfx_kernel.
+ *   alpha  : fraction of exact exchange (0.25 for PBE0).
+ *   prec   : hfx_precision.
+ *   out    : receives the new context (owned by the caller; free with hfx_destroy).
+ * Allocates the context's small device tables (twiddles, the Coulomb table v(G) of N values)
+ * on the current device.  Returns HFX_ERR_INVALID_ARG, HFX_ERR_UNSUPPORTED_GRID, HFX_ERR_OOM
+ * or HFX_ERR_CUDA on failure (and *out = NULL). */
+hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hfx_kernel kernel,
+                      double alpha, hfx_precision prec, hfx_ctx** out);
+
+/* hfx_workspace_bytes -- device scratch that hfx_apply needs for n_orb orbitals and a list
+ * of n_pairs pairs (pair staging, the per-batch transforms and the per-couple energy sums;
+ * plus an FP32 copy of the orbitals on the FP32 path).  Returns 0 on bad arguments. */
+size_t hfx_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs);
+
+/* hfx_set_workspace -- hand the context a caller-owned device buffer (e.g. a torch tensor)
+ * of `bytes` bytes, 256-byte aligned.  The context keeps the pointer until it is replaced
+ * or the context is destroyed; it never frees it.  Calls that use the same context must
+ * not overlap on the GPU. */
+hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes);
+
+/* hfx_apply -- one exact-exchange evaluation (Eqs. vx, vij, HFX).
+ *   orbitals : device, [n_orb][n1][n2][n3], FP64 (FP32 with HFX_ORBITALS_F32); read only.
+ *   n_orb    : number of occupied orbitals (> 0).
+ *   pairs    : device int32 [n_pairs][2], entries 0 <= i <= j < n_orb, any order (Sec. 2.1
+ *              screening: any subset of pairs may be listed).  Invalid entries are skipped
+ *              and reported by hfx_sync_status as HFX_ERR_BAD_PAIR_LIST.
+ *   n_pairs  : >= 0; 0 gives E_x = 0 and V_x phi = 0 (or leaves them with HFX_ACCUMULATE).
+ *   flags    : HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32.
+ *   ex_dev   : device FP64 scalar receiving E_x (Hartree).
+ *   vxphi    : device FP64 [n_orb][n1][n2][n3] receiving V_x phi; NULL only with
+ *              HFX_ENERGY_ONLY.
+ *   cuda_stream : stream to enqueue on.
+ * Needs a workspace of at least hfx_workspace_bytes(c, n_orb, n_pairs).  Asynchronous:
+ * results are valid once the stream reaches them.  Deterministic: the same inputs give
+ * bit-identical results. */
+hfx_status hfx_apply(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
+                     int64_t n_pairs, uint32_t flags, double* ex_dev, double* vxphi,
+                     void* cuda_stream);
+
+/* One problem of a batched call: the arguments of hfx_apply for one context. */
+typedef struct {
+  const void* orbitals;
+  int32_t n_orb;
+  const int32_t* pairs;
+  int64_t n_pairs;
+  uint32_t flags;
+  double* ex_dev;
+  double* vxphi;
+} hfx_apply_args;
+
+/* hfx_apply_batched -- several independent problems (each with its own context, so its own
+ * cell, grid and workspace) enqueued together on one stream: the uneven batch of
+ * independent configurations (the CP-group idea of Sec. 2.2 applied to whole problems).
+ * Same argument rules, per problem, as hfx_apply; stops at the first problem whose
+ * arguments are rejected and returns that error. */
+hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
+                             void* cuda_stream);
+
+/* hfx_sync_status -- wait for `cuda_stream` and return (then clear) the device-side error
+ * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST or HFX_ERR_TIMEOUT. */
+hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
+
+/* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
+ * thread's next libhfx call. */
+const char* hfx_last_error(void);
+
+/* hfx_destroy -- free the context and its tables (not the workspace).  NULL is a no-op. */
+void hfx_destroy(hfx_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFX_H_ */

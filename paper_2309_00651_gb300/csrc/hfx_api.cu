@@ -1,0 +1,744 @@
+// libhfx host side: contexts, tables, the pair-block schedule, workspace layout, the
+// device-side pair-list staging kernels and the per-call launch sequence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hfx.h"
+#include "hfx_internal.h"
+
+using namespace hfx;
+
+// ------------------------------------------------------------------------------------
+// error reporting
+// ------------------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static hfx_status fail(hfx_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define HFX_CUDA_TRY(expr)                                                                     \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(HFX_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                   \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// FFT plans: each edge is split into in-register radices from {16,12,10,9,8,6,5,4,3,2},
+// fewest stages first, then the lowest estimated flop count.
+// ------------------------------------------------------------------------------------
+static const int kRadices[] = {16, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+
+static double radix_cost(int r) {
+  switch (r) {
+    case 2: return 2.0; case 3: return 4.0; case 4: return 4.0; case 5: return 6.8;
+    case 6: return 5.3; case 8: return 5.5; case 9: return 7.6; case 10: return 7.2;
+    case 12: return 7.3; case 16: return 7.5; default: return 99.0;
+  }
+}
+
+static bool factorize(int n, std::vector<int>& best) {
+  if (n == 1) { best.clear(); return true; }
+  bool found = false;
+  double best_cost = 1e30;
+  for (int r : kRadices) {
+    if (n % r) continue;
+    std::vector<int> rest;
+    if (!factorize(n / r, rest)) continue;
+    rest.insert(rest.begin(), r);
+    double cost = 0.0;
+    for (int f : rest) cost += radix_cost(f) + 6.0 * (f - 1) / f;
+    cost += 1000.0 * rest.size();  // fewest stages first (each is a shared-memory round trip)
+    if (!found || cost < best_cost) { best = rest; best_cost = cost; found = true; }
+  }
+  return found;
+}
+
+static bool make_dim_plan(int n, DimPlan& d) {
+  std::vector<int> f;
+  if (n < 2 || n > 256 || !factorize(n, f) || (int)f.size() > kMaxStages) return false;
+  d.n = n;
+  d.ns = (int)f.size();
+  int m = n;
+  for (int s = 0; s < d.ns; ++s) {
+    d.r[s] = f[s];
+    m /= f[s];
+    d.m[s] = m;
+  }
+  for (int s = d.ns; s < kMaxStages; ++s) { d.r[s] = 1; d.m[s] = 1; }
+  return true;
+}
+
+// frequency index stored at position `pos` after the forward (DIF) stages of plan d
+static int freq_of_pos(const DimPlan& d, int pos) {
+  int freq = 0, mult = 1, n = d.n;
+  for (int s = 0; s < d.ns; ++s) {
+    const int m = n / d.r[s];
+    const int k2 = pos / m;
+    pos %= m;
+    freq += mult * k2;
+    mult *= d.r[s];
+    n = m;
+  }
+  return freq;
+}
+
+// ------------------------------------------------------------------------------------
+// pair-block schedule for n_orb orbitals in blocks of `b`: block pairs (I <= J) are arranged
+// in rounds in which no two block pairs share a block (circle method), so every V_x phi tile
+// of a round has one writer; rounds are cut into batches by the transform budget.
+// ------------------------------------------------------------------------------------
+struct Schedule {
+  int n_orb = 0, b = 0, nb = 0, nslots = 0, nbatches = 0;
+  std::vector<int2> slot_blocks;        // slot -> (I, J)
+  std::vector<int> slot_of_bp;          // I*nb + J (I <= J) -> slot
+  std::vector<int> slot_cap;            // couples a slot can hold
+  std::vector<int> batch_slot_begin;    // [nbatches + 1]
+  long long max_batch_couples = 0, max_total_couples = 0;
+  // device copies
+  int2* d_slot_blocks = nullptr;
+  int* d_slot_of_bp = nullptr;
+  int* d_batch_slot_begin = nullptr;
+};
+
+static int block_size_of(int bi, int b, int n_orb) { return std::min(b, n_orb - bi * b); }
+
+static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budget, size_t bytes_per_couple) {
+  S.n_orb = n_orb;
+  S.b = b;
+  S.nb = (n_orb + b - 1) / b;
+  const int nb = S.nb;
+  std::vector<std::vector<int2>> rounds;
+  if (nb == 1) {
+    rounds.push_back({make_int2(0, 0)});
+  } else {
+    const int M = (nb % 2 == 0) ? nb : nb + 1;  // with a dummy block when odd
+    const int fixed = M - 1;
+    for (int r = 0; r < M - 1; ++r) {
+      std::vector<int2> rd;
+      auto add = [&](int a, int c) {
+        if (a >= nb && c >= nb) return;
+        if (a >= nb) { rd.push_back(make_int2(c, c)); return; }   // partner is the dummy: diagonal
+        if (c >= nb) { rd.push_back(make_int2(a, a)); return; }
+        rd.push_back(make_int2(std::min(a, c), std::max(a, c)));
+      };
+      add(r, fixed);
+      for (int k = 1; k < M / 2; ++k) add((r + k) % (M - 1), (r - k + (M - 1)) % (M - 1));
+      rounds.push_back(rd);
+    }
+    if (nb % 2 == 0) {
+      std::vector<int2> rd;
+      for (int i = 0; i < nb; ++i) rd.push_back(make_int2(i, i));
+      rounds.push_back(rd);
+    }
+  }
+  S.slot_blocks.clear();
+  S.slot_cap.clear();
+  S.batch_slot_begin.clear();
+  S.slot_of_bp.assign((size_t)nb * nb, -1);
+  S.max_batch_couples = 0;
+  S.max_total_couples = 0;
+  const long long budget_couples = std::max<long long>(1, (long long)(transform_budget / bytes_per_couple));
+  for (auto& rd : rounds) {
+    long long in_batch = 0;
+    bool open = false;
+    for (auto bp : rd) {
+      const int si = block_size_of(bp.x, b, n_orb), sj = block_size_of(bp.y, b, n_orb);
+      int cap;
+      if (bp.x != bp.y) cap = (si * sj + 1) / 2;
+      else cap = (si * (si - 1) / 2 + 1) / 2 + (si + 1) / 2;
+      if (!open || in_batch + cap > budget_couples) {
+        if (open) S.max_batch_couples = std::max(S.max_batch_couples, in_batch);
+        S.batch_slot_begin.push_back((int)S.slot_blocks.size());
+        in_batch = 0;
+        open = true;
+      }
+      S.slot_of_bp[(size_t)bp.x * nb + bp.y] = (int)S.slot_blocks.size();
+      S.slot_blocks.push_back(bp);
+      S.slot_cap.push_back(cap);
+      in_batch += cap;
+      S.max_total_couples += cap;
+    }
+    if (open) S.max_batch_couples = std::max(S.max_batch_couples, in_batch);
+  }
+  S.nslots = (int)S.slot_blocks.size();
+  S.nbatches = (int)S.batch_slot_begin.size();
+  S.batch_slot_begin.push_back(S.nslots);
+}
+
+// ------------------------------------------------------------------------------------
+// context
+// ------------------------------------------------------------------------------------
+struct hfx_ctx {
+  int grid[3];
+  long long N;
+  double lat[3][3];
+  double omega;
+  double ecut;
+  int kernel;
+  double alpha;
+  int prec;
+  int device;
+  int sm_count;
+  int max_smem;
+  Geo geo;
+  void* d_tw[3] = {nullptr, nullptr, nullptr};
+  void* d_vtab = nullptr;
+  int* d_err = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int bsize = 8;
+  size_t transform_budget = size_t(1) << 30;
+  int blocks_fwd = 1, blocks_x = 1;
+  std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
+};
+
+static size_t real_size(const hfx_ctx* c) { return c->prec == HFX_PREC_FP64 ? 8 : 4; }
+static size_t cplx_size(const hfx_ctx* c) { return 2 * real_size(c); }
+static int zchunk(const hfx_ctx* c) { return c->prec == HFX_PREC_FP64 ? 4 : 8; }
+
+static size_t smem_fwd(const hfx_ctx* c) {
+  return (size_t)(c->grid[1] * c->grid[2] + c->grid[1] + c->grid[2]) * cplx_size(c);
+}
+static size_t smem_x(const hfx_ctx* c) {
+  return (size_t)(c->grid[0] * c->grid[2] + c->grid[0] + c->grid[2]) * cplx_size(c);
+}
+static size_t smem_acc(const hfx_ctx* c) {
+  const int zc = zchunk(c);
+  return (size_t)(c->grid[1] * zc + c->grid[1]) * cplx_size(c) + (size_t)(2 * c->bsize) * c->grid[1] * zc * real_size(c);
+}
+
+static void free_ctx_tables(hfx_ctx* c) {
+  for (auto& p : c->d_tw) { if (p) cudaFree(p); p = nullptr; }
+  if (c->d_vtab) cudaFree(c->d_vtab);
+  if (c->d_err) cudaFree(c->d_err);
+  c->d_vtab = nullptr;
+  c->d_err = nullptr;
+  for (auto& kv : c->sched) {
+    Schedule& S = *kv.second;
+    if (S.d_slot_blocks) cudaFree(S.d_slot_blocks);
+    if (S.d_slot_of_bp) cudaFree(S.d_slot_of_bp);
+    if (S.d_batch_slot_begin) cudaFree(S.d_batch_slot_begin);
+  }
+  c->sched.clear();
+}
+
+template <typename T>
+static std::vector<T> to_real_vec(const std::vector<double>& v) {
+  std::vector<T> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+  return o;
+}
+
+static hfx_status upload(void** dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return fail(HFX_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+  e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+  return HFX_OK;
+}
+
+static hfx_status build_tables(hfx_ctx* c) {
+  // twiddles w_n^t = exp(-2 pi i t / n), t < n, from the rational angle t/n
+  for (int d = 0; d < 3; ++d) {
+    const int n = c->grid[d];
+    std::vector<double> tw(2 * n);
+    for (int t = 0; t < n; ++t) {
+      const cs_pair w = cossin_2pi_frac(t, n);
+      tw[2 * t] = w.c;
+      tw[2 * t + 1] = -w.s;
+    }
+    hfx_status st;
+    if (c->prec == HFX_PREC_FP64) st = upload(&c->d_tw[d], tw.data(), tw.size() * sizeof(double));
+    else { auto f = to_real_vec<float>(tw); st = upload(&c->d_tw[d], f.data(), f.size() * sizeof(float)); }
+    if (st != HFX_OK) return st;
+  }
+  // Coulomb table in storage order: v[x_pos][y_pos][z_pos] = 4 pi / |G|^2 (0 at G = 0)
+  double B[3][3];  // reciprocal rows b_k with a_i . b_k = 2 pi delta_ik
+  {
+    const double (*A)[3] = c->lat;
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                       A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    // inverse transpose: b_k = 2 pi (a_{k+1} x a_{k+2}) / det
+    for (int k = 0; k < 3; ++k) {
+      const double* p = A[(k + 1) % 3];
+      const double* q = A[(k + 2) % 3];
+      B[k][0] = 2.0 * kPi * (p[1] * q[2] - p[2] * q[1]) / det;
+      B[k][1] = 2.0 * kPi * (p[2] * q[0] - p[0] * q[2]) / det;
+      B[k][2] = 2.0 * kPi * (p[0] * q[1] - p[1] * q[0]) / det;
+    }
+  }
+  const int n1 = c->grid[0], n2 = c->grid[1], n3 = c->grid[2];
+  std::vector<int> mf[3];
+  for (int d = 0; d < 3; ++d) {
+    const int n = c->grid[d];
+    mf[d].resize(n);
+    for (int pos = 0; pos < n; ++pos) {
+      const int f = freq_of_pos(c->geo.d[d], pos);
+      mf[d][pos] = (f <= n / 2) ? f : f - n;
+    }
+  }
+  std::vector<double> v((size_t)c->N);
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b)
+      for (int e = 0; e < n3; ++e) {
+        double G[3];
+        for (int k = 0; k < 3; ++k) G[k] = mf[0][a] * B[0][k] + mf[1][b] * B[1][k] + mf[2][e] * B[2][k];
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        double val = (g2 > 0.0) ? 4.0 * kPi / g2 : 0.0;
+        if (c->kernel == HFX_KERNEL_COULOMB_SPHERE && 0.5 * g2 >= 4.0 * c->ecut) val = 0.0;
+        v[((size_t)a * n2 + b) * n3 + e] = val;
+      }
+  hfx_status st;
+  if (c->prec == HFX_PREC_FP64) st = upload(&c->d_vtab, v.data(), v.size() * sizeof(double));
+  else { auto f = to_real_vec<float>(v); st = upload(&c->d_vtab, f.data(), f.size() * sizeof(float)); }
+  if (st != HFX_OK) return st;
+  HFX_CUDA_TRY(cudaMalloc(&c->d_err, sizeof(int)));
+  HFX_CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hfx_kernel kernel,
+                                 double alpha, hfx_precision prec, hfx_ctx** out) {
+  g_last_error.clear();
+  if (!out) return fail(HFX_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!box || !grid) return fail(HFX_ERR_INVALID_ARG, "box or grid is NULL");
+  if (kernel != HFX_KERNEL_COULOMB && kernel != HFX_KERNEL_COULOMB_SPHERE)
+    return fail(HFX_ERR_INVALID_ARG, "unknown kernel %d", (int)kernel);
+  if (prec != HFX_PREC_FP64 && prec != HFX_PREC_FP32) return fail(HFX_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  if (kernel == HFX_KERNEL_COULOMB_SPHERE && !(ecut > 0.0)) return fail(HFX_ERR_INVALID_ARG, "ecut must be > 0");
+  if (!std::isfinite(alpha)) return fail(HFX_ERR_INVALID_ARG, "alpha is not finite");
+  std::unique_ptr<hfx_ctx> c(new hfx_ctx());
+  for (int d = 0; d < 3; ++d) {
+    c->grid[d] = grid[d];
+    if (grid[d] % 2 != 0 || !make_dim_plan(grid[d], c->geo.d[d]))
+      return fail(HFX_ERR_UNSUPPORTED_GRID, "grid edge %d = %d: need an even {2,3,5}-smooth size in [2, 256]", d,
+                  (int)grid[d]);
+  }
+  c->N = (long long)grid[0] * grid[1] * grid[2];
+  c->geo.n1 = grid[0]; c->geo.n2 = grid[1]; c->geo.n3 = grid[2]; c->geo.N = c->N;
+  std::memcpy(c->lat, box->lattice, sizeof(c->lat));
+  const double (*A)[3] = c->lat;
+  const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return fail(HFX_ERR_INVALID_ARG, "cell volume is zero");
+  c->omega = std::fabs(det);
+  c->ecut = ecut;
+  c->kernel = kernel;
+  c->alpha = alpha;
+  c->prec = prec;
+  if (const char* s = std::getenv("HFX_BLOCK")) c->bsize = std::max(1, std::min(32, atoi(s)));
+  if (const char* s = std::getenv("HFX_BATCH_MB")) c->transform_budget = (size_t)std::max(1, atoi(s)) << 20;
+
+  HFX_CUDA_TRY(cudaGetDevice(&c->device));
+  HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
+  HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  const size_t need = std::max(std::max(smem_fwd(c.get()), smem_x(c.get())), smem_acc(c.get())) + 512;
+  if (need > (size_t)c->max_smem)
+    return fail(HFX_ERR_UNSUPPORTED_GRID, "a grid plane needs %zu bytes of shared memory (limit %d) at this precision",
+                need, c->max_smem);
+  cudaError_t e = (prec == HFX_PREC_FP64) ? Passes<double>::set_smem_limit(c->max_smem - 512)
+                                          : Passes<float>::set_smem_limit(c->max_smem - 512);
+  if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+  e = (prec == HFX_PREC_FP64) ? Passes<double>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x)
+                              : Passes<float>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x);
+  if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+  c->blocks_fwd = std::max(1, c->blocks_fwd);
+  c->blocks_x = std::max(1, c->blocks_x);
+  hfx_status st = build_tables(c.get());
+  if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
+  *out = c.release();
+  return HFX_OK;
+}
+
+extern "C" void hfx_destroy(hfx_ctx* c) {
+  if (!c) return;
+  free_ctx_tables(c);
+  delete c;
+}
+
+extern "C" const char* hfx_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (bytes && !dev_ptr) return fail(HFX_ERR_INVALID_ARG, "workspace pointer is NULL");
+  if (((uintptr_t)dev_ptr) % 256) return fail(HFX_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  c->ws = dev_ptr;
+  c->ws_bytes = bytes;
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// workspace layout
+// ------------------------------------------------------------------------------------
+struct Layout {
+  size_t orb32, W, epart, couples, keys, counts, couple_base, cursor, batch_begin, slot_begin, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static Schedule make_host_schedule(const hfx_ctx* c, int n_orb) {
+  Schedule S;
+  build_schedule(S, n_orb, c->bsize, c->transform_budget, (size_t)c->N * cplx_size(c));
+  return S;
+}
+
+static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long long n_pairs) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  const size_t orb32_bytes = (c->prec == HFX_PREC_FP32) ? (size_t)n_orb * c->N * 4 : 0;
+  L.orb32 = take(orb32_bytes);
+  L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
+  L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
+  L.couples = take((size_t)S.max_total_couples * sizeof(int4));
+  L.keys = take((size_t)std::max<long long>(n_pairs, 1) * sizeof(int));
+  const size_t nkeys = 2 * (size_t)S.nslots;
+  L.counts = take(nkeys * sizeof(int));
+  L.couple_base = take((nkeys + 1) * sizeof(int));
+  L.cursor = take(nkeys * sizeof(int));
+  L.batch_begin = take(((size_t)S.nbatches + 1) * sizeof(int));
+  L.slot_begin = take(((size_t)S.nslots + 1) * sizeof(int));
+  L.total = off;
+  return L;
+}
+
+extern "C" size_t hfx_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs) {
+  if (!c || n_orb <= 0 || n_pairs < 0) return 0;
+  Schedule S = make_host_schedule(c, n_orb);
+  return layout_of(c, S, n_orb, n_pairs).total;
+}
+
+static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
+  auto it = c->sched.find(n_orb);
+  if (it != c->sched.end()) { *out = it->second.get(); return HFX_OK; }
+  std::unique_ptr<Schedule> S(new Schedule(make_host_schedule(c, n_orb)));
+  hfx_status st = upload((void**)&S->d_slot_blocks, S->slot_blocks.data(), S->slot_blocks.size() * sizeof(int2));
+  if (st == HFX_OK) st = upload((void**)&S->d_slot_of_bp, S->slot_of_bp.data(), S->slot_of_bp.size() * sizeof(int));
+  if (st == HFX_OK)
+    st = upload((void**)&S->d_batch_slot_begin, S->batch_slot_begin.data(), S->batch_slot_begin.size() * sizeof(int));
+  if (st != HFX_OK) {
+    if (S->d_slot_blocks) cudaFree(S->d_slot_blocks);
+    if (S->d_slot_of_bp) cudaFree(S->d_slot_of_bp);
+    if (S->d_batch_slot_begin) cudaFree(S->d_batch_slot_begin);
+    return st;
+  }
+  *out = S.get();
+  c->sched[n_orb] = std::move(S);
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// pair-list staging kernels (validate, bucket by block pair and weight class, stable order)
+// ------------------------------------------------------------------------------------
+__global__ void k_cast_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  const long long n2 = n / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = reinterpret_cast<const double2*>(src)[i];
+    reinterpret_cast<float2*>(dst)[i] = make_float2((float)v.x, (float)v.y);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) dst[n - 1] = (float)src[n - 1];
+}
+
+__global__ void k_plan_count(const int2* __restrict__ pairs, long long P, int n_orb, int bsize, int nb,
+                             const int* __restrict__ slot_of_bp, int* __restrict__ keys, int* __restrict__ counts,
+                             int* __restrict__ err) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const int2 ij = pairs[p];
+    int key = -1;
+    if (ij.x >= 0 && ij.y < n_orb && ij.x <= ij.y) {
+      const int s = slot_of_bp[(ij.x / bsize) * nb + (ij.y / bsize)];
+      key = 2 * s + (ij.x == ij.y ? 1 : 0);
+      atomicAdd(&counts[key], 1);
+    } else {
+      atomicOr(err, kErrBadPair);
+    }
+    keys[p] = key;
+  }
+}
+
+// one block: clamp counts to capacity, couples per key (ceil(count/2)), exclusive scan,
+// couple ranges per slot and per batch
+__global__ void __launch_bounds__(1024) k_plan_scan(int nslots, const int2* __restrict__ slot_blocks, int bsize, int n_orb,
+                                                    int* __restrict__ counts, int* __restrict__ couple_base, int nbatches,
+                                                    const int* __restrict__ batch_slot_begin, int* __restrict__ batch_begin,
+                                                    int* __restrict__ slot_begin, int* __restrict__ err) {
+  __shared__ int wsum[32];
+  const int nkeys = 2 * nslots;
+  const int per = (nkeys + blockDim.x - 1) / blockDim.x;
+  const int k0 = min(nkeys, (int)threadIdx.x * per), k1 = min(nkeys, k0 + per);
+  int local = 0;
+  for (int k = k0; k < k1; ++k) {
+    const int2 bp = slot_blocks[k >> 1];
+    const int si = min(bsize, n_orb - bp.x * bsize), sj = min(bsize, n_orb - bp.y * bsize);
+    int cap;
+    if (bp.x != bp.y) cap = (k & 1) ? 0 : si * sj;
+    else cap = (k & 1) ? si : si * (si - 1) / 2;
+    int cnt = counts[k];
+    if (cnt > cap) { cnt = cap; atomicOr(err, kErrBadPair); }
+    counts[k] = cnt;
+    local += (cnt + 1) >> 1;
+  }
+  // block exclusive scan of `local`
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    int s = (lane < nw) ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += t;
+    }
+    if (lane < nw) wsum[lane] = s;  // inclusive warp totals
+  }
+  __syncthreads();
+  int run = incl - local + (w > 0 ? wsum[w - 1] : 0);
+  for (int k = k0; k < k1; ++k) {
+    couple_base[k] = run;
+    run += (counts[k] + 1) >> 1;
+  }
+  if (threadIdx.x == blockDim.x - 1) couple_base[nkeys] = run;
+  __syncthreads();
+  for (int s = threadIdx.x; s <= nslots; s += blockDim.x) slot_begin[s] = couple_base[2 * s];
+  for (int b = threadIdx.x; b <= nbatches; b += blockDim.x) batch_begin[b] = couple_base[2 * batch_slot_begin[b]];
+}
+
+// one warp: stable placement of every valid pair into its bucket; pair number t of a bucket
+// becomes half (t & 1) of couple couple_base[key] + t/2.
+__global__ void __launch_bounds__(32) k_plan_scatter(const int2* __restrict__ pairs, long long P,
+                                                     const int* __restrict__ keys, const int* __restrict__ counts,
+                                                     const int* __restrict__ couple_base, int nkeys, int use_smem,
+                                                     int* __restrict__ gcursor, int4* __restrict__ couples) {
+  extern __shared__ int scur[];
+  int* cur = use_smem ? scur : gcursor;
+  const int lane = threadIdx.x;
+  for (int k = lane; k < nkeys; k += 32) cur[k] = 0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  for (long long base = 0; base < P; base += 32) {
+    const long long p = base + lane;
+    const int key = (p < P) ? keys[p] : -1;
+    const unsigned same = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(same & lt);
+    const int leader = __ffs(same) - 1;
+    int c = 0;
+    if (key >= 0) c = cur[key];
+    __syncwarp();
+    if (key >= 0 && lane == leader) cur[key] = c + __popc(same);
+    __syncwarp();
+    if (key >= 0) {
+      const int pos = c + rank;
+      if (pos < counts[key]) {
+        const int2 ij = pairs[p];
+        int* cp = reinterpret_cast<int*>(couples + couple_base[key] + (pos >> 1));
+        cp[(pos & 1) * 2] = ij.x;
+        cp[(pos & 1) * 2 + 1] = ij.y;
+      }
+    }
+  }
+}
+
+// one block: E_x = scale * sum_g w_g sum_y epart[g][y] (fixed order), stored or accumulated
+__global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__ epart, const int4* __restrict__ couples,
+                                                      const int* __restrict__ total_couples, int n2, double scale,
+                                                      int accumulate, double* __restrict__ ex) {
+  __shared__ double red[32];
+  const int total = *total_couples;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+    const int4 cp = couples[g];
+    double t = 0.0;
+    for (int y = 0; y < n2; ++y) t += epart[(long long)g * n2 + y];
+    s += (cp.x == cp.y ? 1.0 : 2.0) * t;
+  }
+  const double tot = block_sum<double>(s, red);
+  if (threadIdx.x == 0) ex[0] = (accumulate ? ex[0] : 0.0) + scale * tot;
+}
+
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+// ------------------------------------------------------------------------------------
+// apply
+// ------------------------------------------------------------------------------------
+template <typename T>
+static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* orb, int n_orb, uint32_t flags,
+                             double* vxphi, cudaStream_t st) {
+  char* ws = (char*)c->ws;
+  using C = cx<T>;
+  C* W = (C*)(ws + L.W);
+  int4* couples = (int4*)(ws + L.couples);
+  int* batch_begin = (int*)(ws + L.batch_begin);
+  int* slot_begin = (int*)(ws + L.slot_begin);
+  double* epart = (double*)(ws + L.epart);
+  const Geo& g = c->geo;
+  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
+  const double vscale = -c->alpha / (double)c->N;
+  const int zc = zchunk(c);
+  const int nzc = (g.n3 + zc - 1) / zc;
+  for (int b = 0; b < S.nbatches; ++b) {
+    const int s0 = S.batch_slot_begin[b], s1 = S.batch_slot_begin[b + 1];
+    long long cap = 0;
+    for (int s = s0; s < s1; ++s) cap += S.slot_cap[s];
+    const long long items1 = cap * g.n1, items2 = cap * g.n2;
+    const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
+    const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
+    Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, batch_begin, b, W, (const C*)c->d_tw[1],
+                      (const C*)c->d_tw[2]);
+    Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, batch_begin, b, W, (const T*)c->d_vtab,
+                         (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
+    if (!energy_only) {
+      dim3 grid3(nzc, g.n1, s1 - s0);
+      Passes<T>::y_inv_acc(g, grid3, smem_acc(c), st, orb, couples, batch_begin, b, slot_begin, S.d_slot_blocks, s0,
+                           S.b, n_orb, W, (const C*)c->d_tw[1], vxphi, vscale);
+    }
+  }
+  return HFX_OK;
+}
+
+static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
+                             uint32_t flags, double* ex_dev, double* vxphi, cudaStream_t st) {
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32)) return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
+  if (n_orb <= 0) return fail(HFX_ERR_INVALID_ARG, "n_orb must be > 0");
+  if (n_pairs < 0 || n_pairs > (int64_t)1 << 31) return fail(HFX_ERR_INVALID_ARG, "n_pairs out of range");
+  if (!orbitals || !ex_dev) return fail(HFX_ERR_INVALID_ARG, "orbitals or ex_dev is NULL");
+  if (n_pairs > 0 && !pairs) return fail(HFX_ERR_INVALID_ARG, "pairs is NULL");
+  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
+  if (!energy_only && !vxphi) return fail(HFX_ERR_INVALID_ARG, "vxphi is NULL without HFX_ENERGY_ONLY");
+  if ((flags & HFX_ORBITALS_F32) && c->prec != HFX_PREC_FP32)
+    return fail(HFX_ERR_INVALID_ARG, "HFX_ORBITALS_F32 needs HFX_PREC_FP32");
+  if (((uintptr_t)orbitals | (uintptr_t)pairs | (uintptr_t)vxphi) % 16 || ((uintptr_t)ex_dev % 8))
+    return fail(HFX_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
+  const size_t vbytes = (size_t)n_orb * c->N * sizeof(double);
+  if (n_pairs == 0) {
+    if (!accumulate) {
+      k_set_scalar<<<1, 1, 0, st>>>(ex_dev, 0.0);
+      if (!energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
+    }
+    HFX_CUDA_TRY(cudaGetLastError());
+    return HFX_OK;
+  }
+  Schedule* S = nullptr;
+  hfx_status s = get_schedule(c, n_orb, &S);
+  if (s != HFX_OK) return s;
+  const Layout L = layout_of(c, *S, n_orb, n_pairs);
+  if (!c->ws || c->ws_bytes < L.total)
+    return fail(HFX_ERR_OOM, "workspace too small: have %zu bytes, need %zu (hfx_workspace_bytes)", c->ws_bytes, L.total);
+  char* ws = (char*)c->ws;
+  if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
+
+  // stage a1: pair list -> couples
+  const int nkeys = 2 * S->nslots;
+  int* keys = (int*)(ws + L.keys);
+  int* counts = (int*)(ws + L.counts);
+  int* couple_base = (int*)(ws + L.couple_base);
+  int* cursor = (int*)(ws + L.cursor);
+  int4* couples = (int4*)(ws + L.couples);
+  int* batch_begin = (int*)(ws + L.batch_begin);
+  int* slot_begin = (int*)(ws + L.slot_begin);
+  HFX_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)nkeys * sizeof(int), st));
+  HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S->max_total_couples * sizeof(int4), st));
+  {
+    const int threads = 256;
+    const int blocks = (int)std::min<long long>((n_pairs + threads - 1) / threads, (long long)c->sm_count * 8);
+    k_plan_count<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S->b, S->nb, S->d_slot_of_bp, keys,
+                                             counts, c->d_err);
+    k_plan_scan<<<1, 1024, 0, st>>>(S->nslots, S->d_slot_blocks, S->b, n_orb, counts, couple_base, S->nbatches,
+                                    S->d_batch_slot_begin, batch_begin, slot_begin, c->d_err);
+    const size_t cur_bytes = (size_t)nkeys * sizeof(int);
+    const int use_smem = cur_bytes <= 48 * 1024 ? 1 : 0;
+    k_plan_scatter<<<1, 32, use_smem ? cur_bytes : 0, st>>>((const int2*)pairs, n_pairs, keys, counts, couple_base,
+                                                            nkeys, use_smem, cursor, couples);
+  }
+  HFX_CUDA_TRY(cudaGetLastError());
+
+  hfx_status rs;
+  if (c->prec == HFX_PREC_FP64) {
+    rs = run_passes<double>(c, *S, L, (const double*)orbitals, n_orb, flags, vxphi, st);
+  } else {
+    const float* orb32;
+    if (flags & HFX_ORBITALS_F32) {
+      orb32 = (const float*)orbitals;
+    } else {
+      float* dst = (float*)(ws + L.orb32);
+      const long long n = (long long)n_orb * c->N;
+      const int blocks = (int)std::min<long long>((n / 2 + 255) / 256 + 1, (long long)c->sm_count * 16);
+      k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
+      orb32 = dst;
+    }
+    rs = run_passes<float>(c, *S, L, orb32, n_orb, flags, vxphi, st);
+  }
+  if (rs != HFX_OK) return rs;
+  const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
+  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, couple_base + nkeys, c->grid[1], scale,
+                                    accumulate ? 1 : 0, ex_dev);
+  HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_apply(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
+                                uint32_t flags, double* ex_dev, double* vxphi, void* cuda_stream) {
+  g_last_error.clear();
+  return apply_impl(c, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi, (cudaStream_t)cuda_stream);
+}
+
+extern "C" hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n, void* cuda_stream) {
+  g_last_error.clear();
+  if (n < 0 || (n > 0 && (!ctxs || !args))) return fail(HFX_ERR_INVALID_ARG, "bad batch arguments");
+  for (int32_t k = 0; k < n; ++k) {
+    const hfx_apply_args& a = args[k];
+    hfx_status s = apply_impl(ctxs[k], a.orbitals, a.n_orb, a.pairs, a.n_pairs, a.flags, a.ex_dev, a.vxphi,
+                              (cudaStream_t)cuda_stream);
+    if (s != HFX_OK) {
+      std::string m = g_last_error;
+      return fail(s, "problem %d: %s", (int)k, m.c_str());
+    }
+  }
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int h = 0;
+  HFX_CUDA_TRY(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HFX_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h) {
+    HFX_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+    HFX_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  if (h & kErrTimeout) return fail(HFX_ERR_TIMEOUT, "a device-side wait timed out");
+  if (h & kErrBadPair) return fail(HFX_ERR_BAD_PAIR_LIST, "pair list had entries outside 0 <= i <= j < n_orb or too many copies of a pair; they were skipped");
+  return HFX_OK;
+}

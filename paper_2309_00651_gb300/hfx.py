@@ -1,0 +1,229 @@
+"""ctypes binding of libhfx (include/hfx.h): same entry points, torch tensors in, no compute here.
+
+Every step of the exchange path runs in the CUDA library; this module only marshals device
+pointers, sizes and the current CUDA stream.  If libhfx.so is missing it raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhfx.so")
+
+HFX_OK = 0
+STATUS_NAMES = {0: "HFX_OK", -1: "HFX_ERR_INVALID_ARG", -2: "HFX_ERR_UNSUPPORTED_GRID", -3: "HFX_ERR_OOM",
+                -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT"}
+PRECISION = {"fp64": 0, "fp32": 1}
+KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
+HFX_ENERGY_ONLY = 0x1
+HFX_ACCUMULATE = 0x2
+HFX_ORBITALS_F32 = 0x4
+
+# every symbol include/hfx.h declares
+EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
+            "hfx_sync_status", "hfx_last_error", "hfx_destroy")
+
+
+class HfxBox(ctypes.Structure):
+    _fields_ = [("lattice", (ctypes.c_double * 3) * 3)]
+
+
+class HfxApplyArgs(ctypes.Structure):
+    _fields_ = [("orbitals", ctypes.c_void_p), ("n_orb", ctypes.c_int32), ("pairs", ctypes.c_void_p),
+                ("n_pairs", ctypes.c_int64), ("flags", ctypes.c_uint32), ("ex_dev", ctypes.c_void_p),
+                ("vxphi", ctypes.c_void_p)]
+
+
+class HFXError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libhfx.so (built by paper_2309_00651_gb300.build.build()); raises if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhfx.so not found at {path}: build it with paper_2309_00651_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, i32, i64, u32, dbl, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32,
+                                   ctypes.c_double, ctypes.c_size_t)
+    L.hfx_create.argtypes = [ctypes.POINTER(HfxBox), ctypes.POINTER(i32), dbl, ctypes.c_int, dbl, ctypes.c_int,
+                             ctypes.POINTER(vp)]
+    L.hfx_create.restype = ctypes.c_int
+    L.hfx_workspace_bytes.argtypes = [vp, i32, i64]
+    L.hfx_workspace_bytes.restype = sz
+    L.hfx_set_workspace.argtypes = [vp, vp, sz]
+    L.hfx_set_workspace.restype = ctypes.c_int
+    L.hfx_apply.argtypes = [vp, vp, i32, vp, i64, u32, vp, vp, vp]
+    L.hfx_apply.restype = ctypes.c_int
+    L.hfx_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HfxApplyArgs), i32, vp]
+    L.hfx_apply_batched.restype = ctypes.c_int
+    L.hfx_sync_status.argtypes = [vp, vp]
+    L.hfx_sync_status.restype = ctypes.c_int
+    L.hfx_last_error.argtypes = []
+    L.hfx_last_error.restype = ctypes.c_char_p
+    L.hfx_destroy.argtypes = [vp]
+    L.hfx_destroy.restype = None
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != HFX_OK:
+        msg = load_library().hfx_last_error()
+        raise HFXError(status, msg.decode() if msg else "")
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else int(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------------------
+# entry points, same names as the C ABI
+# ---------------------------------------------------------------------------------------
+
+def hfx_create(lattice, grid: Sequence[int], ecut: float = 0.0, kernel: str = "coulomb", alpha: float = 0.25,
+               precision: str = "fp32") -> ctypes.c_void_p:
+    L = load_library()
+    box = HfxBox()
+    for a in range(3):
+        for b in range(3):
+            box.lattice[a][b] = float(lattice[a][b])
+    g = (ctypes.c_int32 * 3)(*[int(x) for x in grid])
+    out = ctypes.c_void_p()
+    _check(L.hfx_create(ctypes.byref(box), g, float(ecut), KERNEL[kernel], float(alpha), PRECISION[precision],
+                        ctypes.byref(out)))
+    return out
+
+
+def hfx_workspace_bytes(ctx, n_orb: int, n_pairs: int) -> int:
+    return int(load_library().hfx_workspace_bytes(ctx, int(n_orb), int(n_pairs)))
+
+
+def hfx_set_workspace(ctx, buf: torch.Tensor) -> None:
+    _check(load_library().hfx_set_workspace(ctx, _ptr(buf), buf.numel() * buf.element_size()))
+
+
+def hfx_apply(ctx, orbitals: torch.Tensor, pairs: torch.Tensor, ex: torch.Tensor, vxphi: Optional[torch.Tensor],
+              flags: int = 0, stream: Optional[torch.cuda.Stream] = None) -> None:
+    n_orb = orbitals.shape[0]
+    _check(load_library().hfx_apply(ctx, _ptr(orbitals), int(n_orb), _ptr(pairs), int(pairs.shape[0]), int(flags),
+                                    _ptr(ex), _ptr(vxphi), _stream_handle(stream)))
+
+
+def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """ctxs: list of contexts; args: list of (orbitals, pairs, ex, vxphi, flags)."""
+    n = len(ctxs)
+    carr = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    aarr = (HfxApplyArgs * n)()
+    for k, (orb, pairs, ex, v, flags) in enumerate(args):
+        aarr[k] = HfxApplyArgs(_ptr(orb), int(orb.shape[0]), _ptr(pairs), int(pairs.shape[0]), int(flags), _ptr(ex),
+                               _ptr(v))
+    _check(load_library().hfx_apply_batched(carr, aarr, n, _stream_handle(stream)))
+
+
+def hfx_sync_status(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_sync_status(ctx, _stream_handle(stream)))
+
+
+def hfx_last_error() -> str:
+    m = load_library().hfx_last_error()
+    return m.decode() if m else ""
+
+
+def hfx_destroy(ctx) -> None:
+    load_library().hfx_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------------------
+# convenience wrapper: one context + a torch-owned workspace
+# ---------------------------------------------------------------------------------------
+
+class Exchange:
+    """Exact exchange for one cell and grid on the current CUDA device.
+
+    ``apply(phi, pairs)`` returns (E_x as a 1-element float64 device tensor, V_x phi float64
+    [n_orb, n1, n2, n3] or None with energy_only).
+    """
+
+    def __init__(self, lattice, grid: Sequence[int], ecut: float = 0.0, alpha: float = 0.25,
+                 precision: str = "fp32", kernel: str = "coulomb"):
+        self.lattice = [[float(x) for x in row] for row in lattice]
+        self.grid = tuple(int(x) for x in grid)
+        self.alpha = float(alpha)
+        self.precision = precision
+        self.ctx = hfx_create(self.lattice, self.grid, ecut, kernel, alpha, precision)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._ws: Optional[torch.Tensor] = None
+
+    @property
+    def volume(self) -> float:
+        import numpy as np
+        return float(abs(np.linalg.det(np.array(self.lattice))))
+
+    @property
+    def npoints(self) -> int:
+        return self.grid[0] * self.grid[1] * self.grid[2]
+
+    def ensure_workspace(self, n_orb: int, n_pairs: int) -> None:
+        need = hfx_workspace_bytes(self.ctx, n_orb, n_pairs)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            hfx_set_workspace(self.ctx, self._ws)
+
+    def apply(self, phi: torch.Tensor, pairs: torch.Tensor, energy_only: bool = False, accumulate: bool = False,
+              ex: Optional[torch.Tensor] = None, vxphi: Optional[torch.Tensor] = None,
+              stream: Optional[torch.cuda.Stream] = None) -> Tuple[torch.Tensor, Optional[torch.Tensor]]:
+        if not phi.is_cuda or not pairs.is_cuda:
+            raise ValueError("phi and pairs must be CUDA tensors")
+        if phi.dtype not in (torch.float64, torch.float32) or not phi.is_contiguous():
+            raise ValueError("phi must be a contiguous float64 (or float32) tensor [n_orb, n1, n2, n3]")
+        if tuple(phi.shape[1:]) != self.grid:
+            raise ValueError(f"phi grid {tuple(phi.shape[1:])} != context grid {self.grid}")
+        if pairs.dtype != torch.int32 or pairs.dim() != 2 or pairs.shape[1] != 2 or not pairs.is_contiguous():
+            raise ValueError("pairs must be a contiguous int32 tensor [n_pairs, 2]")
+        flags = 0
+        if energy_only:
+            flags |= HFX_ENERGY_ONLY
+        if accumulate:
+            flags |= HFX_ACCUMULATE
+        if phi.dtype == torch.float32:
+            flags |= HFX_ORBITALS_F32
+        n_orb = phi.shape[0]
+        self.ensure_workspace(n_orb, pairs.shape[0])
+        if ex is None:
+            ex = torch.zeros(1, dtype=torch.float64, device=phi.device)
+        if vxphi is None and not energy_only:
+            vxphi = torch.empty(phi.shape, dtype=torch.float64, device=phi.device)
+        hfx_apply(self.ctx, phi, pairs, ex, None if energy_only else vxphi, flags, stream)
+        return ex, (None if energy_only else vxphi)
+
+    def sync_status(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        hfx_sync_status(self.ctx, stream)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            hfx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,81 @@
+"""The C-ABI library builds, loads, exports every symbol include/hfx.h declares, and rejects
+bad arguments on the host before touching a GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2309_00651_gb300 import build, hfx
+    build.build()
+    return hfx.load_library()
+
+
+def declared_symbols():
+    with open(os.path.join(ROOT, "include", "hfx.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hfx_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("hfx_create", "hfx_apply", "hfx_apply_batched", "hfx_set_workspace", "hfx_workspace_bytes",
+              "hfx_sync_status", "hfx_last_error", "hfx_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2309_00651_gb300 import hfx
+    for name in declared_symbols():
+        assert hasattr(lib, name), f"{name} not exported"
+    assert set(declared_symbols()) <= set(hfx.EXPORTED)
+
+
+def test_host_side_argument_errors(lib):
+    from paper_2309_00651_gb300 import hfx
+    box = hfx.HfxBox()
+    for a in range(3):
+        box.lattice[a][a] = 10.0
+    out = ctypes.c_void_p()
+    g = (ctypes.c_int32 * 3)(32, 32, 32)
+    # NULL out
+    assert lib.hfx_create(ctypes.byref(box), g, 20.0, 0, 0.25, 1, None) == -1
+    # a grid edge with a prime factor 7
+    bad = (ctypes.c_int32 * 3)(28, 32, 32)
+    assert lib.hfx_create(ctypes.byref(box), bad, 20.0, 0, 0.25, 1, ctypes.byref(out)) == -2
+    assert "grid edge" in lib.hfx_last_error().decode()
+    assert not out.value
+    # odd edge
+    odd = (ctypes.c_int32 * 3)(15, 32, 32)
+    assert lib.hfx_create(ctypes.byref(box), odd, 20.0, 0, 0.25, 1, ctypes.byref(out)) == -2
+    # unknown precision / kernel
+    assert lib.hfx_create(ctypes.byref(box), g, 20.0, 0, 0.25, 7, ctypes.byref(out)) == -1
+    assert lib.hfx_create(ctypes.byref(box), g, 20.0, 9, 0.25, 1, ctypes.byref(out)) == -1
+    # sphere kernel without a cutoff
+    assert lib.hfx_create(ctypes.byref(box), g, 0.0, 1, 0.25, 1, ctypes.byref(out)) == -1
+    # degenerate cell
+    flat = hfx.HfxBox()
+    assert lib.hfx_create(ctypes.byref(flat), g, 20.0, 0, 0.25, 1, ctypes.byref(out)) == -1
+    # NULL contexts
+    assert lib.hfx_workspace_bytes(None, 16, 136) == 0
+    assert lib.hfx_apply(None, None, 16, None, 0, 0, None, None, None) == -1
+    assert lib.hfx_sync_status(None, None) == -1
+    assert lib.hfx_set_workspace(None, None, 0) == -1
+    lib.hfx_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2309_00651_gb300 import hfx
+    saved = hfx._lib
+    try:
+        hfx._lib = None
+        with pytest.raises(RuntimeError, match="libhfx.so not found"):
+            hfx.load_library(str(tmp_path / "missing.so"))
+    finally:
+        hfx._lib = saved

@@ -1,0 +1,181 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the FP64 path must match to 1e-8 relative and the FP32 path to 1e-6 relative in
+E_x and in ||V_x phi||_F (the stated accuracy targets of the two paths).  Integer work (pair
+staging) is checked exactly through its effect: every listed pair is counted once.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hfx_oracle as O  # noqa: E402
+from paper_2309_00651_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-8, "fp32": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_00651_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def run_gpu(phi, pairs, lattice, prec, **kw):
+    from paper_2309_00651_gb300 import hfx
+    ex = hfx.Exchange(lattice, phi.shape[1:], alpha=kw.pop("alpha", 0.25), precision=prec,
+                      kernel=kw.pop("kernel", "coulomb"), ecut=kw.pop("ecut", 0.0))
+    phi_d = torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    pairs_d = torch.from_numpy(np.ascontiguousarray(pairs, dtype=np.int32)).cuda()
+    E, V = ex.apply(phi_d, pairs_d, **kw)
+    ex.sync_status()
+    out = (E.item(), None if V is None else V.cpu().numpy())
+    ex.close()
+    return out
+
+
+def band_limited(n_orb, n, L, seed, frac=0.25):
+    raw = I.random_pw_orbitals(n_orb, L, n, ecut=0.5 * (2 * math.pi * (frac * n + 0.5) / L) ** 2, seed=seed)
+    phi, _ = I.loewdin(raw, L ** 3)
+    return phi
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_real_plane_wave_closed_form(prec):
+    L, n = 8.5, 16
+    lat = np.diag([L] * 3)
+    kset = np.array([[1, 0, 0], [0, 2, 1], [1, -1, 2], [2, 1, -1]])
+    phi = I.real_plane_wave_orbitals(kset, L, n)
+    E, V = run_gpu(phi, I.all_pairs(len(phi)), lat, prec)
+    E_ref, eps = O.closed_form_real(kset, lat)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    for b in range(len(phi)):
+        assert rel(V[b], eps[b // 2] * phi[b]) <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,n_orb", [(8, 5), (18, 13), (30, 9), (24, 17)])
+def test_small_grids_all_pairs(prec, n, n_orb):
+    """Several tiles, ragged blocks (n_orb not a multiple of the block), ragged z-chunks."""
+    L = 0.6 * n
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=n + n_orb)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert rel(V, V_ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_orthorhombic_non_cubic_grid(prec):
+    Ls = (9.0, 7.5, 11.0)
+    grid = (20, 16, 24)
+    lat = np.diag(Ls)
+    rng = np.random.default_rng(3)
+    raw = rng.standard_normal((7,) + grid)
+    phi, _ = I.loewdin(raw, float(np.prod(Ls)))
+    pairs = I.all_pairs(7)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert rel(V, V_ref) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pw16_n32_full(prec):
+    """The 16-orbital random-PW workload: L = 10 bohr, 32^3, Ecut = 20 Ha, all 136 pairs."""
+    w = I.WORKLOADS["pw16_n32"]
+    phi, pairs, _ = I.make_workload(w)
+    E_ref, V_ref = O.exchange(phi, pairs, w.lattice)
+    E, V = run_gpu(phi, pairs, w.lattice, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert rel(V, V_ref) <= TOL[prec]
+    # per-orbital norm-wise error as well
+    worst = max(rel(V[i], V_ref[i]) for i in range(len(V)))
+    assert worst <= 10 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_shuffled_subset_with_diagonals_and_accumulate(prec):
+    n, L, n_orb = 24, 12.0, 20
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=5)
+    allp = I.all_pairs(n_orb)
+    rng = np.random.default_rng(6)
+    sub = allp[rng.permutation(len(allp))[: len(allp) // 3]]
+    E_ref, V_ref = O.exchange(phi, sub, lat)
+    E, V = run_gpu(phi, sub, lat, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert rel(V, V_ref) <= TOL[prec]
+    # linearity: two halves with HFX_ACCUMULATE equal the whole list
+    from paper_2309_00651_gb300 import hfx
+    ex = hfx.Exchange(lat, (n, n, n), precision=prec)
+    phi_d = torch.from_numpy(phi).cuda()
+    h1 = torch.from_numpy(sub[::2].copy()).cuda()
+    h2 = torch.from_numpy(sub[1::2].copy()).cuda()
+    E1, V1 = ex.apply(phi_d, h1)
+    E2, V2 = ex.apply(phi_d, h2, accumulate=True, ex=E1, vxphi=V1)
+    assert abs(E2.item() - E_ref) <= TOL[prec] * abs(E_ref)
+    assert rel(V2.cpu().numpy(), V_ref) <= TOL[prec]
+    # energy only
+    Ee, Ve = ex.apply(phi_d, torch.from_numpy(sub).cuda(), energy_only=True)
+    assert Ve is None and abs(Ee.item() - E_ref) <= TOL[prec] * abs(E_ref)
+    ex.close()
+
+
+def test_empty_list_and_determinism():
+    from paper_2309_00651_gb300 import hfx
+    n, L, n_orb = 16, 8.0, 6
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=9)
+    ex = hfx.Exchange(lat, (n, n, n), precision="fp32")
+    phi_d = torch.from_numpy(phi).cuda()
+    empty = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    E, V = ex.apply(phi_d, empty)
+    assert E.item() == 0.0 and float(V.abs().max()) == 0.0
+    pairs = torch.from_numpy(I.all_pairs(n_orb)).cuda()
+    Ea, Va = ex.apply(phi_d, pairs)
+    Eb, Vb = ex.apply(phi_d, pairs)
+    assert Ea.item() == Eb.item() and torch.equal(Va, Vb)
+    ex.close()
+
+
+def test_bad_pairs_are_reported_and_skipped():
+    from paper_2309_00651_gb300 import hfx
+    n, L, n_orb = 16, 8.0, 6
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=10)
+    good = I.all_pairs(n_orb)
+    bad = np.concatenate([good, np.array([[3, 1], [0, 6], [-1, 2]], dtype=np.int32)])
+    E_ref, V_ref = O.exchange(phi, good, lat)
+    ex = hfx.Exchange(lat, (n, n, n), precision="fp64")
+    E, V = ex.apply(torch.from_numpy(phi).cuda(), torch.from_numpy(bad).cuda())
+    with pytest.raises(hfx.HFXError) as ei:
+        ex.sync_status()
+    assert ei.value.status == -5
+    assert abs(E.item() - E_ref) <= 1e-8 * abs(E_ref)
+    assert rel(V.cpu().numpy(), V_ref) <= 1e-8
+    ex.sync_status()  # cleared
+    ex.close()
+
+
+def test_sphere_kernel_matches_oracle():
+    n, L, n_orb, ecut = 24, 10.0, 7, 3.0
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=11)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat, sphere_ecut=ecut)
+    E, V = run_gpu(phi, pairs, lat, "fp64", kernel="coulomb_sphere", ecut=ecut)
+    assert abs(E - E_ref) <= 1e-8 * abs(E_ref)
+    assert rel(V, V_ref) <= 1e-8
