@@ -1,0 +1,379 @@
+"""Benchmark of the Gamma-point exact-exchange path (E_x + V_x phi) on GB300.
+
+One step = one full hfx_apply over the whole pair list of the workload (pair-list staging,
+pair products, forward 3D FFTs, Coulomb multiply + energy, inverse 3D FFTs, V_x phi
+accumulation, energy reduction).  Metric: orbital pairs per second.
+
+Default workload: the 32-H2O water box: 128 Gaussian-type orbitals (sigma = 1.2 bohr, four
+per jittered lattice site), L = 18.6 bohr, 72^3 grid, Ecut = 40 Ha, all 8256 pairs, seeded
+synthetic data standing in for the paper's 32-water system.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                       [--impl reference] [--no-fp64-compare] [--no-cpu-baseline]
+Under torchrun each rank runs an independent replica of the workload on its own GPU (pairs of
+independent problems need no exchange); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "HF-exchange orbital pairs/s (E_x+V_xφ), mixed vs FP64 GPU path at stated error"
+UNIT = "pairs/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="libhfx", choices=["libhfx", "reference"])
+    ap.add_argument("--workload", default="water32_n72")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(w, n_pairs):
+    return {
+        "workload": f"{w.name}: {w.n_orb} orbitals, cubic L={w.L} bohr, {w.n}^3 grid, Ecut={w.ecut} Ha, "
+                    f"{'Gaussian sigma=' + str(w.sigma) if w.kind == 'gauss' else 'random PW'} orbitals, "
+                    f"Loewdin, {n_pairs} pairs, seed {w.seed}",
+        "n_orb": w.n_orb, "grid": [w.n, w.n, w.n], "L_bohr": w.L, "n_pairs": int(n_pairs), "alpha": 0.25,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------------
+
+def oracle_rate(phi, pairs, lattice, n_sample, seed=0):
+    """Time the oracle (as it stands) on a seeded sample of pairs; returns (pairs/s, seconds, E, V)."""
+    from oracle import hfx_oracle as O
+    from paper_2309_00651_gb300 import inputs as I
+    sub = I.random_pairs_subset(pairs, n_sample, seed)
+    t0 = time.perf_counter()
+    E, V = O.exchange(phi, sub, lattice, alpha=0.25)
+    dt = time.perf_counter() - t0
+    return len(sub) / dt, dt, sub, E, V
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2309_00651_gb300 import inputs as I
+    w = I.WORKLOADS[args.workload]
+    phi, pairs, info = I.make_workload(w)
+    # calibrate the per-pair cost, then size each step so the whole run stays within ~3 minutes
+    rate, dt, _, _, _ = oracle_rate(phi, pairs, w.lattice, 4, seed=123)
+    per_step = max(2, int(150.0 / max(1, args.steps + args.warmup) * rate))
+    per_step = min(per_step, len(pairs))
+    for k in range(args.warmup):
+        oracle_rate(phi, pairs, w.lattice, per_step, seed=1000 + k)
+    total_pairs, total_t = 0, 0.0
+    for k in range(args.steps):
+        _, dt, sub, _, _ = oracle_rate(phi, pairs, w.lattice, per_step, seed=k)
+        total_pairs += len(sub)
+        total_t += dt
+    value = total_pairs / total_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_desc(w, len(pairs)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{per_step} seeded random pairs of the {len(pairs)}-pair list per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# the CUDA arm
+# ------------------------------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2309_00651_gb300 import build as B
+    B.build()
+    from paper_2309_00651_gb300 import hfx
+    from paper_2309_00651_gb300 import inputs as I
+
+    w = I.WORKLOADS[args.workload]
+    phi_np, pairs_np, info = I.make_workload(w)
+    n_orb, N = w.n_orb, w.n ** 3
+    P = len(pairs_np)
+    phi = torch.from_numpy(phi_np).to(dev)
+    pairs = torch.from_numpy(pairs_np).to(dev)
+
+    ex = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision=args.precision)
+    ex.ensure_workspace(n_orb, P)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    V = torch.empty(phi.shape, dtype=torch.float64, device=dev)
+    stats = hfx.hfx_plan_stats(ex.ctx, n_orb, P, 0)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ex.apply(phi, pairs, ex=E, vxphi=V)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ex.sync_status()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # timed region: K full steps, per-pass events recorded by the library on the same stream
+    hfx.hfx_profile_enable(ex.ctx, True)
+    hfx.hfx_profile_read(ex.ctx)
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        stop.record(stream)
+        barrier()
+    hfx.hfx_profile_enable(ex.ctx, False)
+    prof = hfx.hfx_profile_read(ex.ctx)
+    ms_total = start.elapsed_time(stop)
+    if world > 1:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * P * args.steps / (ms_total / 1000.0)
+
+    # roofline of the dominant pass (largest device time), algorithmic bytes per couple:
+    #   fwd_yz writes the packed transform (8 N B per couple, FP32 complex);
+    #   x_coulomb reads and writes it (16 N B); y_inv_acc reads it (8 N B).
+    csize = 8 if args.precision == "fp32" else 16
+    per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_inv_acc": csize * N}
+    n_couples_total = stats["couples"]  # packed complex transforms per call (full list: every block pair full)
+    dom = max(per_couple, key=lambda k: prof[k]["ms"])
+    launches = max(1, prof[dom]["launches"])
+    avg_ms = prof[dom]["ms"] / launches
+    couples_per_launch = n_couples_total * args.steps / launches
+    alg_bytes = per_couple[dom] * couples_per_launch
+    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = None
+    prof_file = os.path.join(ROOT, "profiles", f"{dom}_{w.name}_{args.precision}.traffic.json")
+    if os.path.exists(prof_file):
+        try:
+            with open(prof_file) as f:
+                tj = json.load(f)
+            if tj.get("kernel_source_hash") == B.source_hash():
+                traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_kind": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
+                "pass_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof}}
+
+    # end to end through the public API with host buffers: H2D orbitals + pairs, D2H E + V
+    phi_h = torch.from_numpy(phi_np).pin_memory()
+    pairs_h = torch.from_numpy(pairs_np).pin_memory()
+    V_h = torch.empty(phi.shape, dtype=torch.float64).pin_memory()
+    E_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    phi_dev = torch.empty_like(phi)
+    pairs_dev = torch.empty_like(pairs)
+
+    def e2e_step():
+        phi_dev.copy_(phi_h, non_blocking=True)
+        pairs_dev.copy_(pairs_h, non_blocking=True)
+        ex.apply(phi_dev, pairs_dev, ex=E, vxphi=V)
+        V_h.copy_(V, non_blocking=True)
+        E_h.copy_(E, non_blocking=True)
+
+    e2e_step()
+    barrier()
+    s2, t2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    t2.record(stream)
+    barrier()
+    e2e_ms = s2.elapsed_time(t2) / args.e2e_steps
+    e2e = {"value": world * P / (e2e_ms / 1000.0), "unit": UNIT,
+           "h2d_bytes_per_step": phi_h.numel() * 8 + pairs_h.numel() * 4,
+           "d2h_bytes_per_step": V_h.numel() * 8 + 8, "ms_per_step": e2e_ms}
+
+    # homogeneity check of this result: E_x = 1/2 (Omega/N) sum_i <phi_i, V_i>
+    E_val = float(E.item())
+    hom = 0.5 * (w.volume / N) * float(torch.sum(phi * V).item())
+    checks = {"E_x": E_val, "homogeneity_rel_err": abs(hom - E_val) / abs(E_val)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded water-box-shaped orbitals; no dataset)",
+        "config": dict(workload_desc(w, P), precision=args.precision,
+                       l2="inputs larger than L2 (FP64 orbitals %.0f MB + transform batches %.0f MB per step)" % (
+                           phi_np.nbytes / 1e6, stats["max_batch_couples"] * N * csize / 1e6),
+                       parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                       block=stats["block"], batches=stats["batches"]),
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": stats["launches"] * args.steps,
+        "clocks": clk.summary(),
+        "checks": checks,
+    }
+
+    if rank == 0 and args.precision == "fp32" and not args.no_fp64_compare:
+        ex64 = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision="fp64")
+        ex64.ensure_workspace(n_orb, P)
+        E64 = torch.zeros(1, dtype=torch.float64, device=dev)
+        V64 = torch.empty_like(V)
+        ex64.apply(phi, pairs, ex=E64, vxphi=V64)
+        torch.cuda.synchronize()
+        k64 = 2
+        s3, t3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s3.record(stream)
+        for _ in range(k64):
+            ex64.apply(phi, pairs, ex=E64, vxphi=V64)
+        t3.record(stream)
+        torch.cuda.synchronize()
+        ms64 = s3.elapsed_time(t3) / k64
+        line["fp64_gpu_path"] = {
+            "value": P / (ms64 / 1000.0), "unit": UNIT, "ms_per_step": ms64, "steps": k64,
+            "mixed_speedup": (P / (ms_step / 1000.0)) / (P / (ms64 / 1000.0)),
+            "E_rel_diff_fp32_vs_fp64": abs(E_val - E64.item()) / abs(E64.item()),
+            "V_rel_diff_fp32_vs_fp64": float(torch.linalg.norm(V - V64) / torch.linalg.norm(V64)),
+        }
+        ex64.close()
+
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle as it stands on the host cores, on a bounded sample of the same workload;
+        # the GPU path runs the same sample list for the stated error
+        ncpu = len(os.sched_getaffinity(0))
+        rate, dt, _, _, _ = oracle_rate(phi_np, pairs_np, w.lattice, 4, seed=321)
+        n_sample = int(max(8, min(P, 20.0 * rate)))
+        rate, dt, sub, E_o, V_o = oracle_rate(phi_np, pairs_np, w.lattice, n_sample, seed=7)
+        sub_d = torch.from_numpy(sub).to(dev)
+        Es, Vs = ex.apply(phi, sub_d)
+        torch.cuda.synchronize()
+        Vs_np = Vs.cpu().numpy()
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(sub)} seeded random pairs of the {P}-pair list ({dt:.1f} s, numpy FP64, "
+                      f"1 thread of {ncpu} host cores)",
+            "gpu_error_on_sample": {"precision": args.precision,
+                                    "E_rel": abs(Es.item() - E_o) / abs(E_o),
+                                    "V_rel": float(np.linalg.norm(Vs_np - V_o) / np.linalg.norm(V_o))},
+        }
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ex.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

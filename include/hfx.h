@@ -142,6 +142,23 @@ hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, i
  * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST or HFX_ERR_TIMEOUT. */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
 
+/* hfx_plan_stats -- what hfx_apply(c, ..., n_orb, ..., n_pairs, flags, ...) will launch, from the
+ * host schedule alone (no device work):
+ *   out[0] = kernel launches per call, out[1] = batches, out[2] = orbital block size,
+ *   out[3] = largest number of packed pair couples (two pairs per complex 3D transform) held
+ *   by one batch, out[4] = couples of the whole call when every block pair is full (the
+ *   exact count for the complete pair list). */
+hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[5]);
+
+/* hfx_profile_enable / hfx_profile_read -- per-pass device time.  While enabled, every
+ * hfx_apply on the context records CUDA events around each pass on its own stream (pair
+ * staging, forward yz-plane pass, x/Coulomb pass, inverse-y/accumulate pass, energy sum).
+ * hfx_profile_read waits for the recorded events and returns, per pass (index 0..4 in that
+ * order), the summed milliseconds and the number of launches since the last read, then
+ * resets them.  Not for use inside stream capture. */
+hfx_status hfx_profile_enable(hfx_ctx* c, int on);
+hfx_status hfx_profile_read(hfx_ctx* c, double ms[5], int64_t launches[5]);
+
 /* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
  * thread's next libhfx call. */
 const char* hfx_last_error(void);

@@ -32,6 +32,19 @@ def nvcc_path() -> str:
     raise RuntimeError("nvcc not found (CUDA toolkit required to build libhfx)")
 
 
+def source_hash() -> str:
+    """Hash of the CUDA/C sources and headers alone (the same on every machine)."""
+    h = hashlib.sha256()
+    for d in (CSRC, INCLUDE):
+        for name in sorted(os.listdir(d)):
+            p = os.path.join(d, name)
+            if os.path.isfile(p):
+                h.update(name.encode())
+                with open(p, "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _stamp() -> str:
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):

@@ -209,7 +209,39 @@ struct hfx_ctx {
   size_t transform_budget = size_t(1) << 30;
   int blocks_fwd = 1, blocks_x = 1;
   std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
+  // optional per-pass device timing (hfx_profile_enable)
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
 };
+
+enum { kProfStage = 0, kProfFwd = 1, kProfX = 2, kProfAcc = 3, kProfEnergy = 4, kProfSlots = 5 };
+
+static cudaEvent_t prof_event(hfx_ctx* c) {
+  if (c->ev_pool.empty()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = c->ev_pool.back();
+  c->ev_pool.pop_back();
+  return e;
+}
+
+// records an event on `st` when profiling is on; returns it (or NULL)
+static cudaEvent_t prof_mark(hfx_ctx* c, cudaStream_t st) {
+  if (!c->prof_on) return nullptr;
+  cudaEvent_t e = prof_event(c);
+  if (e) cudaEventRecord(e, st);
+  return e;
+}
+static void prof_close(hfx_ctx* c, int slot, cudaEvent_t begin, cudaStream_t st) {
+  if (!c->prof_on || !begin) return;
+  cudaEvent_t e = prof_event(c);
+  if (!e) return;
+  cudaEventRecord(e, st);
+  c->ev_pending.push_back({slot, {begin, e}});
+}
 
 static size_t real_size(const hfx_ctx* c) { return c->prec == HFX_PREC_FP64 ? 8 : 4; }
 static size_t cplx_size(const hfx_ctx* c) { return 2 * real_size(c); }
@@ -227,6 +259,10 @@ static size_t smem_acc(const hfx_ctx* c) {
 }
 
 static void free_ctx_tables(hfx_ctx* c) {
+  for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+  c->ev_pending.clear();
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
   for (auto& p : c->d_tw) { if (p) cudaFree(p); p = nullptr; }
   if (c->d_vtab) cudaFree(c->d_vtab);
   if (c->d_err) cudaFree(c->d_err);
@@ -611,14 +647,20 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
     const long long items1 = cap * g.n1, items2 = cap * g.n2;
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
+    cudaEvent_t e0 = prof_mark(c, st);
     Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, batch_begin, b, W, (const C*)c->d_tw[1],
                       (const C*)c->d_tw[2]);
+    prof_close(c, kProfFwd, e0, st);
+    e0 = prof_mark(c, st);
     Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, batch_begin, b, W, (const T*)c->d_vtab,
                          (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
+    prof_close(c, kProfX, e0, st);
     if (!energy_only) {
       dim3 grid3(nzc, g.n1, s1 - s0);
+      e0 = prof_mark(c, st);
       Passes<T>::y_inv_acc(g, grid3, smem_acc(c), st, orb, couples, batch_begin, b, slot_begin, S.d_slot_blocks, s0,
                            S.b, n_orb, W, (const C*)c->d_tw[1], vxphi, vscale);
+      prof_close(c, kProfAcc, e0, st);
     }
   }
   return HFX_OK;
@@ -666,6 +708,7 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
   int4* couples = (int4*)(ws + L.couples);
   int* batch_begin = (int*)(ws + L.batch_begin);
   int* slot_begin = (int*)(ws + L.slot_begin);
+  cudaEvent_t e_stage = prof_mark(c, st);
   HFX_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)nkeys * sizeof(int), st));
   HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S->max_total_couples * sizeof(int4), st));
   {
@@ -684,6 +727,7 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
 
   hfx_status rs;
   if (c->prec == HFX_PREC_FP64) {
+    prof_close(c, kProfStage, e_stage, st);
     rs = run_passes<double>(c, *S, L, (const double*)orbitals, n_orb, flags, vxphi, st);
   } else {
     const float* orb32;
@@ -696,12 +740,15 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
       k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
       orb32 = dst;
     }
+    prof_close(c, kProfStage, e_stage, st);
     rs = run_passes<float>(c, *S, L, orb32, n_orb, flags, vxphi, st);
   }
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
+  cudaEvent_t e_en = prof_mark(c, st);
   k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, couple_base + nkeys, c->grid[1], scale,
                                     accumulate ? 1 : 0, ex_dev);
+  prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
 }
@@ -741,4 +788,50 @@ extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
   if (h & kErrTimeout) return fail(HFX_ERR_TIMEOUT, "a device-side wait timed out");
   if (h & kErrBadPair) return fail(HFX_ERR_BAD_PAIR_LIST, "pair list had entries outside 0 <= i <= j < n_orb or too many copies of a pair; they were skipped");
   return HFX_OK;
+}
+
+extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[5]) {
+  g_last_error.clear();
+  if (!c || !out || n_orb <= 0 || n_pairs < 0) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
+  Schedule S = make_host_schedule(c, n_orb);
+  const bool eo = (flags & HFX_ENERGY_ONLY) != 0;
+  long long launches = 0;
+  if (n_pairs > 0) {
+    launches = 3 /* count, scan, scatter */ + 1 /* energy */ + (long long)S.nbatches * (eo ? 2 : 3);
+    if (c->prec == HFX_PREC_FP32 && !(flags & HFX_ORBITALS_F32)) launches += 1; /* FP64 -> FP32 orbitals */
+  } else if (!(flags & HFX_ACCUMULATE)) {
+    launches = 1;
+  }
+  out[0] = launches;
+  out[1] = S.nbatches;
+  out[2] = S.b;
+  out[3] = S.max_batch_couples;
+  out[4] = S.max_total_couples;
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_profile_enable(hfx_ctx* c, int on) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  c->prof_on = on != 0;
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[5], int64_t launches[5]) {
+  g_last_error.clear();
+  if (!c || !ms || !launches) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
+  for (int k = 0; k < kProfSlots; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  hfx_status st = HFX_OK;
+  for (auto& pe : c->ev_pending) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(pe.second.second);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pe.second.first, pe.second.second);
+    if (e != cudaSuccess && st == HFX_OK) st = fail(HFX_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
+    ms[pe.first] += t;
+    launches[pe.first] += 1;
+    c->ev_pool.push_back(pe.second.first);
+    c->ev_pool.push_back(pe.second.second);
+  }
+  c->ev_pending.clear();
+  return st;
 }

@@ -26,7 +26,9 @@ HFX_ORBITALS_F32 = 0x4
 
 # every symbol include/hfx.h declares
 EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
-            "hfx_sync_status", "hfx_last_error", "hfx_destroy")
+            "hfx_sync_status", "hfx_plan_stats", "hfx_profile_enable", "hfx_profile_read", "hfx_last_error",
+            "hfx_destroy")
+PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_inv_acc", "energy")
 
 
 class HfxBox(ctypes.Structure):
@@ -71,6 +73,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_apply_batched.restype = ctypes.c_int
     L.hfx_sync_status.argtypes = [vp, vp]
     L.hfx_sync_status.restype = ctypes.c_int
+    L.hfx_plan_stats.argtypes = [vp, i32, i64, u32, ctypes.POINTER(i64)]
+    L.hfx_plan_stats.restype = ctypes.c_int
+    L.hfx_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.hfx_profile_enable.restype = ctypes.c_int
+    L.hfx_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+    L.hfx_profile_read.restype = ctypes.c_int
     L.hfx_last_error.argtypes = []
     L.hfx_last_error.restype = ctypes.c_char_p
     L.hfx_destroy.argtypes = [vp]
@@ -140,6 +148,24 @@ def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) ->
 
 def hfx_sync_status(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
     _check(load_library().hfx_sync_status(ctx, _stream_handle(stream)))
+
+
+def hfx_plan_stats(ctx, n_orb: int, n_pairs: int, flags: int = 0) -> dict:
+    out = (ctypes.c_int64 * 5)()
+    _check(load_library().hfx_plan_stats(ctx, int(n_orb), int(n_pairs), int(flags), out))
+    return {"launches": int(out[0]), "batches": int(out[1]), "block": int(out[2]), "max_batch_couples": int(out[3]),
+            "couples": int(out[4])}
+
+
+def hfx_profile_enable(ctx, on: bool) -> None:
+    _check(load_library().hfx_profile_enable(ctx, 1 if on else 0))
+
+
+def hfx_profile_read(ctx) -> dict:
+    ms = (ctypes.c_double * 5)()
+    n = (ctypes.c_int64 * 5)()
+    _check(load_library().hfx_profile_read(ctx, ms, n))
+    return {name: {"ms": float(ms[k]), "launches": int(n[k])} for k, name in enumerate(PASS_NAMES)}
 
 
 def hfx_last_error() -> str:

@@ -75,6 +75,9 @@ WORKLOADS = {
     "water32_n72": Workload("water32_n72", 128, 18.6, 72, 40.0, "gauss", seed=0, sigma=1.2),
     # 64 H2O box (paper's Fe3+/64-water cell size), 256 random-PW orbitals, 96^3, 20 Ha.
     "water64_n96": Workload("water64_n96", 256, 23.5, 96, 20.0, "pw", seed=0),
+    # small case of the water-box workload for profiling captures: 32 orbitals in the same
+    # 18.6 bohr cell and 72^3 grid (528 pairs; one batch of transforms still exceeds L2).
+    "water8_n72": Workload("water8_n72", 32, 18.6, 72, 40.0, "gauss", seed=0, sigma=1.2),
     # 128 H2O box (paper's 15.64 A cell = 29.6 bohr), 512 Gaussian orbitals, 128^3, 40 Ha,
     # overlap-screened pair list s_ij > 1e-6.
     "water128_n128": Workload("water128_n128", 512, 29.6, 128, 40.0, "gauss", seed=0,
