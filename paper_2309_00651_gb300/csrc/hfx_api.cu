@@ -84,6 +84,8 @@ static bool make_dim_plan(int n, DimPlan& d) {
     d.m[s] = m;
   }
   for (int s = d.ns; s < kMaxStages; ++s) { d.r[s] = 1; d.m[s] = 1; }
+  for (int s = 0; s < kMaxStages; ++s) d.mdiv[s] = FastDiv::make((uint32_t)d.m[s]);
+  d.ndiv = FastDiv::make((uint32_t)n);
   return true;
 }
 
@@ -110,18 +112,32 @@ struct Schedule {
   int n_orb = 0, b = 0, nb = 0, nslots = 0, nbatches = 0;
   std::vector<int2> slot_blocks;        // slot -> (I, J)
   std::vector<int> slot_of_bp;          // I*nb + J (I <= J) -> slot
-  std::vector<int> slot_cap;            // couples a slot can hold
+  std::vector<int> slot_cap;            // couples a slot holds (canonical layout, holes allowed)
+  std::vector<int> slot_couple_base;    // [nslots + 1], prefix of slot_cap
   std::vector<int> batch_slot_begin;    // [nbatches + 1]
+  // per batch: slots taken by the dense accumulation kernel and by the generic one
+  std::vector<int> dense_slots, generic_slots;             // concatenated over batches
+  std::vector<int> dense_begin, generic_begin;             // [nbatches + 1] offsets into the lists
   long long max_batch_couples = 0, max_total_couples = 0;
   // device copies
   int2* d_slot_blocks = nullptr;
   int* d_slot_of_bp = nullptr;
-  int* d_batch_slot_begin = nullptr;
+  int* d_slot_couple_base = nullptr;
+  int* d_dense_slots = nullptr;
+  int* d_generic_slots = nullptr;
 };
 
 static int block_size_of(int bi, int b, int n_orb) { return std::min(b, n_orb - bi * b); }
 
-static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budget, size_t bytes_per_couple) {
+// couples of a slot in the canonical layout: I != J: all sI sJ pairs, couple t/2 of
+// t = (i - I0) sJ + (j - J0); I == J: the sI (sI-1)/2 pairs i < j first, then the sI diagonal ones.
+static int slot_capacity(int si, int sj, bool diag) {
+  if (!diag) return (si * sj + 1) / 2;
+  return (si * (si - 1) / 2 + 1) / 2 + (si + 1) / 2;
+}
+
+static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budget, size_t bytes_per_couple,
+                           bool dense_ok) {
   S.n_orb = n_orb;
   S.b = b;
   S.nb = (n_orb + b - 1) / b;
@@ -162,9 +178,7 @@ static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budge
     bool open = false;
     for (auto bp : rd) {
       const int si = block_size_of(bp.x, b, n_orb), sj = block_size_of(bp.y, b, n_orb);
-      int cap;
-      if (bp.x != bp.y) cap = (si * sj + 1) / 2;
-      else cap = (si * (si - 1) / 2 + 1) / 2 + (si + 1) / 2;
+      const int cap = slot_capacity(si, sj, bp.x == bp.y);
       if (!open || in_batch + cap > budget_couples) {
         if (open) S.max_batch_couples = std::max(S.max_batch_couples, in_batch);
         S.batch_slot_begin.push_back((int)S.slot_blocks.size());
@@ -182,6 +196,22 @@ static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budge
   S.nslots = (int)S.slot_blocks.size();
   S.nbatches = (int)S.batch_slot_begin.size();
   S.batch_slot_begin.push_back(S.nslots);
+  S.slot_couple_base.assign(S.nslots + 1, 0);
+  for (int k = 0; k < S.nslots; ++k) S.slot_couple_base[k + 1] = S.slot_couple_base[k] + S.slot_cap[k];
+  S.dense_slots.clear();
+  S.generic_slots.clear();
+  S.dense_begin.assign(1, 0);
+  S.generic_begin.assign(1, 0);
+  for (int bt = 0; bt < S.nbatches; ++bt) {
+    for (int k = S.batch_slot_begin[bt]; k < S.batch_slot_begin[bt + 1]; ++k) {
+      const int2 bp = S.slot_blocks[k];
+      const bool full = block_size_of(bp.x, b, n_orb) == b && block_size_of(bp.y, b, n_orb) == b;
+      if (dense_ok && bp.x != bp.y && full) S.dense_slots.push_back(k);
+      else S.generic_slots.push_back(k);
+    }
+    S.dense_begin.push_back((int)S.dense_slots.size());
+    S.generic_begin.push_back((int)S.generic_slots.size());
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -248,14 +278,21 @@ static size_t cplx_size(const hfx_ctx* c) { return 2 * real_size(c); }
 static int zchunk(const hfx_ctx* c) { return c->prec == HFX_PREC_FP64 ? 4 : 8; }
 
 static size_t smem_fwd(const hfx_ctx* c) {
-  return (size_t)(c->grid[1] * c->grid[2] + c->grid[1] + c->grid[2]) * cplx_size(c);
+  return (size_t)(c->grid[1] * (c->grid[2] + 1) + c->grid[1] + c->grid[2]) * cplx_size(c);
 }
 static size_t smem_x(const hfx_ctx* c) {
-  return (size_t)(c->grid[0] * c->grid[2] + c->grid[0] + c->grid[2]) * cplx_size(c);
+  return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c);
 }
 static size_t smem_acc(const hfx_ctx* c) {
   const int zc = zchunk(c);
   return (size_t)(c->grid[1] * zc + c->grid[1]) * cplx_size(c) + (size_t)(2 * c->bsize) * c->grid[1] * zc * real_size(c);
+}
+static size_t smem_dense(const hfx_ctx* c) {
+  const int zc = zchunk(c);
+  return (size_t)(c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c);
+}
+static bool dense_available(const hfx_ctx* c) {
+  return c->prec == HFX_PREC_FP64 ? Passes<double>::has_dense(c->bsize) : Passes<float>::has_dense(c->bsize);
 }
 
 static void free_ctx_tables(hfx_ctx* c) {
@@ -270,9 +307,9 @@ static void free_ctx_tables(hfx_ctx* c) {
   c->d_err = nullptr;
   for (auto& kv : c->sched) {
     Schedule& S = *kv.second;
-    if (S.d_slot_blocks) cudaFree(S.d_slot_blocks);
-    if (S.d_slot_of_bp) cudaFree(S.d_slot_of_bp);
-    if (S.d_batch_slot_begin) cudaFree(S.d_batch_slot_begin);
+    for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
+                    (void*)S.d_dense_slots, (void*)S.d_generic_slots})
+      if (p) cudaFree(p);
   }
   c->sched.clear();
 }
@@ -373,6 +410,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   }
   c->N = (long long)grid[0] * grid[1] * grid[2];
   c->geo.n1 = grid[0]; c->geo.n2 = grid[1]; c->geo.n3 = grid[2]; c->geo.N = c->N;
+  c->geo.S = grid[2] + 1;  // odd row stride: column accesses of consecutive lines hit distinct banks
   std::memcpy(c->lat, box->lattice, sizeof(c->lat));
   const double (*A)[3] = c->lat;
   const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
@@ -389,7 +427,8 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-  const size_t need = std::max(std::max(smem_fwd(c.get()), smem_x(c.get())), smem_acc(c.get())) + 512;
+  const size_t need = std::max(std::max(smem_fwd(c.get()), smem_x(c.get())),
+                                std::max(smem_acc(c.get()), smem_dense(c.get()))) + 512;
   if (need > (size_t)c->max_smem)
     return fail(HFX_ERR_UNSUPPORTED_GRID, "a grid plane needs %zu bytes of shared memory (limit %d) at this precision",
                 need, c->max_smem);
@@ -429,18 +468,19 @@ extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes)
 // workspace layout
 // ------------------------------------------------------------------------------------
 struct Layout {
-  size_t orb32, W, epart, couples, keys, counts, couple_base, cursor, batch_begin, slot_begin, total;
+  size_t orb32, W, epart, couples, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static Schedule make_host_schedule(const hfx_ctx* c, int n_orb) {
   Schedule S;
-  build_schedule(S, n_orb, c->bsize, c->transform_budget, (size_t)c->N * cplx_size(c));
+  build_schedule(S, n_orb, c->bsize, c->transform_budget, (size_t)c->N * cplx_size(c), dense_available(c));
   return S;
 }
 
 static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long long n_pairs) {
+  (void)n_pairs;
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
@@ -449,13 +489,6 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
-  L.keys = take((size_t)std::max<long long>(n_pairs, 1) * sizeof(int));
-  const size_t nkeys = 2 * (size_t)S.nslots;
-  L.counts = take(nkeys * sizeof(int));
-  L.couple_base = take((nkeys + 1) * sizeof(int));
-  L.cursor = take(nkeys * sizeof(int));
-  L.batch_begin = take(((size_t)S.nbatches + 1) * sizeof(int));
-  L.slot_begin = take(((size_t)S.nslots + 1) * sizeof(int));
   L.total = off;
   return L;
 }
@@ -470,14 +503,20 @@ static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
   auto it = c->sched.find(n_orb);
   if (it != c->sched.end()) { *out = it->second.get(); return HFX_OK; }
   std::unique_ptr<Schedule> S(new Schedule(make_host_schedule(c, n_orb)));
-  hfx_status st = upload((void**)&S->d_slot_blocks, S->slot_blocks.data(), S->slot_blocks.size() * sizeof(int2));
-  if (st == HFX_OK) st = upload((void**)&S->d_slot_of_bp, S->slot_of_bp.data(), S->slot_of_bp.size() * sizeof(int));
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    return upload(dst, src, std::max<size_t>(bytes, 4));
+  };
+  hfx_status st = up((void**)&S->d_slot_blocks, S->slot_blocks.data(), S->slot_blocks.size() * sizeof(int2));
+  if (st == HFX_OK) st = up((void**)&S->d_slot_of_bp, S->slot_of_bp.data(), S->slot_of_bp.size() * sizeof(int));
   if (st == HFX_OK)
-    st = upload((void**)&S->d_batch_slot_begin, S->batch_slot_begin.data(), S->batch_slot_begin.size() * sizeof(int));
+    st = up((void**)&S->d_slot_couple_base, S->slot_couple_base.data(), S->slot_couple_base.size() * sizeof(int));
+  if (st == HFX_OK) st = up((void**)&S->d_dense_slots, S->dense_slots.data(), S->dense_slots.size() * sizeof(int));
+  if (st == HFX_OK)
+    st = up((void**)&S->d_generic_slots, S->generic_slots.data(), S->generic_slots.size() * sizeof(int));
   if (st != HFX_OK) {
-    if (S->d_slot_blocks) cudaFree(S->d_slot_blocks);
-    if (S->d_slot_of_bp) cudaFree(S->d_slot_of_bp);
-    if (S->d_batch_slot_begin) cudaFree(S->d_batch_slot_begin);
+    for (void* p : {(void*)S->d_slot_blocks, (void*)S->d_slot_of_bp, (void*)S->d_slot_couple_base,
+                    (void*)S->d_dense_slots, (void*)S->d_generic_slots})
+      if (p) cudaFree(p);
     return st;
   }
   *out = S.get();
@@ -497,126 +536,54 @@ __global__ void k_cast_f32(const double* __restrict__ src, float* __restrict__ d
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) dst[n - 1] = (float)src[n - 1];
 }
 
-__global__ void k_plan_count(const int2* __restrict__ pairs, long long P, int n_orb, int bsize, int nb,
-                             const int* __restrict__ slot_of_bp, int* __restrict__ keys, int* __restrict__ counts,
-                             int* __restrict__ err) {
+// every listed pair goes to its fixed place in the canonical couple layout of its block pair;
+// entries outside 0 <= i <= j < n_orb, and second copies of a pair, are flagged and skipped
+__global__ void k_plan_place(const int2* __restrict__ pairs, long long P, int n_orb, int bsize, int nb,
+                             const int* __restrict__ slot_of_bp, const int* __restrict__ slot_couple_base,
+                             int4* __restrict__ couples, int* __restrict__ err) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
     const int2 ij = pairs[p];
-    int key = -1;
-    if (ij.x >= 0 && ij.y < n_orb && ij.x <= ij.y) {
-      const int s = slot_of_bp[(ij.x / bsize) * nb + (ij.y / bsize)];
-      key = 2 * s + (ij.x == ij.y ? 1 : 0);
-      atomicAdd(&counts[key], 1);
+    const int i = ij.x, j = ij.y;
+    if (!(i >= 0 && j < n_orb && i <= j)) { atomicOr(err, kErrBadPair); continue; }
+    const int bi = i / bsize, bj = j / bsize;
+    const int slot = slot_of_bp[bi * nb + bj];
+    const int I0 = bi * bsize, J0 = bj * bsize;
+    const int si = min(bsize, n_orb - I0), sj = min(bsize, n_orb - J0);
+    int t, c;
+    if (bi != bj) {
+      t = (i - I0) * sj + (j - J0);
+      c = t >> 1;
+    } else if (i != j) {
+      const int a = i - I0, b = j - I0;  // a < b
+      t = a * si - a * (a + 1) / 2 + (b - a - 1);
+      c = t >> 1;
     } else {
-      atomicOr(err, kErrBadPair);
+      const int noff = si * (si - 1) / 2;
+      t = i - I0;
+      c = (noff + 1) / 2 + (t >> 1);
     }
-    keys[p] = key;
-  }
-}
-
-// one block: clamp counts to capacity, couples per key (ceil(count/2)), exclusive scan,
-// couple ranges per slot and per batch
-__global__ void __launch_bounds__(1024) k_plan_scan(int nslots, const int2* __restrict__ slot_blocks, int bsize, int n_orb,
-                                                    int* __restrict__ counts, int* __restrict__ couple_base, int nbatches,
-                                                    const int* __restrict__ batch_slot_begin, int* __restrict__ batch_begin,
-                                                    int* __restrict__ slot_begin, int* __restrict__ err) {
-  __shared__ int wsum[32];
-  const int nkeys = 2 * nslots;
-  const int per = (nkeys + blockDim.x - 1) / blockDim.x;
-  const int k0 = min(nkeys, (int)threadIdx.x * per), k1 = min(nkeys, k0 + per);
-  int local = 0;
-  for (int k = k0; k < k1; ++k) {
-    const int2 bp = slot_blocks[k >> 1];
-    const int si = min(bsize, n_orb - bp.x * bsize), sj = min(bsize, n_orb - bp.y * bsize);
-    int cap;
-    if (bp.x != bp.y) cap = (k & 1) ? 0 : si * sj;
-    else cap = (k & 1) ? si : si * (si - 1) / 2;
-    int cnt = counts[k];
-    if (cnt > cap) { cnt = cap; atomicOr(err, kErrBadPair); }
-    counts[k] = cnt;
-    local += (cnt + 1) >> 1;
-  }
-  // block exclusive scan of `local`
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) wsum[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    int s = (lane < nw) ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += t;
-    }
-    if (lane < nw) wsum[lane] = s;  // inclusive warp totals
-  }
-  __syncthreads();
-  int run = incl - local + (w > 0 ? wsum[w - 1] : 0);
-  for (int k = k0; k < k1; ++k) {
-    couple_base[k] = run;
-    run += (counts[k] + 1) >> 1;
-  }
-  if (threadIdx.x == blockDim.x - 1) couple_base[nkeys] = run;
-  __syncthreads();
-  for (int s = threadIdx.x; s <= nslots; s += blockDim.x) slot_begin[s] = couple_base[2 * s];
-  for (int b = threadIdx.x; b <= nbatches; b += blockDim.x) batch_begin[b] = couple_base[2 * batch_slot_begin[b]];
-}
-
-// one warp: stable placement of every valid pair into its bucket; pair number t of a bucket
-// becomes half (t & 1) of couple couple_base[key] + t/2.
-__global__ void __launch_bounds__(32) k_plan_scatter(const int2* __restrict__ pairs, long long P,
-                                                     const int* __restrict__ keys, const int* __restrict__ counts,
-                                                     const int* __restrict__ couple_base, int nkeys, int use_smem,
-                                                     int* __restrict__ gcursor, int4* __restrict__ couples) {
-  extern __shared__ int scur[];
-  int* cur = use_smem ? scur : gcursor;
-  const int lane = threadIdx.x;
-  for (int k = lane; k < nkeys; k += 32) cur[k] = 0;
-  __syncwarp();
-  const unsigned lt = (1u << lane) - 1u;
-  for (long long base = 0; base < P; base += 32) {
-    const long long p = base + lane;
-    const int key = (p < P) ? keys[p] : -1;
-    const unsigned same = __match_any_sync(0xffffffffu, key);
-    const int rank = __popc(same & lt);
-    const int leader = __ffs(same) - 1;
-    int c = 0;
-    if (key >= 0) c = cur[key];
-    __syncwarp();
-    if (key >= 0 && lane == leader) cur[key] = c + __popc(same);
-    __syncwarp();
-    if (key >= 0) {
-      const int pos = c + rank;
-      if (pos < counts[key]) {
-        const int2 ij = pairs[p];
-        int* cp = reinterpret_cast<int*>(couples + couple_base[key] + (pos >> 1));
-        cp[(pos & 1) * 2] = ij.x;
-        cp[(pos & 1) * 2 + 1] = ij.y;
-      }
-    }
+    int* cp = reinterpret_cast<int*>(couples + slot_couple_base[slot] + c) + 2 * (t & 1);
+    if (atomicCAS(cp, -1, i) != -1) { atomicOr(err, kErrBadPair); continue; }
+    cp[1] = j;
   }
 }
 
 // one block: E_x = scale * sum_g w_g sum_y epart[g][y] (fixed order), stored or accumulated
 __global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__ epart, const int4* __restrict__ couples,
-                                                      const int* __restrict__ total_couples, int n2, double scale,
-                                                      int accumulate, double* __restrict__ ex) {
+                                                      int total, int n2, double scale, int accumulate,
+                                                      double* __restrict__ ex) {
   __shared__ double red[32];
-  const int total = *total_couples;
   double s = 0.0;
   for (int g = threadIdx.x; g < total; g += blockDim.x) {
     const int4 cp = couples[g];
+    if (couple_empty(cp)) continue;
+    // both halves of a couple share a weight class: diagonal pairs count once, others twice
+    const bool diag = cp.x >= 0 ? cp.x == cp.y : cp.z == cp.w;
     double t = 0.0;
     for (int y = 0; y < n2; ++y) t += epart[(long long)g * n2 + y];
-    s += (cp.x == cp.y ? 1.0 : 2.0) * t;
+    s += (diag ? 1.0 : 2.0) * t;
   }
-  const double tot = block_sum<double>(s, red);
+  const double tot = block_sum(s, red);
   if (threadIdx.x == 0) ex[0] = (accumulate ? ex[0] : 0.0) + scale * tot;
 }
 
@@ -632,34 +599,41 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
   using C = cx<T>;
   C* W = (C*)(ws + L.W);
   int4* couples = (int4*)(ws + L.couples);
-  int* batch_begin = (int*)(ws + L.batch_begin);
-  int* slot_begin = (int*)(ws + L.slot_begin);
   double* epart = (double*)(ws + L.epart);
   const Geo& g = c->geo;
   const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
   const double vscale = -c->alpha / (double)c->N;
   const int zc = zchunk(c);
   const int nzc = (g.n3 + zc - 1) / zc;
+  const int pts = g.n2 * zc;
+  const int dense_np = pts > 2 * kDenseMaxThreads ? 4 : 2;
+  const int dense_threads = std::min(kDenseMaxThreads, (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
   for (int b = 0; b < S.nbatches; ++b) {
     const int s0 = S.batch_slot_begin[b], s1 = S.batch_slot_begin[b + 1];
-    long long cap = 0;
-    for (int s = s0; s < s1; ++s) cap += S.slot_cap[s];
-    const long long items1 = cap * g.n1, items2 = cap * g.n2;
+    const int c0 = S.slot_couple_base[s0], c1 = S.slot_couple_base[s1];
+    const long long items1 = (long long)(c1 - c0) * g.n1, items2 = (long long)(c1 - c0) * g.n2;
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
     cudaEvent_t e0 = prof_mark(c, st);
-    Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, batch_begin, b, W, (const C*)c->d_tw[1],
+    Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
                       (const C*)c->d_tw[2]);
     prof_close(c, kProfFwd, e0, st);
     e0 = prof_mark(c, st);
-    Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, batch_begin, b, W, (const T*)c->d_vtab,
+    Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, couples, c0, c1, W, (const T*)c->d_vtab,
                          (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
     prof_close(c, kProfX, e0, st);
     if (!energy_only) {
-      dim3 grid3(nzc, g.n1, s1 - s0);
       e0 = prof_mark(c, st);
-      Passes<T>::y_inv_acc(g, grid3, smem_acc(c), st, orb, couples, batch_begin, b, slot_begin, S.d_slot_blocks, s0,
-                           S.b, n_orb, W, (const C*)c->d_tw[1], vxphi, vscale);
+      const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
+      const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
+      if (nd > 0)
+        Passes<T>::y_acc_dense(g, dim3(nzc, g.n1, nd), dense_threads, smem_dense(c), st, S.b, orb, couples,
+                               S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
+                               (const C*)c->d_tw[1], vxphi, vscale);
+      if (ng > 0)
+        Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
+                                 S.d_generic_slots + S.generic_begin[b], S.d_slot_couple_base, S.d_slot_blocks, S.b,
+                                 n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale);
       prof_close(c, kProfAcc, e0, st);
     }
   }
@@ -699,29 +673,16 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
   char* ws = (char*)c->ws;
   if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
 
-  // stage a1: pair list -> couples
-  const int nkeys = 2 * S->nslots;
-  int* keys = (int*)(ws + L.keys);
-  int* counts = (int*)(ws + L.counts);
-  int* couple_base = (int*)(ws + L.couple_base);
-  int* cursor = (int*)(ws + L.cursor);
-  int4* couples = (int4*)(ws + L.couples);
-  int* batch_begin = (int*)(ws + L.batch_begin);
-  int* slot_begin = (int*)(ws + L.slot_begin);
+  // stage a1: pair list -> couples in the canonical layout
   cudaEvent_t e_stage = prof_mark(c, st);
-  HFX_CUDA_TRY(cudaMemsetAsync(counts, 0, (size_t)nkeys * sizeof(int), st));
+  int4* couples = (int4*)(ws + L.couples);
   HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S->max_total_couples * sizeof(int4), st));
   {
     const int threads = 256;
-    const int blocks = (int)std::min<long long>((n_pairs + threads - 1) / threads, (long long)c->sm_count * 8);
-    k_plan_count<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S->b, S->nb, S->d_slot_of_bp, keys,
-                                             counts, c->d_err);
-    k_plan_scan<<<1, 1024, 0, st>>>(S->nslots, S->d_slot_blocks, S->b, n_orb, counts, couple_base, S->nbatches,
-                                    S->d_batch_slot_begin, batch_begin, slot_begin, c->d_err);
-    const size_t cur_bytes = (size_t)nkeys * sizeof(int);
-    const int use_smem = cur_bytes <= 48 * 1024 ? 1 : 0;
-    k_plan_scatter<<<1, 32, use_smem ? cur_bytes : 0, st>>>((const int2*)pairs, n_pairs, keys, counts, couple_base,
-                                                            nkeys, use_smem, cursor, couples);
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_pairs + threads - 1) / threads,
+                                                                        (long long)c->sm_count * 8));
+    k_plan_place<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S->b, S->nb, S->d_slot_of_bp,
+                                             S->d_slot_couple_base, couples, c->d_err);
   }
   HFX_CUDA_TRY(cudaGetLastError());
 
@@ -746,8 +707,8 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
   cudaEvent_t e_en = prof_mark(c, st);
-  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, couple_base + nkeys, c->grid[1], scale,
-                                    accumulate ? 1 : 0, ex_dev);
+  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S->max_total_couples, c->grid[1],
+                                    scale, accumulate ? 1 : 0, ex_dev);
   prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
@@ -797,7 +758,10 @@ extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_
   const bool eo = (flags & HFX_ENERGY_ONLY) != 0;
   long long launches = 0;
   if (n_pairs > 0) {
-    launches = 3 /* count, scan, scatter */ + 1 /* energy */ + (long long)S.nbatches * (eo ? 2 : 3);
+    launches = 1 /* placement */ + 1 /* energy */ + (long long)S.nbatches * 2;
+    if (!eo)
+      for (int b = 0; b < S.nbatches; ++b)
+        launches += (S.dense_begin[b + 1] > S.dense_begin[b]) + (S.generic_begin[b + 1] > S.generic_begin[b]);
     if (c->prec == HFX_PREC_FP32 && !(flags & HFX_ORBITALS_F32)) launches += 1; /* FP64 -> FP32 orbitals */
   } else if (!(flags & HFX_ACCUMULATE)) {
     launches = 1;

@@ -10,21 +10,23 @@ namespace hfx {
 
 template <typename T>
 struct Passes {
-  // opt the three pass kernels into `bytes` of dynamic shared memory
+  // opt the pass kernels into `bytes` of dynamic shared memory
   static cudaError_t set_smem_limit(int bytes);
   // resident blocks per SM of the two plane kernels at the given dynamic shared memory
   static cudaError_t occupancy(size_t smem_fwd, size_t smem_x, int* blocks_fwd, int* blocks_x);
+  // true when a dense accumulation kernel exists for orbital blocks of size b
+  static bool has_dense(int b);
 
-  static void fwd_yz(const Geo& g, int grid, size_t smem, cudaStream_t st, const T* orb,
-                     const int4* couples, const int* batch_begin, int batch, cx<T>* W,
-                     const cx<T>* tw2, const cx<T>* tw3);
-  static void x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t st, const int* batch_begin,
-                        int batch, cx<T>* W, const T* vtab, const cx<T>* tw1, const cx<T>* tw3,
-                        double* epart, int energy_only);
-  static void y_inv_acc(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const T* orb,
-                        const int4* couples, const int* batch_begin, int batch, const int* slot_begin,
-                        const int2* slot_blocks, int slot0, int bsize, int n_orb, const cx<T>* W,
-                        const cx<T>* tw2, double* V, double vscale);
+  static void fwd_yz(const Geo& g, int grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples, int c0,
+                     int c1, cx<T>* W, const cx<T>* tw2, const cx<T>* tw3);
+  static void x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                        cx<T>* W, const T* vtab, const cx<T>* tw1, const cx<T>* tw3, double* epart, int energy_only);
+  static void y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b, const T* orb,
+                          const int4* couples, const int* slot_list, const int* slot_couple_base,
+                          const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
+  static void y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples,
+                            const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int bsize,
+                            int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
 };
 
 }  // namespace hfx

@@ -1,18 +1,19 @@
-// Kernels of the exchange path.  One call runs, per batch of packed pair couples:
+// Kernels of the exchange path.  One call runs, per batch of packed pair couples (two real pair
+// densities per complex transform, Z = rho_a + i rho_b):
 //
-//   k_fwd_yz   (per couple, per x-plane)   Z = phi_a1 phi_a2 + i phi_b1 phi_b2, forward FFT
-//                                           along z then y in shared memory -> W
-//   k_x_coulomb(per couple, per y-plane)   forward FFT along x; v(G) multiply and the energy
-//                                           sum sum_G v |Z|^2 (FP64); inverse FFT along x,
-//                                           inverse FFT along z -> W
-//   k_y_inv_acc(per block pair, per x-plane, per z-chunk)
-//                                           inverse FFT along y of every couple of the block
-//                                           pair, V_a1 += v_a phi_a2, V_a2 += v_a phi_a1,
-//                                           ... accumulated on chip, then added to V_x phi (FP64)
+//   k_fwd_yz    (couple, x-plane)   Z = phi_a1 phi_a2 + i phi_b1 phi_b2; forward FFT along z
+//                                    and y in shared memory -> W
+//   k_x_coulomb (couple, y-plane)   forward FFT along x; v(G) multiply and the energy sum
+//                                    sum_G v |Z|^2 (FP64); inverse FFT along x and z -> W
+//   k_y_acc_dense (off-diagonal block pair of full blocks, x-plane, z-chunk)
+//                                    inverse FFT along y of the block pair's couples one orbital
+//                                    row at a time; V_i and V_J accumulated in registers
+//   k_y_acc_generic (any other block pair, x-plane, z-chunk)
+//                                    the same with the accumulators in shared memory
 //
 // Transforms are in place: forward stages are decimation in frequency (natural order in,
-// digit-reversed out), inverse stages are decimation in time (digit-reversed in, natural out),
-// so no reordering pass exists; v(G) is tabulated in the digit-reversed storage order.
+// digit-reversed out), inverse stages decimation in time (digit-reversed in, natural out), so no
+// reordering pass exists; v(G) is tabulated in the digit-reversed storage order.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,16 +24,39 @@ namespace hfx {
 
 constexpr int kMaxStages = 8;
 
+// Division by a fixed divisor d < 2^16 for dividends x < 2^16: q = floor(x * ceil(2^32/d) / 2^32).
+// The product's error is below x / 2^32 < 2^-16 < 1/d, so the floor is exact.
+struct FastDiv {
+  uint32_t d, M;
+  static FastDiv make(uint32_t d_) {
+    FastDiv f;
+    f.d = d_;
+    f.M = d_ > 1 ? 0xFFFFFFFFu / d_ + 1u : 0u;
+    return f;
+  }
+  __device__ __forceinline__ int div(int x) const { return d == 1 ? x : (int)__umulhi((uint32_t)x, M); }
+};
+
+__device__ __forceinline__ FastDiv fastdiv_dev(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.M = d > 1 ? 0xFFFFFFFFu / d + 1u : 0u;
+  return f;
+}
+
 struct DimPlan {
-  int n;                 // length
-  int ns;                // number of stages
-  int r[kMaxStages];     // radix of stage s (stage 0 first in the forward transform)
-  int m[kMaxStages];     // sub-length after stage s: m[s] = n / (r[0] ... r[s]); m[ns-1] = 1
+  int n;                    // length
+  int ns;                   // number of stages
+  int r[kMaxStages];        // radix of stage s (stage 0 first in the forward transform)
+  int m[kMaxStages];        // sub-length after stage s: m[s] = n / (r[0] ... r[s]); m[ns-1] = 1
+  FastDiv mdiv[kMaxStages];
+  FastDiv ndiv;             // division by n (lines of this length in a plane)
 };
 
 struct Geo {
   int n1, n2, n3;
-  long long N;           // n1 n2 n3
+  long long N;              // n1 n2 n3
+  int S;                    // padded shared-memory row stride of the planes: n3 + 1 (odd)
   DimPlan d[3];
 };
 
@@ -41,32 +65,35 @@ constexpr int kErrBadPair = 1;
 constexpr int kErrTimeout = 2;
 
 constexpr int kThreadsPlane = 256;  // k_fwd_yz / k_x_coulomb
-constexpr int kThreadsAcc = 128;    // k_y_inv_acc
+constexpr int kThreadsAcc = 128;    // k_y_acc_generic
 
 template <typename T> struct ZChunk;
 template <> struct ZChunk<float> { static constexpr int value = 8; };   // 64-byte rows
 template <> struct ZChunk<double> { static constexpr int value = 4; };  // 64-byte rows
 
+__device__ __forceinline__ bool couple_empty(int4 cp) { return cp.x < 0 && cp.z < 0; }
+
 // ----------------------------------------------------------------------------------
 // one in-place radix-R stage over `lines` lines of length n held in shared memory.
 // Element e of line l lives at buf[l*ls + e*es].  Butterfly q in [0, n/R): j1 = q mod m,
 // elements (q - j1) R + j1 + k m, k < R.  Forward (DIF): DFT then twiddle w_L^{j1 k};
-// inverse (DIT): conj twiddle then inverse DFT.  L = R m.  LINE_FAST maps consecutive
-// threads to consecutive lines (column lines), else to consecutive butterflies of a line.
+// inverse (DIT): conj twiddle then inverse DFT (L = R m).  Consecutive threads take the same
+// butterfly of consecutive lines, so twiddle reads are broadcasts and, with an odd or unit
+// line stride, the data accesses hit distinct banks.
 // ----------------------------------------------------------------------------------
-template <int R, bool INV, bool LINE_FAST, typename C>
+template <int R, bool INV, typename C>
 __device__ __forceinline__ void fft_stage(C* __restrict__ buf, const C* __restrict__ tw, int lines,
-                                          int n, int m, int ls, int es) {
+                                          FastDiv ldiv, int n, int m, FastDiv mdiv, int ls, int es) {
   const int nq = n / R;
   const int total = lines * nq;
   const int tstride = n / (R * m);
+  const int step = m * es;
   for (int id = threadIdx.x; id < total; id += blockDim.x) {
-    int line, q;
-    if (LINE_FAST) { line = id % lines; q = id / lines; }
-    else { q = id % nq; line = id / nq; }
-    const int j1 = q % m;
-    const int base = line * ls + ((q - j1) * R + j1) * es;
-    const int step = m * es;
+    const int q = ldiv.div(id);
+    const int line = id - q * lines;
+    const int blk = mdiv.div(q);
+    const int j1 = q - blk * m;
+    const int base = line * ls + (blk * R * m + j1) * es;
     C v[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) v[k] = buf[base + k * step];
@@ -88,63 +115,43 @@ __device__ __forceinline__ void fft_stage(C* __restrict__ buf, const C* __restri
   }
 }
 
-template <bool INV, bool LINE_FAST, typename C>
-__device__ __forceinline__ void fft_stage_rt(int R, C* buf, const C* tw, int lines, int n, int m,
-                                             int ls, int es) {
+template <bool INV, typename C>
+__device__ __forceinline__ void fft_stage_rt(int R, C* buf, const C* tw, int lines, FastDiv ldiv, int n, int m,
+                                             FastDiv mdiv, int ls, int es) {
   switch (R) {
-    case 2: fft_stage<2, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 3: fft_stage<3, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 4: fft_stage<4, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 5: fft_stage<5, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 6: fft_stage<6, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 8: fft_stage<8, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 9: fft_stage<9, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 10: fft_stage<10, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 12: fft_stage<12, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
-    case 16: fft_stage<16, INV, LINE_FAST>(buf, tw, lines, n, m, ls, es); break;
+    case 2: fft_stage<2, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 3: fft_stage<3, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 4: fft_stage<4, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 5: fft_stage<5, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 6: fft_stage<6, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 8: fft_stage<8, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 9: fft_stage<9, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 10: fft_stage<10, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 12: fft_stage<12, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
+    case 16: fft_stage<16, INV>(buf, tw, lines, ldiv, n, m, mdiv, ls, es); break;
     default: break;
   }
 }
 
-// all forward stages [s_begin, s_end) of one dimension; a barrier after each
-template <bool LINE_FAST, typename C>
-__device__ __forceinline__ void fft_forward(const DimPlan& d, int s_begin, int s_end, C* buf, const C* tw,
-                                            int lines, int ls, int es) {
+// forward stages [s_begin, s_end) of one dimension, a barrier after each
+template <typename C>
+__device__ __forceinline__ void fft_forward(const DimPlan& d, int s_begin, int s_end, C* buf, const C* tw, int lines,
+                                            FastDiv ldiv, int ls, int es) {
   for (int s = s_begin; s < s_end; ++s) {
-    fft_stage_rt<false, LINE_FAST>(d.r[s], buf, tw, lines, d.n, d.m[s], ls, es);
+    fft_stage_rt<false>(d.r[s], buf, tw, lines, ldiv, d.n, d.m[s], d.mdiv[s], ls, es);
     __syncthreads();
   }
 }
-// inverse stages s = s_hi-1 down to s_lo; a barrier after each
-template <bool LINE_FAST, typename C>
-__device__ __forceinline__ void fft_inverse(const DimPlan& d, int s_lo, int s_hi, C* buf, const C* tw,
-                                            int lines, int ls, int es) {
+// inverse stages s = s_hi-1 down to s_lo, a barrier after each
+template <typename C>
+__device__ __forceinline__ void fft_inverse(const DimPlan& d, int s_lo, int s_hi, C* buf, const C* tw, int lines,
+                                            FastDiv ldiv, int ls, int es) {
   for (int s = s_hi - 1; s >= s_lo; --s) {
-    fft_stage_rt<true, LINE_FAST>(d.r[s], buf, tw, lines, d.n, d.m[s], ls, es);
+    fft_stage_rt<true>(d.r[s], buf, tw, lines, ldiv, d.n, d.m[s], d.mdiv[s], ls, es);
     __syncthreads();
   }
 }
 
-// ----------------------------------------------------------------------------------
-// vectorised copies between global and shared memory (16-byte units)
-// ----------------------------------------------------------------------------------
-template <typename C>
-__device__ __forceinline__ void copy_g2s(C* __restrict__ dst, const C* __restrict__ src, int count) {
-  // count complex values, both 16-byte aligned, count * sizeof(C) multiple of 16
-  const int4* s = reinterpret_cast<const int4*>(src);
-  int4* d = reinterpret_cast<int4*>(dst);
-  const int nv = count * int(sizeof(C)) / 16;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) d[i] = __ldg(s + i);
-}
-template <typename C>
-__device__ __forceinline__ void copy_s2g(C* __restrict__ dst, const C* __restrict__ src, int count) {
-  const int4* s = reinterpret_cast<const int4*>(src);
-  int4* d = reinterpret_cast<int4*>(dst);
-  const int nv = count * int(sizeof(C)) / 16;
-  for (int i = threadIdx.x; i < nv; i += blockDim.x) d[i] = s[i];
-}
-
-template <typename T>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   // deterministic tree: warp shuffles, then warp 0 over the warp partials
 #pragma unroll
@@ -163,71 +170,110 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;  // valid in thread 0
 }
 
+// 16-byte vectors of complex values: two float2 or one double2
+template <typename C> struct Vec16;
+template <> struct Vec16<float2> {
+  using type = float4;
+  static constexpr int per = 2;
+  static __device__ __forceinline__ void split(const float4& v, float2 (&c)[2]) {
+    c[0] = make_float2(v.x, v.y);
+    c[1] = make_float2(v.z, v.w);
+  }
+  static __device__ __forceinline__ float4 join(const float2 (&c)[2]) { return make_float4(c[0].x, c[0].y, c[1].x, c[1].y); }
+};
+template <> struct Vec16<double2> {
+  using type = double2;
+  static constexpr int per = 1;
+  static __device__ __forceinline__ void split(const double2& v, double2 (&c)[1]) { c[0] = v; }
+  static __device__ __forceinline__ double2 join(const double2 (&c)[1]) { return c[0]; }
+};
+
+// copy rows of n3 complex values from global (row stride gstride) into a padded shared plane
+// (row stride S) and back; 16-byte global accesses.
+template <typename C>
+__device__ __forceinline__ void rows_g2s(C* __restrict__ buf, int S, const C* __restrict__ src, long long gstride,
+                                         int rows, int n3) {
+  using VT = Vec16<C>;
+  constexpr int PER = VT::per;
+  const int vpr = n3 / PER;
+  for (int i = threadIdx.x; i < rows * vpr; i += blockDim.x) {
+    const int r = i / vpr, v = i - r * vpr;
+    C c[PER];
+    VT::split(__ldg(reinterpret_cast<const typename VT::type*>(src + r * gstride) + v), c);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) buf[r * S + v * PER + k] = c[k];
+  }
+}
+template <typename C>
+__device__ __forceinline__ void rows_s2g(C* __restrict__ dst, long long gstride, const C* __restrict__ buf, int S,
+                                         int rows, int n3) {
+  using VT = Vec16<C>;
+  constexpr int PER = VT::per;
+  const int vpr = n3 / PER;
+  for (int i = threadIdx.x; i < rows * vpr; i += blockDim.x) {
+    const int r = i / vpr, v = i - r * vpr;
+    C c[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) c[k] = buf[r * S + v * PER + k];
+    reinterpret_cast<typename VT::type*>(dst + r * gstride)[v] = VT::join(c);
+  }
+}
+
 // ----------------------------------------------------------------------------------
 // pass 1: pair product + forward FFT along z and y of one x-plane
 // ----------------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreadsPlane)
-k_fwd_yz(Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
-         const int* __restrict__ batch_begin, int batch, cx<T>* __restrict__ W,
+k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W,
          const cx<T>* __restrict__ tw2g, const cx<T>* __restrict__ tw3g) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
   const int plane = n2 * n3;
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw2 = buf + plane;
+  C* tw2 = buf + n2 * S;
   C* tw3 = tw2 + n2;
   for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
 
-  const int c0 = batch_begin[batch], c1 = batch_begin[batch + 1];
   const long long items = (long long)(c1 - c0) * n1;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const int cl = int(it / n1);
     const int x = int(it - (long long)cl * n1);
     const int4 cp = couples[c0 + cl];
+    if (couple_empty(cp)) continue;
     const long long off = (long long)x * plane;
-    const T* pa1 = orb + (long long)cp.x * g.N + off;
-    const T* pa2 = orb + (long long)cp.y * g.N + off;
-    const bool hasb = cp.z >= 0;
+    const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+    const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * g.N + off;
+    const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * g.N + off;
     const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * g.N + off;
     const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
-    __syncthreads();  // previous item's store has finished reading buf
-    if constexpr (sizeof(T) == 4) {
-      const int nv = plane / 4;
-      for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        float4 a1 = __ldg(reinterpret_cast<const float4*>(pa1) + i);
-        float4 a2 = __ldg(reinterpret_cast<const float4*>(pa2) + i);
-        float4 b1 = make_float4(0.f, 0.f, 0.f, 0.f), b2 = b1;
-        if (hasb) {
-          b1 = __ldg(reinterpret_cast<const float4*>(pb1) + i);
-          b2 = __ldg(reinterpret_cast<const float4*>(pb2) + i);
-        }
-        float4* d = reinterpret_cast<float4*>(buf + 4 * i);
-        d[0] = make_float4(a1.x * a2.x, b1.x * b2.x, a1.y * a2.y, b1.y * b2.y);
-        d[1] = make_float4(a1.z * a2.z, b1.z * b2.z, a1.w * a2.w, b1.w * b2.w);
-      }
-    } else {
-      const int nv = plane / 2;
-      for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-        double2 a1 = __ldg(reinterpret_cast<const double2*>(pa1) + i);
-        double2 a2 = __ldg(reinterpret_cast<const double2*>(pa2) + i);
-        double2 b1 = make_double2(0.0, 0.0), b2 = b1;
-        if (hasb) {
-          b1 = __ldg(reinterpret_cast<const double2*>(pb1) + i);
-          b2 = __ldg(reinterpret_cast<const double2*>(pb2) + i);
-        }
-        buf[2 * i] = make_double2(a1.x * a2.x, b1.x * b2.x);
-        buf[2 * i + 1] = make_double2(a1.y * a2.y, b1.y * b2.y);
+    __syncthreads();  // previous item's store has finished reading buf (and tables are loaded)
+    constexpr int V = 16 / int(sizeof(T));  // reals per 16-byte load
+    using LV = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const int nv = plane / V;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      LV a1 = {}, a2 = {}, b1 = {}, b2 = {};
+      if (hasa) { a1 = __ldg(reinterpret_cast<const LV*>(pa1) + i); a2 = __ldg(reinterpret_cast<const LV*>(pa2) + i); }
+      if (hasb) { b1 = __ldg(reinterpret_cast<const LV*>(pb1) + i); b2 = __ldg(reinterpret_cast<const LV*>(pb2) + i); }
+      const T* fa1 = reinterpret_cast<const T*>(&a1);
+      const T* fa2 = reinterpret_cast<const T*>(&a2);
+      const T* fb1 = reinterpret_cast<const T*>(&b1);
+      const T* fb2 = reinterpret_cast<const T*>(&b2);
+      const int p0 = i * V;
+      int y = p0 / n3, z = p0 - y * n3;  // a vector may straddle two rows when n3 % V != 0
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        if (z == n3) { z = 0; ++y; }
+        buf[y * S + z] = mk<C>(fa1[k] * fa2[k], fb1[k] * fb2[k]);
+        ++z;
       }
     }
     __syncthreads();
-    // z: n2 rows of length n3 (contiguous), butterflies of a row on consecutive threads
-    fft_forward<false>(g.d[2], 0, g.d[2].ns, buf, tw3, n2, n3, 1);
-    // y: n3 columns of length n2 (stride n3), consecutive threads on consecutive columns
-    fft_forward<true>(g.d[1], 0, g.d[1].ns, buf, tw2, n3, 1, n3);
-    copy_s2g(W + ((long long)cl * n1 + x) * plane, buf, plane);
+    // z: n2 rows (stride S) of length n3; y: n3 columns (stride 1) of length n2 (element stride S)
+    fft_forward(g.d[2], 0, g.d[2].ns, buf, tw3, n2, g.d[1].ndiv, S, 1);
+    fft_forward(g.d[1], 0, g.d[1].ns, buf, tw2, n3, g.d[2].ndiv, 1, S);
+    rows_s2g(W + ((long long)cl * n1 + x) * plane, n3, buf, S, n2, n3);
   }
 }
 
@@ -235,22 +281,23 @@ k_fwd_yz(Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
 // pass 2: forward FFT along x, Coulomb multiply + energy, inverse along x and z
 // ----------------------------------------------------------------------------------
 template <int R, typename C, typename T>
-__device__ __forceinline__ void x_last_coulomb(C* __restrict__ buf, int n1, int n3, const T* __restrict__ vy,
-                                               long long vstride_x, bool energy_only, double& e_acc) {
+__device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int n1, int n3, FastDiv zdiv,
+                                                 const T* __restrict__ vy, long long vstride_x, bool energy_only) {
+  double e_acc = 0.0;
   // last forward stage of x (m = 1: no twiddles) fused with the first inverse stage (also m = 1)
-  const int nq = n1 / R;
-  const int total = n3 * nq;
+  const int total = n3 * (n1 / R);
   for (int id = threadIdx.x; id < total; id += blockDim.x) {
-    const int z = id % n3, q = id / n3;
-    const int base = q * R * n3 + z;
+    const int q = zdiv.div(id);
+    const int z = id - q * n3;
+    const int base = q * R * S + z;
     C v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = buf[base + k * n3];
+    for (int k = 0; k < R; ++k) v[k] = buf[base + k * S];
     Dft<R, -1, C>::run(v);
     T e = T(0);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const T vg = vy[(long long)(q * R + k) * vstride_x + z];
+      const T vg = __ldg(vy + (long long)(q * R + k) * vstride_x + z);
       e += vg * (v[k].x * v[k].x + v[k].y * v[k].y);
       v[k].x *= vg;
       v[k].y *= vg;
@@ -259,164 +306,262 @@ __device__ __forceinline__ void x_last_coulomb(C* __restrict__ buf, int n1, int 
     if (!energy_only) {
       Dft<R, 1, C>::run(v);
 #pragma unroll
-      for (int k = 0; k < R; ++k) buf[base + k * n3] = v[k];
+      for (int k = 0; k < R; ++k) buf[base + k * S] = v[k];
     }
   }
+  return e_acc;
 }
 
 template <typename C, typename T>
-__device__ __forceinline__ void x_last_coulomb_rt(int R, C* buf, int n1, int n3, const T* vy, long long vsx,
-                                                  bool eo, double& e) {
+__device__ __forceinline__ double x_last_coulomb_rt(int R, C* buf, int S, int n1, int n3, FastDiv zdiv, const T* vy,
+                                                    long long vsx, bool eo) {
   switch (R) {
-    case 2: x_last_coulomb<2>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 3: x_last_coulomb<3>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 4: x_last_coulomb<4>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 5: x_last_coulomb<5>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 6: x_last_coulomb<6>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 8: x_last_coulomb<8>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 9: x_last_coulomb<9>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 10: x_last_coulomb<10>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 12: x_last_coulomb<12>(buf, n1, n3, vy, vsx, eo, e); break;
-    case 16: x_last_coulomb<16>(buf, n1, n3, vy, vsx, eo, e); break;
-    default: break;
+    case 2: return x_last_coulomb<2>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 3: return x_last_coulomb<3>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 4: return x_last_coulomb<4>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 5: return x_last_coulomb<5>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 6: return x_last_coulomb<6>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 8: return x_last_coulomb<8>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 9: return x_last_coulomb<9>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 10: return x_last_coulomb<10>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 12: return x_last_coulomb<12>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    case 16: return x_last_coulomb<16>(buf, S, n1, n3, zdiv, vy, vsx, eo);
+    default: return 0.0;
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsPlane)
-k_x_coulomb(Geo g, const int* __restrict__ batch_begin, int batch, cx<T>* __restrict__ W,
-            const T* __restrict__ vtab, const cx<T>* __restrict__ tw1g, const cx<T>* __restrict__ tw3g,
-            double* __restrict__ epart, int energy_only) {
+k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
+            const cx<T>* __restrict__ tw1g, const cx<T>* __restrict__ tw3g, double* __restrict__ epart,
+            int energy_only) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
-  const int tile = n1 * n3;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw1 = buf + tile;
+  C* tw1 = buf + n1 * S;
   C* tw3 = tw1 + n1;
   __shared__ double red[32];
   for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = tw1g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
 
-  const int c0 = batch_begin[batch], c1 = batch_begin[batch + 1];
   const long long items = (long long)(c1 - c0) * n2;
   const long long plane = (long long)n2 * n3;
   for (long long it = blockIdx.x; it < items; it += gridDim.x) {
     const int cl = int(it / n2);
     const int y = int(it - (long long)cl * n2);
+    if (couple_empty(couples[c0 + cl])) continue;
     C* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
     __syncthreads();
-    // rows x of the tile: W[cl][x][y][:], n3 contiguous complex values each
-    const int vpr = n3 * int(sizeof(C)) / 16;
-    for (int i = threadIdx.x; i < n1 * vpr; i += blockDim.x) {
-      const int xx = i / vpr, vv = i - xx * vpr;
-      reinterpret_cast<int4*>(buf + xx * n3)[vv] = reinterpret_cast<const int4*>(wc + xx * plane)[vv];
-    }
+    rows_g2s(buf, S, wc, plane, n1, n3);  // rows x: W[cl][x][y][:]
     __syncthreads();
     const DimPlan& dx = g.d[0];
-    fft_forward<true>(dx, 0, dx.ns - 1, buf, tw1, n3, 1, n3);
-    double e = 0.0;
-    x_last_coulomb_rt(dx.r[dx.ns - 1], buf, n1, n3, vtab + (long long)y * n3, plane, energy_only != 0, e);
-    const double es = block_sum<T>(e, red);
+    // x: n3 columns of length n1 (element stride S)
+    fft_forward(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
+    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vtab + (long long)y * n3, plane,
+                                       energy_only != 0);
+    const double es = block_sum(e, red);
     if (threadIdx.x == 0) epart[(long long)(c0 + cl) * n2 + y] = es;
     if (energy_only) continue;
     __syncthreads();
-    fft_inverse<true>(dx, 0, dx.ns - 1, buf, tw1, n3, 1, n3);
-    fft_inverse<false>(g.d[2], 0, g.d[2].ns, buf, tw3, n1, n3, 1);
-    for (int i = threadIdx.x; i < n1 * vpr; i += blockDim.x) {
-      const int xx = i / vpr, vv = i - xx * vpr;
-      reinterpret_cast<int4*>(wc + xx * plane)[vv] = reinterpret_cast<const int4*>(buf + xx * n3)[vv];
+    fft_inverse(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
+    fft_inverse(g.d[2], 0, g.d[2].ns, buf, tw3, n1, g.d[0].ndiv, S, 1);  // z: n1 rows
+    rows_s2g(wc, plane, buf, S, n1, n3);
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// pass 3a: off-diagonal block pair (I, J) of two full blocks of B orbitals.  Couples sit in
+// canonical order: couple c holds pairs (I0 + c / (B/2), J0 + 2 (c mod B/2)) and (.., +1).
+// For each orbital row i the B/2 couples of the row are inverse-transformed along y together;
+// then every thread, for its own points, forms V_i = sum_j v_ij phi_j (added to V_x phi in FP64)
+// and accumulates V_j += v_ij phi_i in registers, flushed once at the end.
+// ----------------------------------------------------------------------------------
+constexpr int kDenseMaxThreads = 512;
+
+template <typename T, int B, int NP>
+__global__ void __launch_bounds__(kDenseMaxThreads, 1)
+k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, const int* __restrict__ slot_list,
+              const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
+              const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale) {
+  using C = cx<T>;
+  constexpr int ZC = ZChunk<T>::value;
+  constexpr int HB = B / 2;
+  constexpr int LN = HB * ZC;  // lines of the interleaved tile [y][t][zz]
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  const int z0 = blockIdx.x * ZC;
+  const int zcn = min(ZC, n3 - z0);
+  const int x = blockIdx.y;
+  const int slot = slot_list[blockIdx.z];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw2 = buf + n2 * LN;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
+
+  const int2 blk = slot_blocks[slot];
+  const int I0 = blk.x * B, J0 = blk.y * B;
+  const int cs = slot_couple_base[slot];
+  const long long plane = (long long)n2 * n3;
+  const long long rowoff = (long long)x * plane + z0;
+  const int pts = n2 * ZC;
+
+  // this thread's points
+  long long goff[NP];
+  bool ok[NP];
+  int sp[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int p = threadIdx.x + k * blockDim.x;
+    const int y = p / ZC, zz = p - (p / ZC) * ZC;
+    ok[k] = p < pts && zz < zcn;
+    sp[k] = y * LN + zz;  // + t * ZC for couple t
+    goff[k] = rowoff + (long long)y * n3 + zz;
+  }
+  T phiJ[NP][B], accJ[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      phiJ[k][j] = ok[k] ? __ldg(orb + (long long)(J0 + j) * g.N + goff[k]) : T(0);
+      accJ[k][j] = T(0);
+    }
+
+  const FastDiv ldiv = fastdiv_dev(LN);
+  constexpr int PER = 16 / int(sizeof(C));
+  for (int r = 0; r < B; ++r) {
+    __syncthreads();  // previous row's point pass done with buf
+    // load the row's HB couple tiles: rows of ZC complex at W[c][x][y][z0..]
+    for (int i = threadIdx.x; i < HB * n2 * (ZC / PER); i += blockDim.x) {
+      const int v = i % (ZC / PER);
+      const int rest = i / (ZC / PER);
+      const int t = rest % HB, y = rest / HB;
+      const int c = cs + r * HB + t;
+      int4 val = make_int4(0, 0, 0, 0);
+      if (!couple_empty(couples[c]) && v * PER < zcn)
+        val = __ldg(reinterpret_cast<const int4*>(W + ((long long)(c - c0) * n1 + x) * plane + (long long)y * n3 + z0) + v);
+      reinterpret_cast<int4*>(buf + y * LN + t * ZC)[v] = val;
+    }
+    __syncthreads();
+    fft_inverse(g.d[1], 0, g.d[1].ns, buf, tw2, LN, ldiv, 1, LN);
+    const int i_orb = I0 + r;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      if (!ok[k]) continue;
+      const T phii = __ldg(orb + (long long)i_orb * g.N + goff[k]);
+      T acci = T(0);
+#pragma unroll
+      for (int t = 0; t < HB; ++t) {
+        const C v = buf[sp[k] + t * ZC];
+        acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
+        accJ[k][2 * t] += v.x * phii;
+        accJ[k][2 * t + 1] += v.y * phii;
+      }
+      double* dst = V + (long long)i_orb * g.N + goff[k];
+      *dst += vscale * double(acci);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      double* dst = V + (long long)(J0 + j) * g.N + goff[k];
+      *dst += vscale * double(accJ[k][j]);
     }
   }
 }
 
 // ----------------------------------------------------------------------------------
-// pass 3: inverse FFT along y for every couple of one block pair on one (x, z-chunk) tile,
-// V_x phi accumulation on chip, one FP64 read-modify-write of V per block pair
+// pass 3b: any block pair (diagonal, ragged or with a block size without a dense kernel):
+// inverse FFT along y couple by couple on one (x, z-chunk) tile, accumulators in shared memory,
+// one FP64 read-modify-write of V per block pair
 // ----------------------------------------------------------------------------------
 struct AccCtx {
   int i0, ni;   // block I: orbitals [i0, i0 + ni)
   int j0, nj;   // block J (same as I for a diagonal block pair)
-  bool same;
-  __device__ __forceinline__ int local(int o) const { return (o - i0 < ni && o >= i0) ? o - i0 : ni + (o - j0); }
+  __device__ __forceinline__ int local(int o) const { return (o >= i0 && o - i0 < ni) ? o - i0 : ni + (o - j0); }
 };
 
 template <int R, typename C, typename T>
-__device__ __forceinline__ void y_last_acc(C* __restrict__ buf, const C* __restrict__ tw, int n2, int m, int zc,
+__device__ __forceinline__ void y_last_acc(C* __restrict__ buf, const C* __restrict__ tw, int m, FastDiv zcdiv,
                                            int zcn, T* __restrict__ acc, int tile_pts, const T* __restrict__ orb,
                                            long long N, long long rowoff, int n3, int4 cp, const AccCtx& ac) {
   // final inverse stage (stage 0: L = n2, one block, m = n2 / R), natural-order outputs
-  const int total = zcn * m;
-  const int la1 = ac.local(cp.x), la2 = ac.local(cp.y);
-  const bool hasb = cp.z >= 0;
+  constexpr int ZC = ZChunk<T>::value;
+  const int total = ZC * m;
+  const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+  const int la1 = hasa ? ac.local(cp.x) : 0, la2 = hasa ? ac.local(cp.y) : 0;
   const int lb1 = hasb ? ac.local(cp.z) : 0, lb2 = hasb ? ac.local(cp.w) : 0;
-  const T* pa1 = orb + (long long)cp.x * N + rowoff;
-  const T* pa2 = orb + (long long)cp.y * N + rowoff;
+  const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * N + rowoff;
+  const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * N + rowoff;
   const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * N + rowoff;
   const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * N + rowoff;
   const bool adiag = cp.x == cp.y, bdiag = cp.z == cp.w;
   for (int id = threadIdx.x; id < total; id += blockDim.x) {
-    const int zz = id % zcn, j1 = id / zcn;
+    const int j1 = zcdiv.div(id);
+    const int zz = id - j1 * ZC;
     C v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = buf[(j1 + k * m) * zc + zz];
+    for (int k = 0; k < R; ++k) v[k] = buf[(j1 + k * m) * ZC + zz];
     if (m > 1) {
 #pragma unroll
       for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[j1 * k]);
     }
     Dft<R, 1, C>::run(v);
+    if (zz >= zcn) continue;
 #pragma unroll
     for (int k = 0; k < R; ++k) {
       const int y = j1 + k * m;
-      const int p = y * zc + zz;
+      const int p = y * ZC + zz;
       const long long go = (long long)y * n3 + zz;
-      const T va = v[k].x, vb = v[k].y;
-      const T fa1 = __ldg(pa1 + go), fa2 = __ldg(pa2 + go);
-      acc[la1 * tile_pts + p] += va * fa2;
-      if (!adiag) acc[la2 * tile_pts + p] += va * fa1;
+      if (hasa) {
+        const T fa1 = __ldg(pa1 + go), fa2 = __ldg(pa2 + go);
+        acc[la1 * tile_pts + p] += v[k].x * fa2;
+        if (!adiag) acc[la2 * tile_pts + p] += v[k].x * fa1;
+      }
       if (hasb) {
         const T fb1 = __ldg(pb1 + go), fb2 = __ldg(pb2 + go);
-        acc[lb1 * tile_pts + p] += vb * fb2;
-        if (!bdiag) acc[lb2 * tile_pts + p] += vb * fb1;
+        acc[lb1 * tile_pts + p] += v[k].y * fb2;
+        if (!bdiag) acc[lb2 * tile_pts + p] += v[k].y * fb1;
       }
     }
   }
 }
 
 template <typename C, typename T>
-__device__ __forceinline__ void y_last_acc_rt(int R, C* buf, const C* tw, int n2, int m, int zc, int zcn, T* acc,
+__device__ __forceinline__ void y_last_acc_rt(int R, C* buf, const C* tw, int m, FastDiv zcdiv, int zcn, T* acc,
                                               int tp, const T* orb, long long N, long long ro, int n3, int4 cp,
                                               const AccCtx& ac) {
   switch (R) {
-    case 2: y_last_acc<2>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 3: y_last_acc<3>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 4: y_last_acc<4>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 5: y_last_acc<5>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 6: y_last_acc<6>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 8: y_last_acc<8>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 9: y_last_acc<9>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 10: y_last_acc<10>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 12: y_last_acc<12>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 16: y_last_acc<16>(buf, tw, n2, m, zc, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 2: y_last_acc<2>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 3: y_last_acc<3>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 4: y_last_acc<4>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 5: y_last_acc<5>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 6: y_last_acc<6>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 8: y_last_acc<8>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 9: y_last_acc<9>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 10: y_last_acc<10>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 12: y_last_acc<12>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
+    case 16: y_last_acc<16>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
     default: break;
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreadsAcc)
-k_y_inv_acc(Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
-            const int* __restrict__ batch_begin, int batch, const int* __restrict__ slot_begin,
-            const int2* __restrict__ slot_blocks, int slot0, int bsize, int n_orb,
-            const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g, double* __restrict__ V,
-            double vscale) {
+k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, const int* __restrict__ slot_list,
+                const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int bsize, int n_orb,
+                int c0, const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g, double* __restrict__ V,
+                double vscale) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
+  constexpr int PER = 16 / int(sizeof(C));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int z0 = blockIdx.x * ZC;
   const int zcn = min(ZC, n3 - z0);
   const int x = blockIdx.y;
-  const int slot = slot0 + blockIdx.z;
+  const int slot = slot_list[blockIdx.z];
   const int tile_pts = n2 * ZC;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw2 = buf + tile_pts;
@@ -426,40 +571,41 @@ k_y_inv_acc(Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
   AccCtx ac;
   ac.i0 = blk.x * bsize; ac.ni = min(bsize, n_orb - ac.i0);
   ac.j0 = blk.y * bsize; ac.nj = min(bsize, n_orb - ac.j0);
-  ac.same = blk.x == blk.y;
-  const int nloc = ac.same ? ac.ni : ac.ni + ac.nj;
+  const int nloc = (blk.x == blk.y) ? ac.ni : ac.ni + ac.nj;
 
   for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
   for (int i = threadIdx.x; i < nloc * tile_pts; i += blockDim.x) acc[i] = T(0);
 
-  const int cb0 = batch_begin[batch];
-  const int cs = slot_begin[slot], ce = slot_begin[slot + 1];
+  const int cs = slot_couple_base[slot], ce = slot_couple_base[slot + 1];
   const long long plane = (long long)n2 * n3;
   const long long rowoff = (long long)x * plane + z0;
   const DimPlan& dy = g.d[1];
+  const FastDiv zcdiv = fastdiv_dev(ZC);
   for (int c = cs; c < ce; ++c) {
     const int4 cp = couples[c];
-    const C* src = W + ((long long)(c - cb0) * n1 + x) * plane + z0;
-    __syncthreads();  // previous couple done with buf (and acc/tw init complete)
-    // tile [n2][ZC]: rows of zcn complex (zcn even, 16-byte multiples)
-    const int vpr = zcn * int(sizeof(C)) / 16;
-    for (int i = threadIdx.x; i < n2 * vpr; i += blockDim.x) {
-      const int yy = i / vpr, vv = i - yy * vpr;
-      reinterpret_cast<int4*>(buf + yy * ZC)[vv] = __ldg(reinterpret_cast<const int4*>(src + (long long)yy * n3) + vv);
+    if (couple_empty(cp)) continue;
+    const C* src = W + ((long long)(c - c0) * n1 + x) * plane + z0;
+    __syncthreads();  // previous couple done with buf (and init complete)
+    for (int i = threadIdx.x; i < n2 * (ZC / PER); i += blockDim.x) {
+      const int yy = i / (ZC / PER), vv = i - yy * (ZC / PER);
+      int4 val = make_int4(0, 0, 0, 0);
+      if (vv * PER < zcn) val = __ldg(reinterpret_cast<const int4*>(src + (long long)yy * n3) + vv);
+      reinterpret_cast<int4*>(buf + yy * ZC)[vv] = val;
     }
     __syncthreads();
-    fft_inverse<true>(dy, 1, dy.ns, buf, tw2, zcn, 1, ZC);
-    y_last_acc_rt(dy.r[0], buf, tw2, n2, dy.m[0], ZC, zcn, acc, tile_pts, orb, g.N, rowoff, n3, cp, ac);
+    fft_inverse(dy, 1, dy.ns, buf, tw2, ZC, zcdiv, 1, ZC);
+    y_last_acc_rt(dy.r[0], buf, tw2, dy.m[0], zcdiv, zcn, acc, tile_pts, orb, g.N, rowoff, n3, cp, ac);
   }
   __syncthreads();
   // flush: V[o][x][y][z0 + zz] += vscale * acc
-  for (int i = threadIdx.x; i < nloc * n2 * zcn; i += blockDim.x) {
-    const int lo = i / (n2 * zcn);
-    const int rem = i - lo * (n2 * zcn);
-    const int yy = rem / zcn, zz = rem - yy * zcn;
+  for (int i = threadIdx.x; i < nloc * tile_pts; i += blockDim.x) {
+    const int lo = i / tile_pts;
+    const int p = i - lo * tile_pts;
+    const int yy = p / ZC, zz = p - yy * ZC;
+    if (zz >= zcn) continue;
     const int o = (lo < ac.ni) ? ac.i0 + lo : ac.j0 + (lo - ac.ni);
     double* dst = V + (long long)o * g.N + rowoff + (long long)yy * n3 + zz;
-    *dst += vscale * double(acc[lo * tile_pts + yy * ZC + zz]);
+    *dst += vscale * double(acc[i]);
   }
 }
 

@@ -1,4 +1,4 @@
-// Launchers of the three passes for one real type `Real` (included by hfx_passes_f32.cu and
+// Launchers of the passes for one real type `Real` (included by hfx_passes_f32.cu and
 // hfx_passes_f64.cu, so the two precisions compile in parallel).
 #include "hfx_internal.h"
 
@@ -6,11 +6,17 @@ namespace hfx {
 
 template <>
 cudaError_t Passes<Real>::set_smem_limit(int bytes) {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_yz<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_x_coulomb<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_y_inv_acc<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const void* ks[] = {(const void*)k_fwd_yz<Real>,           (const void*)k_x_coulomb<Real>,
+                      (const void*)k_y_acc_dense<Real, 4, 2>, (const void*)k_y_acc_dense<Real, 4, 4>,
+                      (const void*)k_y_acc_dense<Real, 8, 2>, (const void*)k_y_acc_dense<Real, 8, 4>,
+                      (const void*)k_y_acc_generic<Real>};
+  for (const void* k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <>
@@ -21,27 +27,44 @@ cudaError_t Passes<Real>::occupancy(size_t smem_fwd, size_t smem_x, int* blocks_
 }
 
 template <>
-void Passes<Real>::fwd_yz(const Geo& g, int grid, size_t smem, cudaStream_t st, const Real* orb,
-                          const int4* couples, const int* batch_begin, int batch, cx<Real>* W,
-                          const cx<Real>* tw2, const cx<Real>* tw3) {
-  k_fwd_yz<Real><<<grid, kThreadsPlane, smem, st>>>(g, orb, couples, batch_begin, batch, W, tw2, tw3);
+bool Passes<Real>::has_dense(int b) { return b == 4 || b == 8; }
+
+template <>
+void Passes<Real>::fwd_yz(const Geo& g, int grid, size_t smem, cudaStream_t st, const Real* orb, const int4* couples,
+                          int c0, int c1, cx<Real>* W, const cx<Real>* tw2, const cx<Real>* tw3) {
+  k_fwd_yz<Real><<<grid, kThreadsPlane, smem, st>>>(g, orb, couples, c0, c1, W, tw2, tw3);
 }
 
 template <>
-void Passes<Real>::x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t st, const int* batch_begin,
-                             int batch, cx<Real>* W, const Real* vtab, const cx<Real>* tw1,
-                             const cx<Real>* tw3, double* epart, int energy_only) {
-  k_x_coulomb<Real><<<grid, kThreadsPlane, smem, st>>>(g, batch_begin, batch, W, vtab, tw1, tw3, epart,
-                                                       energy_only);
+void Passes<Real>::x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                             cx<Real>* W, const Real* vtab, const cx<Real>* tw1, const cx<Real>* tw3, double* epart,
+                             int energy_only) {
+  k_x_coulomb<Real><<<grid, kThreadsPlane, smem, st>>>(g, couples, c0, c1, W, vtab, tw1, tw3, epart, energy_only);
 }
 
 template <>
-void Passes<Real>::y_inv_acc(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const Real* orb,
-                             const int4* couples, const int* batch_begin, int batch, const int* slot_begin,
-                             const int2* slot_blocks, int slot0, int bsize, int n_orb, const cx<Real>* W,
-                             const cx<Real>* tw2, double* V, double vscale) {
-  k_y_inv_acc<Real><<<grid, kThreadsAcc, smem, st>>>(g, orb, couples, batch_begin, batch, slot_begin,
-                                                     slot_blocks, slot0, bsize, n_orb, W, tw2, V, vscale);
+void Passes<Real>::y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b,
+                               const Real* orb, const int4* couples, const int* slot_list, const int* slot_couple_base,
+                               const int2* slot_blocks, int c0, const cx<Real>* W, const cx<Real>* tw2, double* V,
+                               double vscale) {
+  // points per thread so that one block of at most kDenseMaxThreads threads covers the tile
+  const int pts = g.n2 * ZChunk<Real>::value;
+  const bool np4 = pts > 2 * kDenseMaxThreads;
+#define HFX_DENSE(BB, NPP)                                                                                      \
+  k_y_acc_dense<Real, BB, NPP><<<grid, threads, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks, \
+                                                            c0, W, tw2, V, vscale)
+  if (b == 8) { if (np4) HFX_DENSE(8, 4); else HFX_DENSE(8, 2); }
+  else { if (np4) HFX_DENSE(4, 4); else HFX_DENSE(4, 2); }
+#undef HFX_DENSE
+}
+
+template <>
+void Passes<Real>::y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const Real* orb,
+                                 const int4* couples, const int* slot_list, const int* slot_couple_base,
+                                 const int2* slot_blocks, int bsize, int n_orb, int c0, const cx<Real>* W,
+                                 const cx<Real>* tw2, double* V, double vscale) {
+  k_y_acc_generic<Real><<<grid, kThreadsAcc, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks,
+                                                        bsize, n_orb, c0, W, tw2, V, vscale);
 }
 
 template struct Passes<Real>;

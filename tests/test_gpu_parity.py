@@ -151,6 +151,40 @@ def test_empty_list_and_determinism():
     ex.close()
 
 
+def test_result_independent_of_pair_order():
+    """Pairs are placed canonically per block pair, so any ordering gives bit-identical results."""
+    from paper_2309_00651_gb300 import hfx
+    n, L, n_orb = 18, 9.0, 21
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=12)
+    pairs = I.all_pairs(n_orb)
+    ex = hfx.Exchange(lat, (n, n, n), precision="fp32")
+    phi_d = torch.from_numpy(phi).cuda()
+    Ea, Va = ex.apply(phi_d, torch.from_numpy(pairs).cuda())
+    perm = np.random.default_rng(13).permutation(len(pairs))
+    Eb, Vb = ex.apply(phi_d, torch.from_numpy(pairs[perm].copy()).cuda())
+    assert Ea.item() == Eb.item() and torch.equal(Va, Vb)
+    ex.close()
+
+
+def test_duplicate_pairs_are_reported_and_counted_once():
+    from paper_2309_00651_gb300 import hfx
+    n, L, n_orb = 16, 8.0, 10
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=14)
+    good = I.all_pairs(n_orb)
+    dup = np.concatenate([good, good[[3, 17, 40]]])
+    E_ref, V_ref = O.exchange(phi, good, lat)
+    ex = hfx.Exchange(lat, (n, n, n), precision="fp64")
+    E, V = ex.apply(torch.from_numpy(phi).cuda(), torch.from_numpy(dup).cuda())
+    with pytest.raises(hfx.HFXError) as ei:
+        ex.sync_status()
+    assert ei.value.status == -5
+    assert abs(E.item() - E_ref) <= 1e-8 * abs(E_ref)
+    assert rel(V.cpu().numpy(), V_ref) <= 1e-8
+    ex.close()
+
+
 def test_bad_pairs_are_reported_and_skipped():
     from paper_2309_00651_gb300 import hfx
     n, L, n_orb = 16, 8.0, 6
