@@ -503,8 +503,12 @@ static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
   auto it = c->sched.find(n_orb);
   if (it != c->sched.end()) { *out = it->second.get(); return HFX_OK; }
   std::unique_ptr<Schedule> S(new Schedule(make_host_schedule(c, n_orb)));
-  auto up = [&](void** dst, const void* src, size_t bytes) {
-    return upload(dst, src, std::max<size_t>(bytes, 4));
+  auto up = [&](void** dst, const void* src, size_t bytes) -> hfx_status {
+    if (bytes == 0) {  // an empty list still gets a valid (unused) device pointer
+      cudaError_t e = cudaMalloc(dst, 16);
+      return e == cudaSuccess ? HFX_OK : fail(HFX_ERR_OOM, "cudaMalloc(16) failed: %s", cudaGetErrorString(e));
+    }
+    return upload(dst, src, bytes);
   };
   hfx_status st = up((void**)&S->d_slot_blocks, S->slot_blocks.data(), S->slot_blocks.size() * sizeof(int2));
   if (st == HFX_OK) st = up((void**)&S->d_slot_of_bp, S->slot_of_bp.data(), S->slot_of_bp.size() * sizeof(int));
