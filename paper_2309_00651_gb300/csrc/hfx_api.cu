@@ -281,7 +281,8 @@ static size_t smem_fwd(const hfx_ctx* c) {
   return (size_t)(c->grid[1] * (c->grid[2] + 1) + c->grid[1] + c->grid[2]) * cplx_size(c);
 }
 static size_t smem_x(const hfx_ctx* c) {
-  return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c);
+  return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c) +
+         (size_t)c->grid[0] * c->grid[2] * real_size(c);
 }
 static size_t smem_acc(const hfx_ctx* c) {
   const int zc = zchunk(c);
@@ -289,7 +290,8 @@ static size_t smem_acc(const hfx_ctx* c) {
 }
 static size_t smem_dense(const hfx_ctx* c) {
   const int zc = zchunk(c);
-  return (size_t)(c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c);
+  return (size_t)(2 * c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c) +
+         (size_t)2 * c->bsize * c->grid[1] * zc * real_size(c);
 }
 static bool dense_available(const hfx_ctx* c) {
   return c->prec == HFX_PREC_FP64 ? Passes<double>::has_dense(c->bsize) : Passes<float>::has_dense(c->bsize);
@@ -610,8 +612,9 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
   const int zc = zchunk(c);
   const int nzc = (g.n3 + zc - 1) / zc;
   const int pts = g.n2 * zc;
-  const int dense_np = pts > 2 * kDenseMaxThreads ? 4 : 2;
-  const int dense_threads = std::min(kDenseMaxThreads, (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
+  const int dense_np = pts > 2 * DenseBounds<2>::threads ? 4 : 2;
+  const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
+                                     (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
   for (int b = 0; b < S.nbatches; ++b) {
     const int s0 = S.batch_slot_begin[b], s1 = S.batch_slot_begin[b + 1];
     const int c0 = S.slot_couple_base[s0], c1 = S.slot_couple_base[s1];

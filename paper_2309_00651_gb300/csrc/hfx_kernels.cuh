@@ -170,52 +170,24 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return r;  // valid in thread 0
 }
 
-// 16-byte vectors of complex values: two float2 or one double2
-template <typename C> struct Vec16;
-template <> struct Vec16<float2> {
-  using type = float4;
-  static constexpr int per = 2;
-  static __device__ __forceinline__ void split(const float4& v, float2 (&c)[2]) {
-    c[0] = make_float2(v.x, v.y);
-    c[1] = make_float2(v.z, v.w);
-  }
-  static __device__ __forceinline__ float4 join(const float2 (&c)[2]) { return make_float4(c[0].x, c[0].y, c[1].x, c[1].y); }
-};
-template <> struct Vec16<double2> {
-  using type = double2;
-  static constexpr int per = 1;
-  static __device__ __forceinline__ void split(const double2& v, double2 (&c)[1]) { c[0] = v; }
-  static __device__ __forceinline__ double2 join(const double2 (&c)[1]) { return c[0]; }
-};
-
-// copy rows of n3 complex values from global (row stride gstride) into a padded shared plane
-// (row stride S) and back; 16-byte global accesses.
+// plane copies, one complex value per thread step (consecutive threads on consecutive z: 8- or
+// 16-byte coalesced global accesses and conflict-free shared accesses into the padded rows)
 template <typename C>
-__device__ __forceinline__ void rows_g2s(C* __restrict__ buf, int S, const C* __restrict__ src, long long gstride,
-                                         int rows, int n3) {
-  using VT = Vec16<C>;
-  constexpr int PER = VT::per;
-  const int vpr = n3 / PER;
-  for (int i = threadIdx.x; i < rows * vpr; i += blockDim.x) {
-    const int r = i / vpr, v = i - r * vpr;
-    C c[PER];
-    VT::split(__ldg(reinterpret_cast<const typename VT::type*>(src + r * gstride) + v), c);
-#pragma unroll
-    for (int k = 0; k < PER; ++k) buf[r * S + v * PER + k] = c[k];
+__device__ __forceinline__ void plane_g2s(C* __restrict__ buf, int S, const C* __restrict__ src, long long gstride,
+                                          int rows, int n3, FastDiv n3div) {
+  const int total = rows * n3;
+  for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    const int r = n3div.div(p), z = p - r * n3;
+    buf[r * S + z] = __ldg(src + r * gstride + z);
   }
 }
 template <typename C>
-__device__ __forceinline__ void rows_s2g(C* __restrict__ dst, long long gstride, const C* __restrict__ buf, int S,
-                                         int rows, int n3) {
-  using VT = Vec16<C>;
-  constexpr int PER = VT::per;
-  const int vpr = n3 / PER;
-  for (int i = threadIdx.x; i < rows * vpr; i += blockDim.x) {
-    const int r = i / vpr, v = i - r * vpr;
-    C c[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) c[k] = buf[r * S + v * PER + k];
-    reinterpret_cast<typename VT::type*>(dst + r * gstride)[v] = VT::join(c);
+__device__ __forceinline__ void plane_s2g(C* __restrict__ dst, long long gstride, const C* __restrict__ buf, int S,
+                                          int rows, int n3, FastDiv n3div) {
+  const int total = rows * n3;
+  for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    const int r = n3div.div(p), z = p - r * n3;
+    dst[r * gstride + z] = buf[r * S + z];
   }
 }
 
@@ -249,31 +221,18 @@ k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* _
     const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * g.N + off;
     const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
     __syncthreads();  // previous item's store has finished reading buf (and tables are loaded)
-    constexpr int V = 16 / int(sizeof(T));  // reals per 16-byte load
-    using LV = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-    const int nv = plane / V;
-    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-      LV a1 = {}, a2 = {}, b1 = {}, b2 = {};
-      if (hasa) { a1 = __ldg(reinterpret_cast<const LV*>(pa1) + i); a2 = __ldg(reinterpret_cast<const LV*>(pa2) + i); }
-      if (hasb) { b1 = __ldg(reinterpret_cast<const LV*>(pb1) + i); b2 = __ldg(reinterpret_cast<const LV*>(pb2) + i); }
-      const T* fa1 = reinterpret_cast<const T*>(&a1);
-      const T* fa2 = reinterpret_cast<const T*>(&a2);
-      const T* fb1 = reinterpret_cast<const T*>(&b1);
-      const T* fb2 = reinterpret_cast<const T*>(&b2);
-      const int p0 = i * V;
-      int y = p0 / n3, z = p0 - y * n3;  // a vector may straddle two rows when n3 % V != 0
-#pragma unroll
-      for (int k = 0; k < V; ++k) {
-        if (z == n3) { z = 0; ++y; }
-        buf[y * S + z] = mk<C>(fa1[k] * fa2[k], fb1[k] * fb2[k]);
-        ++z;
-      }
+    const FastDiv n3div = g.d[2].ndiv;
+    for (int p = threadIdx.x; p < plane; p += blockDim.x) {
+      const int y = n3div.div(p), z = p - y * n3;
+      const T a = hasa ? __ldg(pa1 + p) * __ldg(pa2 + p) : T(0);
+      const T b = hasb ? __ldg(pb1 + p) * __ldg(pb2 + p) : T(0);
+      buf[y * S + z] = mk<C>(a, b);
     }
     __syncthreads();
     // z: n2 rows (stride S) of length n3; y: n3 columns (stride 1) of length n2 (element stride S)
     fft_forward(g.d[2], 0, g.d[2].ns, buf, tw3, n2, g.d[1].ndiv, S, 1);
     fft_forward(g.d[1], 0, g.d[1].ns, buf, tw2, n3, g.d[2].ndiv, 1, S);
-    rows_s2g(W + ((long long)cl * n1 + x) * plane, n3, buf, S, n2, n3);
+    plane_s2g(W + ((long long)cl * n1 + x) * plane, n3, buf, S, n2, n3, g.d[2].ndiv);
   }
 }
 
@@ -282,7 +241,7 @@ k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* _
 // ----------------------------------------------------------------------------------
 template <int R, typename C, typename T>
 __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int n1, int n3, FastDiv zdiv,
-                                                 const T* __restrict__ vy, long long vstride_x, bool energy_only) {
+                                                 const T* __restrict__ vy, int vstride_x, bool energy_only) {
   double e_acc = 0.0;
   // last forward stage of x (m = 1: no twiddles) fused with the first inverse stage (also m = 1)
   const int total = n3 * (n1 / R);
@@ -297,7 +256,7 @@ __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int
     T e = T(0);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const T vg = __ldg(vy + (long long)(q * R + k) * vstride_x + z);
+      const T vg = vy[(q * R + k) * vstride_x + z];
       e += vg * (v[k].x * v[k].x + v[k].y * v[k].y);
       v[k].x *= vg;
       v[k].y *= vg;
@@ -314,7 +273,7 @@ __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int
 
 template <typename C, typename T>
 __device__ __forceinline__ double x_last_coulomb_rt(int R, C* buf, int S, int n1, int n3, FastDiv zdiv, const T* vy,
-                                                    long long vsx, bool eo) {
+                                                    int vsx, bool eo) {
   switch (R) {
     case 2: return x_last_coulomb<2>(buf, S, n1, n3, zdiv, vy, vsx, eo);
     case 3: return x_last_coulomb<3>(buf, S, n1, n3, zdiv, vy, vsx, eo);
@@ -341,6 +300,7 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw1 = buf + n1 * S;
   C* tw3 = tw1 + n1;
+  T* vs = reinterpret_cast<T*>(tw3 + n3);  // v(G) of this y-plane, [x][z]
   __shared__ double red[32];
   for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = tw1g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
@@ -353,113 +313,154 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
     if (couple_empty(couples[c0 + cl])) continue;
     C* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
     __syncthreads();
-    rows_g2s(buf, S, wc, plane, n1, n3);  // rows x: W[cl][x][y][:]
+    plane_g2s(buf, S, wc, plane, n1, n3, g.d[2].ndiv);  // rows x: W[cl][x][y][:]
+    for (int p = threadIdx.x; p < n1 * n3; p += blockDim.x) {
+      const int xx = g.d[2].ndiv.div(p), z = p - xx * n3;
+      vs[p] = __ldg(vtab + ((long long)xx * n2 + y) * n3 + z);
+    }
     __syncthreads();
     const DimPlan& dx = g.d[0];
     // x: n3 columns of length n1 (element stride S)
     fft_forward(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
-    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vtab + (long long)y * n3, plane,
-                                       energy_only != 0);
+    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vs, n3, energy_only != 0);
     const double es = block_sum(e, red);
     if (threadIdx.x == 0) epart[(long long)(c0 + cl) * n2 + y] = es;
     if (energy_only) continue;
     __syncthreads();
     fft_inverse(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
     fft_inverse(g.d[2], 0, g.d[2].ns, buf, tw3, n1, g.d[0].ndiv, S, 1);  // z: n1 rows
-    rows_s2g(wc, plane, buf, S, n1, n3);
+    plane_s2g(wc, plane, buf, S, n1, n3, g.d[2].ndiv);
   }
+}
+
+// ----------------------------------------------------------------------------------
+// asynchronous 16-byte global -> shared copies (zero-filled when src_bytes == 0)
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // ----------------------------------------------------------------------------------
 // pass 3a: off-diagonal block pair (I, J) of two full blocks of B orbitals.  Couples sit in
 // canonical order: couple c holds pairs (I0 + c / (B/2), J0 + 2 (c mod B/2)) and (.., +1).
-// For each orbital row i the B/2 couples of the row are inverse-transformed along y together;
-// then every thread, for its own points, forms V_i = sum_j v_ij phi_j (added to V_x phi in FP64)
-// and accumulates V_j += v_ij phi_i in registers, flushed once at the end.
+// For each orbital row i the B/2 couples of the row are inverse-transformed along y together
+// (the next row's tiles stream in meanwhile); then every thread, for its own points, forms
+// V_i = sum_j v_ij phi_j (kept on chip) and V_j += v_ij phi_i (registers).  V_x phi is read and
+// written once per block pair and point, in FP64.
 // ----------------------------------------------------------------------------------
 constexpr int kDenseMaxThreads = 512;
+template <int NP> struct DenseBounds;
+template <> struct DenseBounds<2> { static constexpr int threads = 320, blocks = 2; };
+template <> struct DenseBounds<4> { static constexpr int threads = 512, blocks = 1; };
 
 template <typename T, int B, int NP>
-__global__ void __launch_bounds__(kDenseMaxThreads, 1)
-k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, const int* __restrict__ slot_list,
-              const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
-              const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale) {
+__global__ void __launch_bounds__(DenseBounds<NP>::threads, DenseBounds<NP>::blocks)
+k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
+              const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
+              const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
+              const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
   constexpr int HB = B / 2;
-  constexpr int LN = HB * ZC;  // lines of the interleaved tile [y][t][zz]
+  constexpr int LN = HB * ZC;                  // lines of the interleaved tile [y][t][zz]
+  constexpr int PER = 16 / int(sizeof(C));     // complex values per 16-byte copy
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int z0 = blockIdx.x * ZC;
   const int zcn = min(ZC, n3 - z0);
   const int x = blockIdx.y;
   const int slot = slot_list[blockIdx.z];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw2 = buf + n2 * LN;
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
+  const int pts = n2 * ZC;
+  C* tiles = reinterpret_cast<C*>(smem_raw);   // 2 x [n2][LN]
+  C* tw2 = tiles + 2 * n2 * LN;
+  T* phiI = reinterpret_cast<T*>(tw2 + n2);    // [B][pts]
+  T* accI = phiI + B * pts;                    // [B][pts]
 
   const int2 blk = slot_blocks[slot];
   const int I0 = blk.x * B, J0 = blk.y * B;
   const int cs = slot_couple_base[slot];
   const long long plane = (long long)n2 * n3;
   const long long rowoff = (long long)x * plane + z0;
-  const int pts = n2 * ZC;
 
-  // this thread's points
-  long long goff[NP];
-  bool ok[NP];
-  int sp[NP];
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    const int p = threadIdx.x + k * blockDim.x;
-    const int y = p / ZC, zz = p - (p / ZC) * ZC;
-    ok[k] = p < pts && zz < zcn;
-    sp[k] = y * LN + zz;  // + t * ZC for couple t
-    goff[k] = rowoff + (long long)y * n3 + zz;
-  }
-  T phiJ[NP][B], accJ[NP][B];
-#pragma unroll
-  for (int k = 0; k < NP; ++k)
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      phiJ[k][j] = ok[k] ? __ldg(orb + (long long)(J0 + j) * g.N + goff[k]) : T(0);
-      accJ[k][j] = T(0);
-    }
-
-  const FastDiv ldiv = fastdiv_dev(LN);
-  constexpr int PER = 16 / int(sizeof(C));
-  for (int r = 0; r < B; ++r) {
-    __syncthreads();  // previous row's point pass done with buf
-    // load the row's HB couple tiles: rows of ZC complex at W[c][x][y][z0..]
+  // tiles of orbital row r -> buffer r & 1 (empty couples and columns past n3 read as zero)
+  auto issue_row = [&](int r) {
+    C* dstb = tiles + (r & 1) * n2 * LN;
     for (int i = threadIdx.x; i < HB * n2 * (ZC / PER); i += blockDim.x) {
       const int v = i % (ZC / PER);
       const int rest = i / (ZC / PER);
       const int t = rest % HB, y = rest / HB;
       const int c = cs + r * HB + t;
-      int4 val = make_int4(0, 0, 0, 0);
-      if (!couple_empty(couples[c]) && v * PER < zcn)
-        val = __ldg(reinterpret_cast<const int4*>(W + ((long long)(c - c0) * n1 + x) * plane + (long long)y * n3 + z0) + v);
-      reinterpret_cast<int4*>(buf + y * LN + t * ZC)[v] = val;
+      const bool live = !couple_empty(couples[c]) && v * PER < zcn;
+      const C* src = W + ((long long)(c - c0) * n1 + x) * plane + (long long)y * n3 + z0 + v * PER;
+      cp_async16(dstb + y * LN + t * ZC + v * PER, live ? (const void*)src : (const void*)W, live ? 16 : 0);
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  issue_row(0);
+
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
+  for (int i = threadIdx.x; i < B * pts; i += blockDim.x) {
+    const int o = i / pts, p = i - o * pts;
+    const int y = p / ZC, zz = p - y * ZC;
+    phiI[i] = zz < zcn ? __ldg(orb + (long long)(I0 + o) * g.N + rowoff + (long long)y * n3 + zz) : T(0);
+  }
+
+  // this thread's points
+  long long goff[NP];
+  bool ok[NP];
+  int pp[NP];
+  T phiJ[NP][B], accJ[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int p = threadIdx.x + k * blockDim.x;
+    const int y = p / ZC, zz = p - (p / ZC) * ZC;
+    ok[k] = p < pts && zz < zcn;
+    pp[k] = p;
+    goff[k] = rowoff + (long long)y * n3 + zz;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      phiJ[k][j] = ok[k] ? __ldg(orb + (long long)(J0 + j) * g.N + goff[k]) : T(0);
+      accJ[k][j] = T(0);
+    }
+  }
+
+  const FastDiv ldiv = fastdiv_dev(LN);
+  for (int r = 0; r < B; ++r) {
+    if (r + 1 < B) {
+      issue_row(r + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // row r's tiles (and the tables) visible to all threads
+    C* buf = tiles + (r & 1) * n2 * LN;
     fft_inverse(g.d[1], 0, g.d[1].ns, buf, tw2, LN, ldiv, 1, LN);
-    const int i_orb = I0 + r;
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       if (!ok[k]) continue;
-      const T phii = __ldg(orb + (long long)i_orb * g.N + goff[k]);
+      const int p = pp[k];
+      const int y = p / ZC, zz = p - y * ZC;
+      const C* vp = buf + y * LN + zz;
+      const T phii = phiI[r * pts + p];
       T acci = T(0);
 #pragma unroll
       for (int t = 0; t < HB; ++t) {
-        const C v = buf[sp[k] + t * ZC];
+        const C v = vp[t * ZC];
         acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
         accJ[k][2 * t] += v.x * phii;
         accJ[k][2 * t + 1] += v.y * phii;
       }
-      double* dst = V + (long long)i_orb * g.N + goff[k];
-      *dst += vscale * double(acci);
+      accI[r * pts + p] = acci;
     }
+    __syncthreads();  // buffer r & 1 is refilled by the copies issued in the next iteration
   }
+  // flush, FP64 read-modify-write: V_J from registers, V_I from shared memory
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
@@ -467,6 +468,11 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
     for (int j = 0; j < B; ++j) {
       double* dst = V + (long long)(J0 + j) * g.N + goff[k];
       *dst += vscale * double(accJ[k][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      double* dst = V + (long long)(I0 + j) * g.N + goff[k];
+      *dst += vscale * double(accI[j * pts + pp[k]]);
     }
   }
 }

@@ -49,7 +49,7 @@ void Passes<Real>::y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem
                                double vscale) {
   // points per thread so that one block of at most kDenseMaxThreads threads covers the tile
   const int pts = g.n2 * ZChunk<Real>::value;
-  const bool np4 = pts > 2 * kDenseMaxThreads;
+  const bool np4 = pts > 2 * DenseBounds<2>::threads;
 #define HFX_DENSE(BB, NPP)                                                                                      \
   k_y_acc_dense<Real, BB, NPP><<<grid, threads, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks, \
                                                             c0, W, tw2, V, vscale)

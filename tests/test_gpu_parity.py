@@ -185,6 +185,37 @@ def test_duplicate_pairs_are_reported_and_counted_once():
     ex.close()
 
 
+@pytest.mark.parametrize("block", ["4", "8", "5"])
+def test_orbital_block_sizes(block, monkeypatch):
+    """Block sizes with a register-accumulating kernel (4, 8) and without one (5: generic path)."""
+    monkeypatch.setenv("HFX_BLOCK", block)
+    n, L, n_orb = 16, 8.0, 19
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=15)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    for prec in ("fp64", "fp32"):
+        E, V = run_gpu(phi, pairs, lat, prec)
+        assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+        assert rel(V, V_ref) <= TOL[prec]
+
+
+def test_large_tile_sparse_block_pair():
+    """A 90^3 grid (more tile points than one thread block holds two to a thread) and a block pair
+    with missing pairs."""
+    n, L, n_orb = 90, 22.0, 16
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=16, frac=0.15)
+    blk = np.array([[i, j] for i in range(8) for j in range(8, 16) if (i + j) % 5 != 0], dtype=np.int32)
+    extra = np.array([[0, 0], [3, 5], [9, 12], [15, 15]], dtype=np.int32)
+    pairs = np.concatenate([blk, extra])
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    for prec in ("fp64", "fp32"):
+        E, V = run_gpu(phi, pairs, lat, prec)
+        assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+        assert rel(V, V_ref) <= TOL[prec]
+
+
 def test_bad_pairs_are_reported_and_skipped():
     from paper_2309_00651_gb300 import hfx
     n, L, n_orb = 16, 8.0, 6
