@@ -290,7 +290,7 @@ static size_t smem_acc(const hfx_ctx* c) {
 }
 static size_t smem_dense(const hfx_ctx* c) {
   const int zc = zchunk(c);
-  return (size_t)(2 * c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c) +
+  return (size_t)(kDenseRing * c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c) +
          (size_t)2 * c->bsize * c->grid[1] * zc * real_size(c);
 }
 static bool dense_available(const hfx_ctx* c) {

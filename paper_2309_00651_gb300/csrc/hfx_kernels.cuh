@@ -172,13 +172,30 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // plane copies, one complex value per thread step (consecutive threads on consecutive z: 8- or
 // 16-byte coalesced global accesses and conflict-free shared accesses into the padded rows)
+constexpr int kLoadUnroll = 4;  // loads each thread keeps in flight per copy step
+
 template <typename C>
 __device__ __forceinline__ void plane_g2s(C* __restrict__ buf, int S, const C* __restrict__ src, long long gstride,
                                           int rows, int n3, FastDiv n3div) {
   const int total = rows * n3;
-  for (int p = threadIdx.x; p < total; p += blockDim.x) {
-    const int r = n3div.div(p), z = p - r * n3;
-    buf[r * S + z] = __ldg(src + r * gstride + z);
+  for (int p0 = threadIdx.x; p0 < total; p0 += kLoadUnroll * blockDim.x) {
+    C v[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int p = p0 + u * blockDim.x;
+      if (p < total) {
+        const int r = n3div.div(p), z = p - r * n3;
+        v[u] = __ldg(src + r * gstride + z);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int p = p0 + u * blockDim.x;
+      if (p < total) {
+        const int r = n3div.div(p), z = p - r * n3;
+        buf[r * S + z] = v[u];
+      }
+    }
   }
 }
 template <typename C>
@@ -195,7 +212,7 @@ __device__ __forceinline__ void plane_s2g(C* __restrict__ dst, long long gstride
 // pass 1: pair product + forward FFT along z and y of one x-plane
 // ----------------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kThreadsPlane)
+__global__ void __launch_bounds__(kThreadsPlane, 3)
 k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W,
          const cx<T>* __restrict__ tw2g, const cx<T>* __restrict__ tw3g) {
   using C = cx<T>;
@@ -222,11 +239,25 @@ k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* _
     const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
     __syncthreads();  // previous item's store has finished reading buf (and tables are loaded)
     const FastDiv n3div = g.d[2].ndiv;
-    for (int p = threadIdx.x; p < plane; p += blockDim.x) {
-      const int y = n3div.div(p), z = p - y * n3;
-      const T a = hasa ? __ldg(pa1 + p) * __ldg(pa2 + p) : T(0);
-      const T b = hasb ? __ldg(pb1 + p) * __ldg(pb2 + p) : T(0);
-      buf[y * S + z] = mk<C>(a, b);
+    for (int p0 = threadIdx.x; p0 < plane; p0 += kLoadUnroll * blockDim.x) {
+      T a1[kLoadUnroll], a2[kLoadUnroll], b1[kLoadUnroll], b2[kLoadUnroll];
+#pragma unroll
+      for (int u = 0; u < kLoadUnroll; ++u) {
+        const int p = p0 + u * blockDim.x;
+        const bool in = p < plane;
+        a1[u] = (in && hasa) ? __ldg(pa1 + p) : T(0);
+        a2[u] = (in && hasa) ? __ldg(pa2 + p) : T(0);
+        b1[u] = (in && hasb) ? __ldg(pb1 + p) : T(0);
+        b2[u] = (in && hasb) ? __ldg(pb2 + p) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadUnroll; ++u) {
+        const int p = p0 + u * blockDim.x;
+        if (p < plane) {
+          const int y = n3div.div(p), z = p - y * n3;
+          buf[y * S + z] = mk<C>(a1[u] * a2[u], b1[u] * b2[u]);
+        }
+      }
     }
     __syncthreads();
     // z: n2 rows (stride S) of length n3; y: n3 columns (stride 1) of length n2 (element stride S)
@@ -290,7 +321,7 @@ __device__ __forceinline__ double x_last_coulomb_rt(int R, C* buf, int S, int n1
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsPlane)
+__global__ void __launch_bounds__(kThreadsPlane, 3)
 k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
             const cx<T>* __restrict__ tw1g, const cx<T>* __restrict__ tw3g, double* __restrict__ epart,
             int energy_only) {
@@ -314,9 +345,17 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
     C* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
     __syncthreads();
     plane_g2s(buf, S, wc, plane, n1, n3, g.d[2].ndiv);  // rows x: W[cl][x][y][:]
-    for (int p = threadIdx.x; p < n1 * n3; p += blockDim.x) {
-      const int xx = g.d[2].ndiv.div(p), z = p - xx * n3;
-      vs[p] = __ldg(vtab + ((long long)xx * n2 + y) * n3 + z);
+    for (int p0 = threadIdx.x; p0 < n1 * n3; p0 += kLoadUnroll * blockDim.x) {
+      T v[kLoadUnroll];
+#pragma unroll
+      for (int u = 0; u < kLoadUnroll; ++u) {
+        const int p = p0 + u * blockDim.x;
+        const int xx = g.d[2].ndiv.div(p), z = p - xx * n3;
+        v[u] = p < n1 * n3 ? __ldg(vtab + ((long long)xx * n2 + y) * n3 + z) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kLoadUnroll; ++u)
+        if (p0 + u * blockDim.x < n1 * n3) vs[p0 + u * blockDim.x] = v[u];
     }
     __syncthreads();
     const DimPlan& dx = g.d[0];
@@ -355,6 +394,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // written once per block pair and point, in FP64.
 // ----------------------------------------------------------------------------------
 constexpr int kDenseMaxThreads = 512;
+constexpr int kDenseRing = 3;  // orbital rows of couple tiles in flight
 template <int NP> struct DenseBounds;
 template <> struct DenseBounds<2> { static constexpr int threads = 320, blocks = 2; };
 template <> struct DenseBounds<4> { static constexpr int threads = 512, blocks = 1; };
@@ -377,8 +417,8 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
   const int x = blockIdx.y;
   const int slot = slot_list[blockIdx.z];
   const int pts = n2 * ZC;
-  C* tiles = reinterpret_cast<C*>(smem_raw);   // 2 x [n2][LN]
-  C* tw2 = tiles + 2 * n2 * LN;
+  C* tiles = reinterpret_cast<C*>(smem_raw);   // kDenseRing x [n2][LN]
+  C* tw2 = tiles + kDenseRing * n2 * LN;
   T* phiI = reinterpret_cast<T*>(tw2 + n2);    // [B][pts]
   T* accI = phiI + B * pts;                    // [B][pts]
 
@@ -388,9 +428,11 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
   const long long plane = (long long)n2 * n3;
   const long long rowoff = (long long)x * plane + z0;
 
-  // tiles of orbital row r -> buffer r & 1 (empty couples and columns past n3 read as zero)
+  // tiles of orbital row r -> ring buffer r % kDenseRing (empty couples and columns past n3 read as
+  // zero); a row past the block commits an empty group so the group count stays uniform
   auto issue_row = [&](int r) {
-    C* dstb = tiles + (r & 1) * n2 * LN;
+    if (r >= B) { cp_async_commit(); return; }
+    C* dstb = tiles + (r % kDenseRing) * n2 * LN;
     for (int i = threadIdx.x; i < HB * n2 * (ZC / PER); i += blockDim.x) {
       const int v = i % (ZC / PER);
       const int rest = i / (ZC / PER);
@@ -402,7 +444,8 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
     }
     cp_async_commit();
   };
-  issue_row(0);
+#pragma unroll
+  for (int r = 0; r < kDenseRing - 1; ++r) issue_row(r);
 
   for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
   for (int i = threadIdx.x; i < B * pts; i += blockDim.x) {
@@ -432,14 +475,10 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
 
   const FastDiv ldiv = fastdiv_dev(LN);
   for (int r = 0; r < B; ++r) {
-    if (r + 1 < B) {
-      issue_row(r + 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    issue_row(r + kDenseRing - 1);  // its buffer was last read in row r - 1 (barrier passed)
+    cp_async_wait<kDenseRing - 1>();
     __syncthreads();  // row r's tiles (and the tables) visible to all threads
-    C* buf = tiles + (r & 1) * n2 * LN;
+    C* buf = tiles + (r % kDenseRing) * n2 * LN;
     fft_inverse(g.d[1], 0, g.d[1].ns, buf, tw2, LN, ldiv, 1, LN);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -458,7 +497,7 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
       }
       accI[r * pts + p] = acci;
     }
-    __syncthreads();  // buffer r & 1 is refilled by the copies issued in the next iteration
+    __syncthreads();  // buffer r % kDenseRing is refilled by the copies issued in the next iteration
   }
   // flush, FP64 read-modify-write: V_J from registers, V_I from shared memory
 #pragma unroll
