@@ -281,8 +281,7 @@ static size_t smem_fwd(const hfx_ctx* c) {
   return (size_t)(c->grid[1] * (c->grid[2] + 1) + c->grid[1] + c->grid[2]) * cplx_size(c);
 }
 static size_t smem_x(const hfx_ctx* c) {
-  return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c) +
-         (size_t)c->grid[0] * c->grid[2] * real_size(c);
+  return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c);
 }
 static size_t smem_acc(const hfx_ctx* c) {
   const int zc = zchunk(c);

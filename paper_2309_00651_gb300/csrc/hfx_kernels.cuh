@@ -272,7 +272,7 @@ k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* _
 // ----------------------------------------------------------------------------------
 template <int R, typename C, typename T>
 __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int n1, int n3, FastDiv zdiv,
-                                                 const T* __restrict__ vy, int vstride_x, bool energy_only) {
+                                                 const T* __restrict__ vy, long long vstride_x, bool energy_only) {
   double e_acc = 0.0;
   // last forward stage of x (m = 1: no twiddles) fused with the first inverse stage (also m = 1)
   const int total = n3 * (n1 / R);
@@ -287,7 +287,7 @@ __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int
     T e = T(0);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
-      const T vg = vy[(q * R + k) * vstride_x + z];
+      const T vg = __ldg(vy + (q * R + k) * vstride_x + z);
       e += vg * (v[k].x * v[k].x + v[k].y * v[k].y);
       v[k].x *= vg;
       v[k].y *= vg;
@@ -304,7 +304,7 @@ __device__ __forceinline__ double x_last_coulomb(C* __restrict__ buf, int S, int
 
 template <typename C, typename T>
 __device__ __forceinline__ double x_last_coulomb_rt(int R, C* buf, int S, int n1, int n3, FastDiv zdiv, const T* vy,
-                                                    int vsx, bool eo) {
+                                                    long long vsx, bool eo) {
   switch (R) {
     case 2: return x_last_coulomb<2>(buf, S, n1, n3, zdiv, vy, vsx, eo);
     case 3: return x_last_coulomb<3>(buf, S, n1, n3, zdiv, vy, vsx, eo);
@@ -331,7 +331,6 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw1 = buf + n1 * S;
   C* tw3 = tw1 + n1;
-  T* vs = reinterpret_cast<T*>(tw3 + n3);  // v(G) of this y-plane, [x][z]
   __shared__ double red[32];
   for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = tw1g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
@@ -345,23 +344,12 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
     C* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
     __syncthreads();
     plane_g2s(buf, S, wc, plane, n1, n3, g.d[2].ndiv);  // rows x: W[cl][x][y][:]
-    for (int p0 = threadIdx.x; p0 < n1 * n3; p0 += kLoadUnroll * blockDim.x) {
-      T v[kLoadUnroll];
-#pragma unroll
-      for (int u = 0; u < kLoadUnroll; ++u) {
-        const int p = p0 + u * blockDim.x;
-        const int xx = g.d[2].ndiv.div(p), z = p - xx * n3;
-        v[u] = p < n1 * n3 ? __ldg(vtab + ((long long)xx * n2 + y) * n3 + z) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < kLoadUnroll; ++u)
-        if (p0 + u * blockDim.x < n1 * n3) vs[p0 + u * blockDim.x] = v[u];
-    }
     __syncthreads();
     const DimPlan& dx = g.d[0];
     // x: n3 columns of length n1 (element stride S)
     fft_forward(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
-    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vs, n3, energy_only != 0);
+    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vtab + (long long)y * n3,
+                                       plane, energy_only != 0);
     const double es = block_sum(e, red);
     if (threadIdx.x == 0) epart[(long long)(c0 + cl) * n2 + y] = es;
     if (energy_only) continue;
