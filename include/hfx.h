@@ -138,6 +138,32 @@ typedef struct {
 hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
                              void* cuda_stream);
 
+/* hfx_apply_noalloc -- hfx_apply for callers that cannot allocate device memory.
+ * The paper has no counterpart: this exists for callers that must not call cudaMalloc when
+ * they evaluate the exchange -- code running inside a device allocator or memory-pool callback
+ * (allocating there would recurse), hosts whose CUDA memory is owned by another framework that
+ * forbids side allocations, and latency-critical loops that cannot afford cudaMalloc's implicit
+ * synchronisation.  It computes exactly what hfx_apply computes, with the same arguments and
+ * argument errors, but takes no workspace: its scratch (pair staging, transforms, energy sums,
+ * the FP32 orbital copy and the schedule tables) is one static device array of
+ * HFX_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library
+ * holds until the process exits.  It allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call) and never touches the context's own workspace.
+ *   - Problems whose scratch would exceed HFX_NOALLOC_SCRATCH_BYTES are rejected with
+ *     HFX_ERR_OOM before anything is enqueued (e.g. 16 orbitals on a 32^3 grid fit in both
+ *     precisions; use hfx_apply with a workspace beyond that).
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *     with that device current; make that first call before any stream capture.
+ *   - The schedule tables are copied from pageable host memory with cudaMemcpyAsync on
+ *     cuda_stream.
+ *   - Every call shares the one array, which keeps the previous call's contents (each call
+ *     re-initialises what it needs).  Calls that overlap on the GPU -- on any stream, any
+ *     context -- race on the array: serialise them. */
+#define HFX_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
+                             int64_t n_pairs, uint32_t flags, double* ex_dev, double* vxphi,
+                             void* cuda_stream);
+
 /* hfx_sync_status -- wait for `cuda_stream` and return (then clear) the device-side error
  * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST or HFX_ERR_TIMEOUT. */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);

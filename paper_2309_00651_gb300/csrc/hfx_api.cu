@@ -10,6 +10,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -804,4 +805,152 @@ extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[5], int64_t launche
   }
   c->ev_pending.clear();
   return st;
+}
+
+// ------------------------------------------------------------------------------------
+// Allocation-free evaluation.
+//
+// Some callers cannot allocate device memory when they evaluate the exchange: code that runs
+// inside a custom device allocator or memory-pool callback (re-entering cudaMalloc there would
+// recurse or deadlock), a host whose CUDA allocations are owned by another framework that
+// forbids side allocations, or a latency-critical loop where cudaMalloc's implicit device
+// synchronisation is not acceptable.  hfx_apply_noalloc serves them: it runs the same kernels
+// as hfx_apply, but its scratch (pair staging, per-batch transforms, energy partial sums, the
+// FP32 orbital copy and the schedule tables) lives in the file-scope device array below, of
+// kNoallocScratchBytes bytes, which every GPU that loads this library reserves until the
+// process exits.  In host code the array's name only stands in for the symbol: its device
+// address comes from cudaGetSymbolAddress, taken once per device on the first call there.
+// ------------------------------------------------------------------------------------
+constexpr size_t kNoallocScratchBytes = HFX_NOALLOC_SCRATCH_BYTES;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+static void* g_noalloc_addr[kNoallocMaxDevices];  // device address of g_noalloc_scratch, per device
+static std::mutex g_noalloc_mutex;
+
+// device address of the scratch array on the current device (set up on first use there)
+static hfx_status noalloc_scratch(void** out) {
+  int dev = 0;
+  HFX_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(HFX_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(HFX_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
+                                        int64_t n_pairs, uint32_t flags, double* ex_dev, double* vxphi,
+                                        void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32)) return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
+  if (n_orb <= 0) return fail(HFX_ERR_INVALID_ARG, "n_orb must be > 0");
+  if (n_pairs < 0 || n_pairs > (int64_t)1 << 31) return fail(HFX_ERR_INVALID_ARG, "n_pairs out of range");
+  if (!orbitals || !ex_dev) return fail(HFX_ERR_INVALID_ARG, "orbitals or ex_dev is NULL");
+  if (n_pairs > 0 && !pairs) return fail(HFX_ERR_INVALID_ARG, "pairs is NULL");
+  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
+  if (!energy_only && !vxphi) return fail(HFX_ERR_INVALID_ARG, "vxphi is NULL without HFX_ENERGY_ONLY");
+  if ((flags & HFX_ORBITALS_F32) && c->prec != HFX_PREC_FP32)
+    return fail(HFX_ERR_INVALID_ARG, "HFX_ORBITALS_F32 needs HFX_PREC_FP32");
+  if (((uintptr_t)orbitals | (uintptr_t)pairs | (uintptr_t)vxphi) % 16 || ((uintptr_t)ex_dev % 8))
+    return fail(HFX_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
+  const size_t vbytes = (size_t)n_orb * c->N * sizeof(double);
+  if (n_pairs == 0) {
+    if (!accumulate) {
+      k_set_scalar<<<1, 1, 0, st>>>(ex_dev, 0.0);
+      if (!energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
+    }
+    HFX_CUDA_TRY(cudaGetLastError());
+    return HFX_OK;
+  }
+
+  // host schedule; its device tables go to the head of the scratch array, the workspace after them
+  Schedule S = make_host_schedule(c, n_orb);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(std::max<size_t>(bytes, 16)); return o; };
+  const size_t o_blocks = take(S.slot_blocks.size() * sizeof(int2));
+  const size_t o_of_bp = take(S.slot_of_bp.size() * sizeof(int));
+  const size_t o_base = take(S.slot_couple_base.size() * sizeof(int));
+  const size_t o_dense = take(S.dense_slots.size() * sizeof(int));
+  const size_t o_gen = take(S.generic_slots.size() * sizeof(int));
+  const Layout L = layout_of(c, S, n_orb, n_pairs);
+  if (off + L.total > kNoallocScratchBytes)
+    return fail(HFX_ERR_OOM,
+                "problem needs %zu bytes of scratch; the allocation-free entry point holds %zu (use hfx_apply with a "
+                "caller-owned workspace)",
+                off + L.total, kNoallocScratchBytes);
+  void* scratch = nullptr;
+  hfx_status s0 = noalloc_scratch(&scratch);
+  if (s0 != HFX_OK) return s0;
+  char* base = (char*)scratch;
+  auto put = [&](size_t o, const void* src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  };
+  HFX_CUDA_TRY(put(o_blocks, S.slot_blocks.data(), S.slot_blocks.size() * sizeof(int2)));
+  HFX_CUDA_TRY(put(o_of_bp, S.slot_of_bp.data(), S.slot_of_bp.size() * sizeof(int)));
+  HFX_CUDA_TRY(put(o_base, S.slot_couple_base.data(), S.slot_couple_base.size() * sizeof(int)));
+  HFX_CUDA_TRY(put(o_dense, S.dense_slots.data(), S.dense_slots.size() * sizeof(int)));
+  HFX_CUDA_TRY(put(o_gen, S.generic_slots.data(), S.generic_slots.size() * sizeof(int)));
+  S.d_slot_blocks = (int2*)(base + o_blocks);
+  S.d_slot_of_bp = (int*)(base + o_of_bp);
+  S.d_slot_couple_base = (int*)(base + o_base);
+  S.d_dense_slots = (int*)(base + o_dense);
+  S.d_generic_slots = (int*)(base + o_gen);
+
+  // the passes read the context's workspace: point it at the scratch for this call (calls on one
+  // context never overlap), with event timing off (it would create events)
+  struct Restore {
+    hfx_ctx* c;
+    void* ws;
+    size_t bytes;
+    bool prof;
+    ~Restore() { c->ws = ws; c->ws_bytes = bytes; c->prof_on = prof; }
+  } restore{c, c->ws, c->ws_bytes, c->prof_on};
+  c->ws = base + off;
+  c->ws_bytes = kNoallocScratchBytes - off;
+  c->prof_on = false;
+  char* ws = (char*)c->ws;
+
+  if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
+  int4* couples = (int4*)(ws + L.couples);
+  HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S.max_total_couples * sizeof(int4), st));
+  {
+    const int threads = 256;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_pairs + threads - 1) / threads,
+                                                                        (long long)c->sm_count * 8));
+    k_plan_place<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S.b, S.nb, S.d_slot_of_bp,
+                                             S.d_slot_couple_base, couples, c->d_err);
+  }
+  HFX_CUDA_TRY(cudaGetLastError());
+  hfx_status rs;
+  if (c->prec == HFX_PREC_FP64) {
+    rs = run_passes<double>(c, S, L, (const double*)orbitals, n_orb, flags, vxphi, st);
+  } else {
+    const float* orb32;
+    if (flags & HFX_ORBITALS_F32) {
+      orb32 = (const float*)orbitals;
+    } else {
+      float* dst = (float*)(ws + L.orb32);
+      const long long n = (long long)n_orb * c->N;
+      const int blocks = (int)std::min<long long>((n / 2 + 255) / 256 + 1, (long long)c->sm_count * 16);
+      k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
+      orb32 = dst;
+    }
+    rs = run_passes<float>(c, S, L, orb32, n_orb, flags, vxphi, st);
+  }
+  if (rs != HFX_OK) return rs;
+  const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
+  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S.max_total_couples, c->grid[1], scale,
+                                    accumulate ? 1 : 0, ex_dev);
+  HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
 }

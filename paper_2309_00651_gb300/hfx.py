@@ -26,8 +26,9 @@ HFX_ORBITALS_F32 = 0x4
 
 # every symbol include/hfx.h declares
 EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
-            "hfx_sync_status", "hfx_plan_stats", "hfx_profile_enable", "hfx_profile_read", "hfx_last_error",
-            "hfx_destroy")
+            "hfx_apply_noalloc", "hfx_sync_status", "hfx_plan_stats", "hfx_profile_enable", "hfx_profile_read",
+            "hfx_last_error", "hfx_destroy")
+HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_inv_acc", "energy")
 
 
@@ -69,6 +70,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_set_workspace.restype = ctypes.c_int
     L.hfx_apply.argtypes = [vp, vp, i32, vp, i64, u32, vp, vp, vp]
     L.hfx_apply.restype = ctypes.c_int
+    L.hfx_apply_noalloc.argtypes = [vp, vp, i32, vp, i64, u32, vp, vp, vp]
+    L.hfx_apply_noalloc.restype = ctypes.c_int
     L.hfx_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HfxApplyArgs), i32, vp]
     L.hfx_apply_batched.restype = ctypes.c_int
     L.hfx_sync_status.argtypes = [vp, vp]
@@ -133,6 +136,15 @@ def hfx_apply(ctx, orbitals: torch.Tensor, pairs: torch.Tensor, ex: torch.Tensor
     n_orb = orbitals.shape[0]
     _check(load_library().hfx_apply(ctx, _ptr(orbitals), int(n_orb), _ptr(pairs), int(pairs.shape[0]), int(flags),
                                     _ptr(ex), _ptr(vxphi), _stream_handle(stream)))
+
+
+def hfx_apply_noalloc(ctx, orbitals: torch.Tensor, pairs: torch.Tensor, ex: torch.Tensor,
+                      vxphi: Optional[torch.Tensor], flags: int = 0, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """hfx_apply without a workspace, for callers that cannot allocate device memory at call time:
+    the library's own static device scratch (HFX_NOALLOC_SCRATCH_BYTES) is used instead."""
+    n_orb = orbitals.shape[0]
+    _check(load_library().hfx_apply_noalloc(ctx, _ptr(orbitals), int(n_orb), _ptr(pairs), int(pairs.shape[0]),
+                                            int(flags), _ptr(ex), _ptr(vxphi), _stream_handle(stream)))
 
 
 def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) -> None:
