@@ -20,7 +20,8 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhfx.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu"]
+SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu"] + [
+    f"hfx_ct_{n}.cu" for n in (32, 48, 64, 72, 96, 128)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE] + ARCH
 
@@ -80,7 +81,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs

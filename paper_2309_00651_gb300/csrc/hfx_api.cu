@@ -12,6 +12,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hfx.h"
@@ -43,45 +44,18 @@ static hfx_status fail(hfx_status st, const char* fmt, ...) {
   } while (0)
 
 // ------------------------------------------------------------------------------------
-// FFT plans: each edge is split into in-register radices from {16,12,10,9,8,6,5,4,3,2},
-// fewest stages first, then the lowest estimated flop count.
+// FFT plans: each edge is split by best_factors (fft_plan.h)
 // ------------------------------------------------------------------------------------
-static const int kRadices[] = {16, 12, 10, 9, 8, 6, 5, 4, 3, 2};
-
-static double radix_cost(int r) {
-  switch (r) {
-    case 2: return 2.0; case 3: return 4.0; case 4: return 4.0; case 5: return 6.8;
-    case 6: return 5.3; case 8: return 5.5; case 9: return 7.6; case 10: return 7.2;
-    case 12: return 7.3; case 16: return 7.5; default: return 99.0;
-  }
-}
-
-static bool factorize(int n, std::vector<int>& best) {
-  if (n == 1) { best.clear(); return true; }
-  bool found = false;
-  double best_cost = 1e30;
-  for (int r : kRadices) {
-    if (n % r) continue;
-    std::vector<int> rest;
-    if (!factorize(n / r, rest)) continue;
-    rest.insert(rest.begin(), r);
-    double cost = 0.0;
-    for (int f : rest) cost += radix_cost(f) + 6.0 * (f - 1) / f;
-    cost += 1000.0 * rest.size();  // fewest stages first (each is a shared-memory round trip)
-    if (!found || cost < best_cost) { best = rest; best_cost = cost; found = true; }
-  }
-  return found;
-}
-
 static bool make_dim_plan(int n, DimPlan& d) {
-  std::vector<int> f;
-  if (n < 2 || n > 256 || !factorize(n, f) || (int)f.size() > kMaxStages) return false;
+  if (n < 2 || n > 256) return false;
+  const Factors f = best_factors(n);
+  if (f.ns < 1) return false;
   d.n = n;
-  d.ns = (int)f.size();
+  d.ns = f.ns;
   int m = n;
   for (int s = 0; s < d.ns; ++s) {
-    d.r[s] = f[s];
-    m /= f[s];
+    d.r[s] = f.r[s];
+    m /= f.r[s];
     d.m[s] = m;
   }
   for (int s = d.ns; s < kMaxStages; ++s) { d.r[s] = 1; d.m[s] = 1; }
@@ -239,6 +213,10 @@ struct hfx_ctx {
   int bsize = 8;
   size_t transform_budget = size_t(1) << 30;
   int blocks_fwd = 1, blocks_x = 1;
+  // compile-time-geometry passes (FP32, cubic grid with an instantiated edge), else NULL
+  const CtFns* ct = nullptr;
+  void* d_twct = nullptr;        // per-stage twiddle tables of the edge
+  int blocks_fwd_ct = 1, blocks_x_ct = 1;
   std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
   // optional per-pass device timing (hfx_profile_enable)
   bool prof_on = false;
@@ -293,11 +271,37 @@ static size_t smem_dense(const hfx_ctx* c) {
   return (size_t)(kDenseRing * c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c) +
          (size_t)2 * c->bsize * c->grid[1] * zc * real_size(c);
 }
+static size_t smem_plane_ct(int n) { return (size_t)(n * (n + 1) + stage_plan(n).twtotal) * sizeof(float2); }
+static size_t smem_dense_ct(int n, int b) {
+  const int zc = 8, ln = (b / 2) * zc, pts = n * zc;
+  return (size_t)(kDenseRing * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
+}
+
+// per-stage twiddle tables of one edge: stage s with m > 1 holds w_L^{j1 k}, j1 < m, k < r, L = r m
+static std::vector<double> stage_twiddles(int n) {
+  const StagePlan p = stage_plan(n);
+  std::vector<double> tw(2 * (size_t)std::max(p.twtotal, 1), 0.0);
+  for (int s = 0; s < p.ns; ++s) {
+    if (p.m[s] <= 1) continue;
+    const int r = p.r[s], m = p.m[s], L = r * m;
+    for (int j1 = 0; j1 < m; ++j1)
+      for (int k = 0; k < r; ++k) {
+        const cs_pair w = cossin_2pi_frac((long long)j1 * k, L);
+        const size_t idx = (size_t)p.twoff[s] + (size_t)j1 * r + k;
+        tw[2 * idx] = w.c;
+        tw[2 * idx + 1] = -w.s;
+      }
+  }
+  return tw;
+}
+
 static bool dense_available(const hfx_ctx* c) {
   return c->prec == HFX_PREC_FP64 ? Passes<double>::has_dense(c->bsize) : Passes<float>::has_dense(c->bsize);
 }
 
 static void free_ctx_tables(hfx_ctx* c) {
+  if (c->d_twct) cudaFree(c->d_twct);
+  c->d_twct = nullptr;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   c->ev_pending.clear();
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -444,6 +448,22 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   c->blocks_x = std::max(1, c->blocks_x);
   hfx_status st = build_tables(c.get());
   if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
+  // compile-time-geometry passes for FP32 cubic grids with an instantiated edge
+  const char* no_ct = std::getenv("HFX_NO_CT");
+  if (prec == HFX_PREC_FP32 && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
+    const CtFns* f = ct_fns(grid[0]);
+    const int n = grid[0];
+    if (f && std::max(smem_plane_ct(n), smem_dense_ct(n, 8)) + 512 <= (size_t)c->max_smem) {
+      e = f->prepare(c->max_smem - 512, smem_plane_ct(n), &c->blocks_fwd_ct, &c->blocks_x_ct);
+      if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
+      auto tw = to_real_vec<float>(stage_twiddles(n));
+      st = upload(&c->d_twct, tw.data(), tw.size() * sizeof(float));
+      if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
+      c->blocks_fwd_ct = std::max(1, c->blocks_fwd_ct);
+      c->blocks_x_ct = std::max(1, c->blocks_x_ct);
+      c->ct = f;
+    }
+  }
   *out = c.release();
   return HFX_OK;
 }
@@ -621,19 +641,36 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
     const long long items1 = (long long)(c1 - c0) * g.n1, items2 = (long long)(c1 - c0) * g.n2;
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
+    const CtFns* ct = std::is_same<T, float>::value ? c->ct : nullptr;
     cudaEvent_t e0 = prof_mark(c, st);
-    Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
-                      (const C*)c->d_tw[2]);
+    if (ct) {
+      const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
+      ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), st, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
+                 (const float2*)c->d_twct);
+    } else {
+      Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
+                        (const C*)c->d_tw[2]);
+    }
     prof_close(c, kProfFwd, e0, st);
     e0 = prof_mark(c, st);
-    Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, couples, c0, c1, W, (const T*)c->d_vtab,
-                         (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
+    if (ct) {
+      const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
+      ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), st, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
+                    (const float2*)c->d_twct, epart, energy_only ? 1 : 0);
+    } else {
+      Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, couples, c0, c1, W, (const T*)c->d_vtab,
+                           (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
+    }
     prof_close(c, kProfX, e0, st);
     if (!energy_only) {
       e0 = prof_mark(c, st);
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
-      if (nd > 0)
+      if (nd > 0 && ct && S.b == 8)
+        ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
+                        S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
+                        (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
+      else if (nd > 0)
         Passes<T>::y_acc_dense(g, dim3(nzc, g.n1, nd), dense_threads, smem_dense(c), st, S.b, orb, couples,
                                S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
                                (const C*)c->d_tw[1], vxphi, vscale);

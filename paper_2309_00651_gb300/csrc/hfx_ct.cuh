@@ -1,0 +1,373 @@
+// Compile-time-geometry versions of the exchange passes for cubic grids of edge N.
+//
+// Same algorithm and the same in-place DIF/DIT stage order as the runtime kernels in
+// hfx_kernels.cuh (so the digit-reversed storage order, and therefore the Coulomb table, are
+// identical), but every length, stride, radix and loop trip count is a constant: butterfly
+// element offsets become immediate offsets, divisions by constants become multiply-shifts, and
+// each stage reads its twiddles from its own [m][r] table (w_L^{j1 k}), one row per butterfly.
+#pragma once
+#include "hfx_kernels.cuh"
+
+namespace hfx {
+namespace ct {
+
+template <int N> struct Plan { static constexpr StagePlan p = stage_plan(N); };
+
+// one in-place stage over LINES lines (element e of line l at buf[l*LS + e*ES])
+template <int R, int M, bool INV, int LINES, int LS, int ES, int N, int NT, typename C>
+__device__ __forceinline__ void stage(C* __restrict__ buf, const C* __restrict__ twt) {
+  constexpr int NQ = N / R;
+  constexpr int TOTAL = LINES * NQ;
+  constexpr int STEP = M * ES;
+  constexpr int ITERS = (TOTAL + NT - 1) / NT;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int id = threadIdx.x + it * NT;
+    if ((TOTAL % NT) != 0 && id >= TOTAL) break;
+    const int q = id / LINES;
+    const int line = id - q * LINES;
+    const int j1 = q % M;
+    C* p = buf + line * LS + ((q - j1) * R + j1) * ES;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = p[k * STEP];
+    if constexpr (!INV) {
+      Dft<R, -1, C>::run(v);
+      if constexpr (M > 1) {
+        const C* t = twt + j1 * R;
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t[k]);
+      }
+    } else {
+      if constexpr (M > 1) {
+        const C* t = twt + j1 * R;
+#pragma unroll
+        for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], t[k]);
+      }
+      Dft<R, 1, C>::run(v);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) p[k * STEP] = v[k];
+  }
+}
+
+// forward stages S0 .. S1-1, or inverse stages S1-1 .. S0; a barrier after each
+template <int N, bool INV, int S0, int S1, int LINES, int LS, int ES, int NT, typename C>
+__device__ __forceinline__ void stages(C* buf, const C* tw) {
+  constexpr StagePlan P = Plan<N>::p;
+  if constexpr (S0 < S1) {
+    if constexpr (!INV) {
+      stage<P.r[S0], P.m[S0], false, LINES, LS, ES, N, NT>(buf, tw + P.twoff[S0]);
+      __syncthreads();
+      stages<N, false, S0 + 1, S1, LINES, LS, ES, NT>(buf, tw);
+    } else {
+      stage<P.r[S1 - 1], P.m[S1 - 1], true, LINES, LS, ES, N, NT>(buf, tw + P.twoff[S1 - 1]);
+      __syncthreads();
+      stages<N, true, S0, S1 - 1, LINES, LS, ES, NT>(buf, tw);
+    }
+  }
+}
+
+template <typename T> struct Two;  // two consecutive reals
+template <> struct Two<float> { using type = float2; };
+template <> struct Two<double> { using type = double2; };
+
+// store two consecutive complex values (16 or 32 bytes) to global memory
+__device__ __forceinline__ void st2(float2* dst, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(dst) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void st2(double2* dst, double2 a, double2 b) { dst[0] = a; dst[1] = b; }
+__device__ __forceinline__ void ld2(const float2* src, float2& a, float2& b) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+  a = make_float2(v.x, v.y);
+  b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ld2(const double2* src, double2& a, double2& b) {
+  a = __ldg(src);
+  b = __ldg(src + 1);
+}
+
+constexpr int kUnroll = 4;
+
+// ----------------------------------------------------------------------------------
+// pass 1: pair product + forward FFT along z and y of one x-plane
+// ----------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreadsPlane, 3)
+k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples, int c0, int c1,
+            cx<T>* __restrict__ W, const cx<T>* __restrict__ twg) {
+  using C = cx<T>;
+  using T2 = typename Two<T>::type;
+  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr StagePlan P = Plan<N>::p;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw = buf + N * S;
+  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
+
+  const int items = (c1 - c0) * N;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = it / N;
+    const int x = it - cl * N;
+    const int4 cp = couples[c0 + cl];
+    if (couple_empty(cp)) continue;
+    const long long off = (long long)x * PLANE;
+    const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+    const T2* pa1 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.x : 0) * Ntot + off);
+    const T2* pa2 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.y : 0) * Ntot + off);
+    const T2* pb1 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.z : 0) * Ntot + off);
+    const T2* pb2 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.w : 0) * Ntot + off);
+    __syncthreads();  // the previous item's store is done with buf (and the table is loaded)
+    for (int i0 = threadIdx.x; i0 < NV; i0 += kUnroll * NT) {
+      T2 a1[kUnroll], a2[kUnroll], b1[kUnroll], b2[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * NT;
+        const bool in = (NV % (kUnroll * NT) == 0) || i < NV;
+        const T2 zero = {};
+        a1[u] = (in && hasa) ? __ldg(pa1 + i) : zero;
+        a2[u] = (in && hasa) ? __ldg(pa2 + i) : zero;
+        b1[u] = (in && hasb) ? __ldg(pb1 + i) : zero;
+        b2[u] = (in && hasb) ? __ldg(pb2 + i) : zero;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * NT;
+        if ((NV % (kUnroll * NT) == 0) || i < NV) {
+          const int p = 2 * i;
+          const int y = p / N, z = p - y * N;  // N even: both points in row y
+          buf[y * S + z] = mk<C>(a1[u].x * a2[u].x, b1[u].x * b2[u].x);
+          buf[y * S + z + 1] = mk<C>(a1[u].y * a2[u].y, b1[u].y * b2[u].y);
+        }
+      }
+    }
+    __syncthreads();
+    stages<N, false, 0, P.ns, N, S, 1, NT>(buf, tw);  // z: N rows
+    stages<N, false, 0, P.ns, N, 1, S, NT>(buf, tw);  // y: N columns
+    C* dst = W + ((long long)cl * N + x) * PLANE;
+    for (int i = threadIdx.x; i < NV; i += NT) {
+      const int p = 2 * i;
+      const int y = p / N, z = p - y * N;
+      st2(dst + p, buf[y * S + z], buf[y * S + z + 1]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// pass 2: forward FFT along x, Coulomb multiply + energy, inverse along x and z
+// ----------------------------------------------------------------------------------
+template <typename T, int N>
+__global__ void __launch_bounds__(kThreadsPlane, 3)
+k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
+               const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only) {
+  using C = cx<T>;
+  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr StagePlan P = Plan<N>::p;
+  constexpr int RL = P.r[P.ns - 1];  // last forward stage (m = 1)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw = buf + N * S;
+  __shared__ double red[32];
+  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
+
+  const int items = (c1 - c0) * N;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = it / N;
+    const int y = it - cl * N;
+    if (couple_empty(couples[c0 + cl])) continue;
+    C* wc = W + (long long)cl * N * PLANE + (long long)y * N;
+    __syncthreads();
+    // rows x of the tile: W[cl][x][y][:]
+    for (int i0 = threadIdx.x; i0 < NV; i0 += kUnroll * NT) {
+      C u0[kUnroll], u1[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * NT;
+        if ((NV % (kUnroll * NT) == 0) || i < NV) {
+          const int p = 2 * i;
+          const int xx = p / N, z = p - xx * N;
+          ld2(wc + (long long)xx * PLANE + z, u0[u], u1[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int i = i0 + u * NT;
+        if ((NV % (kUnroll * NT) == 0) || i < NV) {
+          const int p = 2 * i;
+          const int xx = p / N, z = p - xx * N;
+          buf[xx * S + z] = u0[u];
+          buf[xx * S + z + 1] = u1[u];
+        }
+      }
+    }
+    __syncthreads();
+    stages<N, false, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // x: N columns, all but the last stage
+    // last forward x stage (no twiddles) + Coulomb + energy + first inverse x stage
+    double e_acc = 0.0;
+    {
+      constexpr int TOTAL = N * (N / RL);
+      const T* vy = vtab + (long long)y * N;
+#pragma unroll 1
+      for (int id = threadIdx.x; id < TOTAL; id += NT) {
+        const int q = id / N, z = id - q * N;
+        C* p = buf + q * RL * S + z;
+        T vg[RL];
+#pragma unroll
+        for (int k = 0; k < RL; ++k) vg[k] = __ldg(vy + (long long)(q * RL + k) * PLANE + z);
+        C v[RL];
+#pragma unroll
+        for (int k = 0; k < RL; ++k) v[k] = p[k * S];
+        Dft<RL, -1, C>::run(v);
+        T e = T(0);
+#pragma unroll
+        for (int k = 0; k < RL; ++k) {
+          e += vg[k] * (v[k].x * v[k].x + v[k].y * v[k].y);
+          v[k].x *= vg[k];
+          v[k].y *= vg[k];
+        }
+        e_acc += double(e);
+        if (!energy_only) {
+          Dft<RL, 1, C>::run(v);
+#pragma unroll
+          for (int k = 0; k < RL; ++k) p[k * S] = v[k];
+        }
+      }
+    }
+    const double es = block_sum(e_acc, red);
+    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = es;
+    if (energy_only) continue;
+    __syncthreads();
+    stages<N, true, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // x inverse, remaining stages
+    stages<N, true, 0, P.ns, N, S, 1, NT>(buf, tw);      // z inverse: N rows
+    for (int i = threadIdx.x; i < NV; i += NT) {
+      const int p = 2 * i;
+      const int xx = p / N, z = p - xx * N;
+      st2(wc + (long long)xx * PLANE + z, buf[xx * S + z], buf[xx * S + z + 1]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// pass 3a with compile-time geometry: see k_y_acc_dense
+// ----------------------------------------------------------------------------------
+template <typename T, int N> struct DenseGeo {
+  static constexpr int ZC = ZChunk<T>::value;
+  static constexpr int PTS = N * ZC;
+  static constexpr int NP = (PTS + 319) / 320;                      // points per thread
+  static constexpr int NT = ((PTS + NP - 1) / NP + 31) / 32 * 32;   // threads
+};
+
+template <typename T, int N, int B>
+__global__ void __launch_bounds__(DenseGeo<T, N>::NT, 2)
+k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
+                 const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
+                 const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
+                 const cx<T>* __restrict__ twg, double* __restrict__ V, double vscale) {
+  using C = cx<T>;
+  using G = DenseGeo<T, N>;
+  constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
+  constexpr int HB = B / 2;
+  constexpr int LN = HB * ZC;
+  constexpr int PER = 16 / int(sizeof(C));
+  constexpr int PLANE = N * N;
+  constexpr StagePlan P = Plan<N>::p;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int z0 = blockIdx.x * ZC;
+  const int zcn = min(ZC, N - z0);
+  const int x = blockIdx.y;
+  const int slot = slot_list[blockIdx.z];
+  C* tiles = reinterpret_cast<C*>(smem_raw);  // kDenseRing x [N][LN]
+  C* tw = tiles + kDenseRing * N * LN;
+  T* phiI = reinterpret_cast<T*>(tw + P.twtotal);  // [B][PTS]
+  T* accI = phiI + B * PTS;                         // [B][PTS]
+
+  const int2 blk = slot_blocks[slot];
+  const int I0 = blk.x * B, J0 = blk.y * B;
+  const int cs = slot_couple_base[slot];
+  const long long rowoff = (long long)x * PLANE + z0;
+
+  auto issue_row = [&](int r) {
+    if (r >= B) { cp_async_commit(); return; }
+    C* dstb = tiles + (r % kDenseRing) * N * LN;
+    constexpr int VPR = ZC / PER;
+    for (int i = threadIdx.x; i < HB * N * VPR; i += NT) {
+      const int v = i % VPR;
+      const int rest = i / VPR;
+      const int t = rest % HB, y = rest / HB;
+      const int c = cs + r * HB + t;
+      const bool live = !couple_empty(couples[c]) && v * PER < zcn;
+      const C* src = W + ((long long)(c - c0) * N + x) * PLANE + (long long)y * N + z0 + v * PER;
+      cp_async16(dstb + y * LN + t * ZC + v * PER, live ? (const void*)src : (const void*)W, live ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int r = 0; r < kDenseRing - 1; ++r) issue_row(r);
+
+  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < B * PTS; i += NT) {
+    const int o = i / PTS, p = i - o * PTS;
+    const int y = p / ZC, zz = p - y * ZC;
+    phiI[i] = zz < zcn ? __ldg(orb + (long long)(I0 + o) * Ntot + rowoff + (long long)y * N + zz) : T(0);
+  }
+
+  long long goff[NP];
+  bool ok[NP];
+  T phiJ[NP][B], accJ[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int p = threadIdx.x + k * NT;
+    const int y = p / ZC, zz = p - y * ZC;
+    ok[k] = p < PTS && zz < zcn;
+    goff[k] = rowoff + (long long)y * N + zz;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      phiJ[k][j] = ok[k] ? __ldg(orb + (long long)(J0 + j) * Ntot + goff[k]) : T(0);
+      accJ[k][j] = T(0);
+    }
+  }
+
+  for (int r = 0; r < B; ++r) {
+    issue_row(r + kDenseRing - 1);
+    cp_async_wait<kDenseRing - 1>();
+    __syncthreads();
+    C* buf = tiles + (r % kDenseRing) * N * LN;
+    stages<N, true, 0, P.ns, LN, 1, LN, NT>(buf, tw);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = threadIdx.x + k * NT;
+      if (!ok[k]) continue;
+      const int y = p / ZC, zz = p - y * ZC;
+      const C* vp = buf + y * LN + zz;
+      const T phii = phiI[r * PTS + p];
+      T acci = T(0);
+#pragma unroll
+      for (int t = 0; t < HB; ++t) {
+        const C v = vp[t * ZC];
+        acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
+        accJ[k][2 * t] += v.x * phii;
+        accJ[k][2 * t + 1] += v.y * phii;
+      }
+      accI[r * PTS + p] = acci;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+    const int p = threadIdx.x + k * NT;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      double* dst = V + (long long)(J0 + j) * Ntot + goff[k];
+      *dst += vscale * double(accJ[k][j]);
+    }
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      double* dst = V + (long long)(I0 + j) * Ntot + goff[k];
+      *dst += vscale * double(accI[j * PTS + p]);
+    }
+  }
+}
+
+}  // namespace ct
+}  // namespace hfx

@@ -30,3 +30,39 @@ struct Passes {
 };
 
 }  // namespace hfx
+
+namespace hfx {
+
+// Compile-time-geometry FP32 passes for cubic grids of edge N (hfx_ct.cuh), one translation unit
+// per N; ct_fns(N) returns NULL for an edge without one.
+struct CtFns {
+  int n;
+  int dense_threads;                    // threads per block of the dense accumulation pass (B = 8)
+  cudaError_t (*prepare)(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x);
+  void (*fwd_yz)(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
+                 int c0, int c1, float2* W, const float2* tw);
+  void (*x_coulomb)(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
+                    const float* vtab, const float2* tw, double* epart, int energy_only);
+  void (*y_acc_dense)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
+                      const int4* couples, const int* slot_list, const int* slot_couple_base,
+                      const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
+};
+
+#define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128)
+#define HFX_CT_DECLARE(NN) const CtFns* ct_fns_##NN();
+HFX_CT_SIZES(HFX_CT_DECLARE)
+#undef HFX_CT_DECLARE
+
+inline const CtFns* ct_fns(int n) {
+  switch (n) {
+#define HFX_CT_CASE(NN) \
+  case NN:              \
+    return ct_fns_##NN();
+    HFX_CT_SIZES(HFX_CT_CASE)
+#undef HFX_CT_CASE
+    default:
+      return nullptr;
+  }
+}
+
+}  // namespace hfx

@@ -19,10 +19,9 @@
 #include <stdint.h>
 
 #include "fft_codelets.cuh"
+#include "fft_plan.h"
 
 namespace hfx {
-
-constexpr int kMaxStages = 8;
 
 // Division by a fixed divisor d < 2^16 for dividends x < 2^16: q = floor(x * ceil(2^32/d) / 2^32).
 // The product's error is below x / 2^32 < 2^-16 < 1/d, so the floor is exact.

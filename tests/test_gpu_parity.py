@@ -216,6 +216,22 @@ def test_large_tile_sparse_block_pair():
         assert rel(V, V_ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("n", [48, 64])
+@pytest.mark.parametrize("no_ct", ["0", "1"])
+def test_compile_time_and_runtime_kernels(n, no_ct, monkeypatch):
+    """FP32 cubic grids with an instantiated edge use compile-time-geometry kernels; HFX_NO_CT=1
+    forces the runtime kernels. Both must match the oracle."""
+    monkeypatch.setenv("HFX_NO_CT", no_ct)
+    L, n_orb = 0.4 * n, 18
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=n + 1, frac=0.2)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, "fp32")
+    assert abs(E - E_ref) <= 1e-6 * abs(E_ref)
+    assert rel(V, V_ref) <= 1e-6
+
+
 def test_bad_pairs_are_reported_and_skipped():
     from paper_2309_00651_gb300 import hfx
     n, L, n_orb = 16, 8.0, 6
