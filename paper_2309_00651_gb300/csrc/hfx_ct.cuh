@@ -68,6 +68,85 @@ __device__ __forceinline__ void stages(C* buf, const C* tw) {
   }
 }
 
+// forward stage 0 of column lines reading its input from global memory: line l's element e at
+// src[l + e*GES]; results go to buf[l*SLS + e*SES].  A barrier follows.
+template <int R, int M, int LINES, int GES, int SLS, int SES, int N, int NT, typename C>
+__device__ __forceinline__ void stage_fwd_g2s(const C* __restrict__ src, C* __restrict__ buf,
+                                              const C* __restrict__ twt) {
+  constexpr int TOTAL = LINES * (N / R);
+  constexpr int ITERS = (TOTAL + NT - 1) / NT;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int id = threadIdx.x + it * NT;
+    if ((TOTAL % NT) != 0 && id >= TOTAL) break;
+    const int q = id / LINES;
+    const int line = id - q * LINES;
+    const int j1 = q % M;
+    const int e0 = (q - j1) * R + j1;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = __ldg(src + line + (e0 + k * M) * GES);
+    Dft<R, -1, C>::run(v);
+    if constexpr (M > 1) {
+      const C* t = twt + j1 * R;
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) buf[line * SLS + (e0 + k * M) * SES] = v[k];
+  }
+  __syncthreads();
+}
+
+// last forward stage (m = 1, no twiddles) of column lines writing its output to global memory
+template <int R, int LINES, int SLS, int SES, int GES, int N, int NT, typename C>
+__device__ __forceinline__ void stage_fwd_last_s2g(const C* __restrict__ buf, C* __restrict__ dst) {
+  constexpr int TOTAL = LINES * (N / R);
+  constexpr int ITERS = (TOTAL + NT - 1) / NT;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int id = threadIdx.x + it * NT;
+    if ((TOTAL % NT) != 0 && id >= TOTAL) break;
+    const int q = id / LINES;
+    const int line = id - q * LINES;
+    const int e0 = q * R;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = buf[line * SLS + (e0 + k) * SES];
+    Dft<R, -1, C>::run(v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) dst[line + (e0 + k) * GES] = v[k];
+  }
+}
+
+// inverse stage 0 (the last one applied) of column lines writing its output to global memory
+template <int R, int M, int LINES, int SLS, int SES, int GES, int N, int NT, typename C>
+__device__ __forceinline__ void stage_inv_s2g(const C* __restrict__ buf, C* __restrict__ dst,
+                                              const C* __restrict__ twt) {
+  constexpr int TOTAL = LINES * (N / R);
+  constexpr int ITERS = (TOTAL + NT - 1) / NT;
+#pragma unroll 1
+  for (int it = 0; it < ITERS; ++it) {
+    const int id = threadIdx.x + it * NT;
+    if ((TOTAL % NT) != 0 && id >= TOTAL) break;
+    const int q = id / LINES;
+    const int line = id - q * LINES;
+    const int j1 = q % M;
+    const int e0 = (q - j1) * R + j1;
+    C v[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = buf[line * SLS + (e0 + k * M) * SES];
+    if constexpr (M > 1) {
+      const C* t = twt + j1 * R;
+#pragma unroll
+      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], t[k]);
+    }
+    Dft<R, 1, C>::run(v);
+#pragma unroll
+    for (int k = 0; k < R; ++k) dst[line + (e0 + k * M) * GES] = v[k];
+  }
+}
+
 template <typename T> struct Two;  // two consecutive reals
 template <> struct Two<float> { using type = float2; };
 template <> struct Two<double> { using type = double2; };
@@ -142,14 +221,10 @@ k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ 
       }
     }
     __syncthreads();
-    stages<N, false, 0, P.ns, N, S, 1, NT>(buf, tw);  // z: N rows
-    stages<N, false, 0, P.ns, N, 1, S, NT>(buf, tw);  // y: N columns
-    C* dst = W + ((long long)cl * N + x) * PLANE;
-    for (int i = threadIdx.x; i < NV; i += NT) {
-      const int p = 2 * i;
-      const int y = p / N, z = p - y * N;
-      st2(dst + p, buf[y * S + z], buf[y * S + z + 1]);
-    }
+    stages<N, false, 0, P.ns, N, S, 1, NT>(buf, tw);      // z: N rows
+    stages<N, false, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // y: N columns, all but the last stage
+    // last y stage straight to W[cl][x][y][z] (consecutive threads on consecutive z)
+    stage_fwd_last_s2g<P.r[P.ns - 1], N, 1, S, N, N, NT>(buf, W + ((long long)cl * N + x) * PLANE);
   }
 }
 
@@ -164,6 +239,7 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
   constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
   constexpr StagePlan P = Plan<N>::p;
   constexpr int RL = P.r[P.ns - 1];  // last forward stage (m = 1)
+  static_assert(P.ns >= 2, "compile-time x pass needs at least two stages");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
@@ -177,31 +253,9 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
     if (couple_empty(couples[c0 + cl])) continue;
     C* wc = W + (long long)cl * N * PLANE + (long long)y * N;
     __syncthreads();
-    // rows x of the tile: W[cl][x][y][:]
-    for (int i0 = threadIdx.x; i0 < NV; i0 += kUnroll * NT) {
-      C u0[kUnroll], u1[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * NT;
-        if ((NV % (kUnroll * NT) == 0) || i < NV) {
-          const int p = 2 * i;
-          const int xx = p / N, z = p - xx * N;
-          ld2(wc + (long long)xx * PLANE + z, u0[u], u1[u]);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * NT;
-        if ((NV % (kUnroll * NT) == 0) || i < NV) {
-          const int p = 2 * i;
-          const int xx = p / N, z = p - xx * N;
-          buf[xx * S + z] = u0[u];
-          buf[xx * S + z + 1] = u1[u];
-        }
-      }
-    }
-    __syncthreads();
-    stages<N, false, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // x: N columns, all but the last stage
+    // x stage 0 straight from W[cl][x][y][z] (line z, element x at stride PLANE)
+    stage_fwd_g2s<P.r[0], P.m[0], N, PLANE, 1, S, N, NT>(wc, buf, tw + P.twoff[0]);
+    stages<N, false, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // remaining x stages but the last
     // last forward x stage (no twiddles) + Coulomb + energy + first inverse x stage
     double e_acc = 0.0;
     {
@@ -237,13 +291,11 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
     if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = es;
     if (energy_only) continue;
     __syncthreads();
-    stages<N, true, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // x inverse, remaining stages
+    // inverse transforms along different axes commute: z first (rows), then the remaining x
+    // stages, the last of which writes W directly
     stages<N, true, 0, P.ns, N, S, 1, NT>(buf, tw);      // z inverse: N rows
-    for (int i = threadIdx.x; i < NV; i += NT) {
-      const int p = 2 * i;
-      const int xx = p / N, z = p - xx * N;
-      st2(wc + (long long)xx * PLANE + z, buf[xx * S + z], buf[xx * S + z + 1]);
-    }
+    stages<N, true, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // x inverse stages ns-2 .. 1
+    stage_inv_s2g<P.r[0], P.m[0], N, 1, S, PLANE, N, NT>(buf, wc, tw + P.twoff[0]);
   }
 }
 
@@ -286,6 +338,35 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   const int cs = slot_couple_base[slot];
   const long long rowoff = (long long)x * PLANE + z0;
 
+  // which couples of the block pair hold pairs (bit t of the mask: couple cs + t)
+  static_assert(B * HB <= 32, "one mask word per block pair");
+  __shared__ unsigned live_mask;
+  if (threadIdx.x < 32) {
+    const unsigned m = __ballot_sync(0xffffffffu, threadIdx.x < B * HB && !couple_empty(couples[cs + threadIdx.x]));
+    if (threadIdx.x == 0) live_mask = m;
+  }
+  __syncthreads();
+  const unsigned live = live_mask;
+
+  // phi_I (kept) and phi_J (staged in the accI area until it moves to registers) tiles, rows of
+  // ZC reals; they join the first copy group
+  {
+    constexpr int RPER = 16 / int(sizeof(T));  // reals per 16-byte copy
+    constexpr int VPR = ZC / RPER;
+    for (int i = threadIdx.x; i < 2 * B * N * VPR; i += NT) {
+      const int v = i % VPR;
+      const int rest = i / VPR;
+      const int y = rest % N;
+      const int oo = rest / N;  // 0..2B-1: I block then J block
+      const int o = oo < B ? I0 + oo : J0 + (oo - B);
+      T* dst = (oo < B ? phiI + oo * PTS : accI + (oo - B) * PTS) + y * ZC + v * RPER;
+      const int valid = zcn - v * RPER;
+      const int bytes = valid >= RPER ? 16 : (valid > 0 ? valid * int(sizeof(T)) : 0);
+      const T* src = orb + (long long)o * Ntot + rowoff + (long long)y * N + v * RPER;
+      cp_async16(dst, bytes ? (const void*)src : (const void*)orb, bytes);
+    }
+  }
+
   auto issue_row = [&](int r) {
     if (r >= B) { cp_async_commit(); return; }
     C* dstb = tiles + (r % kDenseRing) * N * LN;
@@ -295,9 +376,9 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
       const int rest = i / VPR;
       const int t = rest % HB, y = rest / HB;
       const int c = cs + r * HB + t;
-      const bool live = !couple_empty(couples[c]) && v * PER < zcn;
+      const bool ok_c = ((live >> (r * HB + t)) & 1u) && v * PER < zcn;
       const C* src = W + ((long long)(c - c0) * N + x) * PLANE + (long long)y * N + z0 + v * PER;
-      cp_async16(dstb + y * LN + t * ZC + v * PER, live ? (const void*)src : (const void*)W, live ? 16 : 0);
+      cp_async16(dstb + y * LN + t * ZC + v * PER, ok_c ? (const void*)src : (const void*)W, ok_c ? 16 : 0);
     }
     cp_async_commit();
   };
@@ -305,11 +386,6 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   for (int r = 0; r < kDenseRing - 1; ++r) issue_row(r);
 
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < B * PTS; i += NT) {
-    const int o = i / PTS, p = i - o * PTS;
-    const int y = p / ZC, zz = p - y * ZC;
-    phiI[i] = zz < zcn ? __ldg(orb + (long long)(I0 + o) * Ntot + rowoff + (long long)y * N + zz) : T(0);
-  }
 
   long long goff[NP];
   bool ok[NP];
@@ -321,16 +397,22 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     ok[k] = p < PTS && zz < zcn;
     goff[k] = rowoff + (long long)y * N + zz;
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      phiJ[k][j] = ok[k] ? __ldg(orb + (long long)(J0 + j) * Ntot + goff[k]) : T(0);
-      accJ[k][j] = T(0);
-    }
+    for (int j = 0; j < B; ++j) accJ[k][j] = T(0);
   }
 
   for (int r = 0; r < B; ++r) {
     issue_row(r + kDenseRing - 1);
     cp_async_wait<kDenseRing - 1>();
     __syncthreads();
+    if (r == 0) {
+      // phi_J to registers (the staging area becomes accI after the barriers of the first row)
+#pragma unroll
+      for (int k = 0; k < NP; ++k) {
+        const int p = threadIdx.x + k * NT;
+#pragma unroll
+        for (int j = 0; j < B; ++j) phiJ[k][j] = ok[k] ? accI[j * PTS + p] : T(0);
+      }
+    }
     C* buf = tiles + (r % kDenseRing) * N * LN;
     stages<N, true, 0, P.ns, LN, 1, LN, NT>(buf, tw);
 #pragma unroll
