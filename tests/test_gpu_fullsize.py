@@ -1,0 +1,99 @@
+"""Full-size workloads, in the launch configuration bench.py times, checked on sampled outputs.
+
+* water32_n72 (128 orbitals, 72^3, all 8256 pairs) and water64_n96 (256 orbitals, 96^3, all
+  32896 pairs): the full call on both precision paths; the oracle recomputes, one by one,
+  (V_x phi)_k for sampled orbitals k (from every listed pair that contains k) and E_x over a
+  seeded sample of pairs, which the GPU evaluates as its own pair list.  Properties that hold at
+  any size are checked on the full result: the homogeneity identity E_x = 1/2 (Omega/N) sum
+  <phi_i, (V_x phi)_i>, and agreement between the FP32 and FP64 paths.
+* The uneven batch (independent water boxes of 32..256 orbitals on 48^3..96^3 grids) through
+  hfx_apply_batched: every problem checked on a sampled orbital row and on homogeneity.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hfx_oracle as O  # noqa: E402
+from paper_2309_00651_gb300 import inputs as I  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-8, "fp32": 1e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_00651_gb300 import build
+    build.build()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+@pytest.mark.parametrize("name,rows,n_sample", [("water32_n72", (5, 77), 48), ("water64_n96", (130,), 24)])
+def test_full_workload_sampled(name, rows, n_sample):
+    from paper_2309_00651_gb300 import hfx
+    w = I.WORKLOADS[name]
+    phi, pairs, _ = I.make_workload(w)
+    phi_d = torch.from_numpy(phi).cuda()
+    pairs_d = torch.from_numpy(pairs).cuda()
+    N = w.n ** 3
+    # oracle references, once: sampled rows of V_x phi and E_x over a seeded sample of pairs
+    V_rows = O.exchange_rows(phi, pairs, rows, w.lattice)
+    sub = I.random_pairs_subset(pairs, n_sample, seed=11)
+    E_ref, _ = O.exchange(phi, sub, w.lattice, want_v=False)
+    results = {}
+    for prec in ("fp32", "fp64"):
+        ex = hfx.Exchange(w.lattice, w.grid, precision=prec)
+        E, V = ex.apply(phi_d, pairs_d)
+        ex.sync_status()
+        Ef = E.item()
+        # homogeneity identity on the full result
+        hom = 0.5 * (w.volume / N) * float(torch.sum(phi_d * V).item())
+        assert abs(hom - Ef) <= 10 * TOL[prec] * abs(Ef)
+        for r, k in enumerate(rows):
+            assert rel(V[k].cpu().numpy(), V_rows[r]) <= TOL[prec]
+        # the sampled pairs as the GPU's own pair list
+        Es, _ = ex.apply(phi_d, torch.from_numpy(sub).cuda(), energy_only=True)
+        assert abs(Es.item() - E_ref) <= TOL[prec] * abs(E_ref)
+        results[prec] = (Ef, V.cpu().numpy())
+        ex.close()
+    # the two precision paths agree to the FP32 tolerance
+    assert abs(results["fp32"][0] - results["fp64"][0]) <= 1e-6 * abs(results["fp64"][0])
+    assert rel(results["fp32"][1], results["fp64"][1]) <= 1e-6
+
+
+def test_uneven_batch_through_apply_batched():
+    from paper_2309_00651_gb300 import hfx
+    ws = I.batched_workloads()
+    # the smallest, the largest and three in between keep the oracle checks to seconds
+    order = np.argsort([w.n_orb * w.n ** 3 for w in ws])
+    pick = [ws[i] for i in (order[0], order[6], order[12], order[18], order[-1])]
+    ctxs, args, keep, data = [], [], [], []
+    for w in pick:
+        phi, pairs, _ = I.make_workload(w)
+        ex = hfx.Exchange(w.lattice, w.grid, precision="fp32")
+        ex.ensure_workspace(w.n_orb, len(pairs))
+        phi_d = torch.from_numpy(phi).cuda()
+        pairs_d = torch.from_numpy(pairs).cuda()
+        E = torch.zeros(1, dtype=torch.float64, device="cuda")
+        V = torch.empty_like(phi_d)
+        ctxs.append(ex.ctx)
+        args.append((phi_d, pairs_d, E, V, 0))
+        keep.append(ex)
+        data.append((w, phi, pairs))
+    hfx.hfx_apply_batched(ctxs, args)
+    torch.cuda.synchronize()
+    for (w, phi, pairs), (phi_d, _, E, V, _), ex in zip(data, args, keep):
+        ex.sync_status()
+        N = w.n ** 3
+        hom = 0.5 * (w.volume / N) * float(torch.sum(phi_d * V).item())
+        assert abs(hom - E.item()) <= 1e-5 * abs(E.item())
+        k = w.n_orb // 3
+        V_row = O.exchange_rows(phi, pairs, [k], w.lattice)[0]
+        assert rel(V[k].cpu().numpy(), V_row) <= 1e-6
+        ex.close()
