@@ -434,20 +434,30 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     }
     __syncthreads();
   }
+  // flush, FP64 read-modify-write of V_J (registers) and V_I (shared memory): every load is issued
+  // before any store (a store could alias a later load, which would serialise the round trips)
+  double old[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * Ntot + goff[k]) : 0.0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+#pragma unroll
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + vscale * double(accJ[k][j]);
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : 0.0;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
     const int p = threadIdx.x + k * NT;
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      double* dst = V + (long long)(J0 + j) * Ntot + goff[k];
-      *dst += vscale * double(accJ[k][j]);
-    }
-#pragma unroll
-    for (int j = 0; j < B; ++j) {
-      double* dst = V + (long long)(I0 + j) * Ntot + goff[k];
-      *dst += vscale * double(accI[j * PTS + p]);
-    }
+    for (int j = 0; j < B; ++j)
+      V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vscale * double(accI[j * PTS + p]);
   }
 }
 

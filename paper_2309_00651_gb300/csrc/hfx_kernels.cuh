@@ -486,20 +486,30 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
     }
     __syncthreads();  // buffer r % kDenseRing is refilled by the copies issued in the next iteration
   }
-  // flush, FP64 read-modify-write: V_J from registers, V_I from shared memory
+  // flush, FP64 read-modify-write: V_J from registers, V_I from shared memory; all loads first
+  // (a store could alias a later load, which would serialise the round trips)
+  double old[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * g.N + goff[k]) : 0.0;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      double* dst = V + (long long)(J0 + j) * g.N + goff[k];
-      *dst += vscale * double(accJ[k][j]);
-    }
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * g.N + goff[k]] = old[k][j] + vscale * double(accJ[k][j]);
+  }
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      double* dst = V + (long long)(I0 + j) * g.N + goff[k];
-      *dst += vscale * double(accI[j * pts + pp[k]]);
-    }
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * g.N + goff[k]) : 0.0;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+    const int p = pp[k];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      V[(long long)(I0 + j) * g.N + goff[k]] = old[k][j] + vscale * double(accI[j * pts + p]);
   }
 }
 
@@ -629,15 +639,27 @@ k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const 
     y_last_acc_rt(dy.r[0], buf, tw2, dy.m[0], zcdiv, zcn, acc, tile_pts, orb, g.N, rowoff, n3, cp, ac);
   }
   __syncthreads();
-  // flush: V[o][x][y][z0 + zz] += vscale * acc
-  for (int i = threadIdx.x; i < nloc * tile_pts; i += blockDim.x) {
-    const int lo = i / tile_pts;
-    const int p = i - lo * tile_pts;
-    const int yy = p / ZC, zz = p - yy * ZC;
-    if (zz >= zcn) continue;
-    const int o = (lo < ac.ni) ? ac.i0 + lo : ac.j0 + (lo - ac.ni);
-    double* dst = V + (long long)o * g.N + rowoff + (long long)yy * n3 + zz;
-    *dst += vscale * double(acc[i]);
+  // flush: V[o][x][y][z0 + zz] += vscale * acc, in groups whose loads all precede their stores
+  constexpr int G = 8;
+  const int total = nloc * tile_pts;
+  for (int i0 = threadIdx.x; i0 < total; i0 += G * blockDim.x) {
+    double old[G];
+    long long off[G];
+    bool on[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int i = i0 + u * blockDim.x;
+      const int lo = i / tile_pts;
+      const int p = i - lo * tile_pts;
+      const int yy = p / ZC, zz = p - yy * ZC;
+      on[u] = i < total && zz < zcn;
+      const int o = (lo < ac.ni) ? ac.i0 + lo : ac.j0 + (lo - ac.ni);
+      off[u] = (long long)o * g.N + rowoff + (long long)yy * n3 + zz;
+      old[u] = on[u] ? __ldcg(V + off[u]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < G; ++u)
+      if (on[u]) V[off[u]] = old[u] + vscale * double(acc[i0 + u * blockDim.x]);
   }
 }
 
