@@ -247,27 +247,34 @@ def main():
     ms_step = ms_total / args.steps
     value = world * P * args.steps / (ms_total / 1000.0)
 
-    # roofline of the dominant pass (largest device time), algorithmic bytes per couple:
+    # roofline of the dominant kernel (largest device time), algorithmic bytes per couple:
     #   fwd_yz writes the packed transform (8 N B per couple, FP32 complex);
-    #   x_coulomb reads and writes it (16 N B); y_inv_acc reads it (8 N B).
+    #   x_coulomb reads and writes it (16 N B); the accumulate passes read it (8 N B).
     csize = 8 if args.precision == "fp32" else 16
-    per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_inv_acc": csize * N}
-    n_couples_total = stats["couples"]  # packed complex transforms per call (full list: every block pair full)
+    per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_acc_dense": csize * N,
+                  "y_acc_generic": csize * N}
+    # couples handled by each kernel per call (full pair list: every block pair full)
+    couples_of = {"fwd_yz": stats["couples"], "x_coulomb": stats["couples"],
+                  "y_acc_dense": stats["dense_couples"], "y_acc_generic": stats["couples"] - stats["dense_couples"]}
     dom = max(per_couple, key=lambda k: prof[k]["ms"])
     launches = max(1, prof[dom]["launches"])
     avg_ms = prof[dom]["ms"] / launches
-    couples_per_launch = n_couples_total * args.steps / launches
+    couples_per_launch = couples_of[dom] * args.steps / launches
     alg_bytes = per_couple[dom] * couples_per_launch
     achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    # measured DRAM bytes per couple of this kernel (ncu, small case of the same grid; the traffic
+    # grows in proportion to the couples of a launch), valid only for the sources it was taken on
     traffic = None
-    prof_file = os.path.join(ROOT, "profiles", f"{dom}_{w.name}_{args.precision}.traffic.json")
+    prof_file = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof_file):
         try:
             with open(prof_file) as f:
                 tj = json.load(f)
-            if tj.get("kernel_source_hash") == B.source_hash():
-                traffic = tj.get("dram_bytes_per_launch")
+            ent = tj.get("kernels", {}).get(dom, {})
+            if tj.get("kernel_hash") == B.kernel_hash() and ent.get("grid") == w.n and \
+                    ent.get("precision") == args.precision:
+                traffic = ent["dram_bytes_per_couple"] * couples_per_launch
         except Exception:
             traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

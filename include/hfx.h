@@ -173,17 +173,19 @@ hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
  *   out[0] = kernel launches per call, out[1] = batches, out[2] = orbital block size,
  *   out[3] = largest number of packed pair couples (two pairs per complex 3D transform) held
  *   by one batch, out[4] = couples of the whole call when every block pair is full (the
- *   exact count for the complete pair list). */
-hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[5]);
+ *   exact count for the complete pair list), out[5] = the part of out[4] in full off-diagonal
+ *   block pairs (handled by the register-accumulating inverse-y pass). */
+hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[6]);
 
 /* hfx_profile_enable / hfx_profile_read -- per-pass device time.  While enabled, every
- * hfx_apply on the context records CUDA events around each pass on its own stream (pair
- * staging, forward yz-plane pass, x/Coulomb pass, inverse-y/accumulate pass, energy sum).
- * hfx_profile_read waits for the recorded events and returns, per pass (index 0..4 in that
- * order), the summed milliseconds and the number of launches since the last read, then
- * resets them.  Not for use inside stream capture. */
+ * hfx_apply on the context records CUDA events around each pass on its own stream.
+ * hfx_profile_read waits for the recorded events and returns, per pass, the summed
+ * milliseconds and the number of launches since the last read, then resets them; index
+ * 0 pair staging (and the FP32 orbital copy), 1 forward yz-plane pass, 2 x/Coulomb pass,
+ * 3 inverse-y/accumulate pass for full off-diagonal block pairs, 4 energy sum,
+ * 5 inverse-y/accumulate pass for the other block pairs.  Not for use inside stream capture. */
 hfx_status hfx_profile_enable(hfx_ctx* c, int on);
-hfx_status hfx_profile_read(hfx_ctx* c, double ms[5], int64_t launches[5]);
+hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]);
 
 /* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
  * thread's next libhfx call. */

@@ -46,6 +46,19 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+KERNEL_SOURCES = ("fft_codelets.cuh", "fft_plan.h", "hfx_kernels.cuh", "hfx_ct.cuh")
+
+
+def kernel_hash() -> str:
+    """Hash of the device-kernel sources only (the code whose hardware counters profiles/ records)."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _stamp() -> str:
     h = hashlib.sha256()
     for d in (CSRC, INCLUDE):

@@ -224,7 +224,7 @@ struct hfx_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
 };
 
-enum { kProfStage = 0, kProfFwd = 1, kProfX = 2, kProfAcc = 3, kProfEnergy = 4, kProfSlots = 5 };
+enum { kProfStage = 0, kProfFwd = 1, kProfX = 2, kProfAcc = 3, kProfEnergy = 4, kProfAccGeneric = 5, kProfSlots = 6 };
 
 static cudaEvent_t prof_event(hfx_ctx* c) {
   if (c->ev_pool.empty()) {
@@ -666,7 +666,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
       e0 = prof_mark(c, st);
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
-      if (nd > 0 && ct && S.b == 8)
+      if (nd > 0 && ct && S.b == 8)  // [dense block pairs]
         ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                         S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
                         (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
@@ -674,11 +674,13 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
         Passes<T>::y_acc_dense(g, dim3(nzc, g.n1, nd), dense_threads, smem_dense(c), st, S.b, orb, couples,
                                S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
                                (const C*)c->d_tw[1], vxphi, vscale);
+      if (nd > 0) prof_close(c, kProfAcc, e0, st);
+      e0 = prof_mark(c, st);
       if (ng > 0)
         Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
                                  S.d_generic_slots + S.generic_begin[b], S.d_slot_couple_base, S.d_slot_blocks, S.b,
                                  n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale);
-      prof_close(c, kProfAcc, e0, st);
+      if (ng > 0) prof_close(c, kProfAccGeneric, e0, st);
     }
   }
   return HFX_OK;
@@ -795,7 +797,7 @@ extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
   return HFX_OK;
 }
 
-extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[5]) {
+extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[6]) {
   g_last_error.clear();
   if (!c || !out || n_orb <= 0 || n_pairs < 0) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
   Schedule S = make_host_schedule(c, n_orb);
@@ -815,6 +817,9 @@ extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_
   out[2] = S.b;
   out[3] = S.max_batch_couples;
   out[4] = S.max_total_couples;
+  long long dense = 0;
+  for (int k : S.dense_slots) dense += S.slot_cap[k];
+  out[5] = dense;
   return HFX_OK;
 }
 
@@ -825,7 +830,7 @@ extern "C" hfx_status hfx_profile_enable(hfx_ctx* c, int on) {
   return HFX_OK;
 }
 
-extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[5], int64_t launches[5]) {
+extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]) {
   g_last_error.clear();
   if (!c || !ms || !launches) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
   for (int k = 0; k < kProfSlots; ++k) { ms[k] = 0.0; launches[k] = 0; }

@@ -29,7 +29,7 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_apply_noalloc", "hfx_sync_status", "hfx_plan_stats", "hfx_profile_enable", "hfx_profile_read",
             "hfx_last_error", "hfx_destroy")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
-PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_inv_acc", "energy")
+PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 
 
 class HfxBox(ctypes.Structure):
@@ -163,10 +163,10 @@ def hfx_sync_status(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
 
 
 def hfx_plan_stats(ctx, n_orb: int, n_pairs: int, flags: int = 0) -> dict:
-    out = (ctypes.c_int64 * 5)()
+    out = (ctypes.c_int64 * 6)()
     _check(load_library().hfx_plan_stats(ctx, int(n_orb), int(n_pairs), int(flags), out))
     return {"launches": int(out[0]), "batches": int(out[1]), "block": int(out[2]), "max_batch_couples": int(out[3]),
-            "couples": int(out[4])}
+            "couples": int(out[4]), "dense_couples": int(out[5])}
 
 
 def hfx_profile_enable(ctx, on: bool) -> None:
@@ -174,8 +174,8 @@ def hfx_profile_enable(ctx, on: bool) -> None:
 
 
 def hfx_profile_read(ctx) -> dict:
-    ms = (ctypes.c_double * 5)()
-    n = (ctypes.c_int64 * 5)()
+    ms = (ctypes.c_double * 6)()
+    n = (ctypes.c_int64 * 6)()
     _check(load_library().hfx_profile_read(ctx, ms, n))
     return {name: {"ms": float(ms[k]), "launches": int(n[k])} for k, name in enumerate(PASS_NAMES)}
 
