@@ -213,6 +213,7 @@ struct hfx_ctx {
   int bsize = 8;
   size_t transform_budget = size_t(1) << 30;
   int blocks_fwd = 1, blocks_x = 1;
+  int gen_grp = 1, gen_phi = 0;  // generic accumulate pass: couples per group, orbital tiles on chip
   // compile-time-geometry passes (FP32, cubic grid with an instantiated edge), else NULL
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
@@ -262,9 +263,24 @@ static size_t smem_fwd(const hfx_ctx* c) {
 static size_t smem_x(const hfx_ctx* c) {
   return (size_t)(c->grid[0] * (c->grid[2] + 1) + c->grid[0] + c->grid[2]) * cplx_size(c);
 }
-static size_t smem_acc(const hfx_ctx* c) {
+static int gen_cap_max(const hfx_ctx* c) { return (c->bsize * c->bsize + 1) / 2; }
+static size_t smem_acc_cfg(const hfx_ctx* c, int grp, int phi) {
   const int zc = zchunk(c);
-  return (size_t)(c->grid[1] * zc + c->grid[1]) * cplx_size(c) + (size_t)(2 * c->bsize) * c->grid[1] * zc * real_size(c);
+  const size_t pts = (size_t)c->grid[1] * zc;
+  return (size_t)(kGenRing * c->grid[1] * grp * zc + c->grid[1]) * cplx_size(c) +
+         (size_t)(2 * c->bsize) * pts * real_size(c) * (1 + phi) + (size_t)gen_cap_max(c) * sizeof(int4);
+}
+static size_t smem_acc(const hfx_ctx* c) { return smem_acc_cfg(c, c->gen_grp, c->gen_phi); }
+// largest couple group (4, 2, 1), orbital tiles on chip when they fit, for the generic pass
+static bool choose_generic(hfx_ctx* c) {
+  for (int grp : {4, 2, 1})
+    for (int phi : {1, 0})
+      if (smem_acc_cfg(c, grp, phi) + 512 <= (size_t)c->max_smem) {
+        c->gen_grp = grp;
+        c->gen_phi = phi;
+        return true;
+      }
+  return false;
 }
 static size_t smem_dense(const hfx_ctx* c) {
   const int zc = zchunk(c);
@@ -433,6 +449,8 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+  if (!choose_generic(c.get()))
+    return fail(HFX_ERR_UNSUPPORTED_GRID, "the accumulation tile of this grid does not fit in shared memory");
   const size_t need = std::max(std::max(smem_fwd(c.get()), smem_x(c.get())),
                                 std::max(smem_acc(c.get()), smem_dense(c.get()))) + 512;
   if (need > (size_t)c->max_smem)
@@ -679,7 +697,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
       if (ng > 0)
         Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
                                  S.d_generic_slots + S.generic_begin[b], S.d_slot_couple_base, S.d_slot_blocks, S.b,
-                                 n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale);
+                                 n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale, c->gen_grp, c->gen_phi,
+                                 gen_cap_max(c));
       if (ng > 0) prof_close(c, kProfAccGeneric, e0, st);
     }
   }

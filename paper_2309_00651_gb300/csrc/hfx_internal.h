@@ -26,7 +26,8 @@ struct Passes {
                           const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
   static void y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples,
                             const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int bsize,
-                            int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
+                            int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale, int grp,
+                            int phi_smem, int cap_max);
 };
 
 }  // namespace hfx

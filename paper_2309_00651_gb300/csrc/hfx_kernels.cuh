@@ -64,7 +64,6 @@ constexpr int kErrBadPair = 1;
 constexpr int kErrTimeout = 2;
 
 constexpr int kThreadsPlane = 256;  // k_fwd_yz / k_x_coulomb
-constexpr int kThreadsAcc = 128;    // k_y_acc_generic
 
 template <typename T> struct ZChunk;
 template <> struct ZChunk<float> { static constexpr int value = 8; };   // 64-byte rows
@@ -514,152 +513,153 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
 }
 
 // ----------------------------------------------------------------------------------
-// pass 3b: any block pair (diagonal, ragged or with a block size without a dense kernel):
-// inverse FFT along y couple by couple on one (x, z-chunk) tile, accumulators in shared memory,
-// one FP64 read-modify-write of V per block pair
+// pass 3b: any block pair (diagonal, ragged, sparse, or a block size without a dense kernel).
+// The block pair's couples are taken `grp` at a time (the next group streams in while the current
+// one is transformed): inverse FFT along y of the group's tiles on one (x, z-chunk), then each
+// thread adds, for its own points, v_a phi_a2 to the accumulator of a1 (and v_a phi_a1 to a2's
+// when a1 != a2), likewise for the b half.  Accumulators (FP32 or FP64 as the path) and, when
+// they fit, the orbital tiles live in shared memory; V_x phi is read and written once per block
+// pair and point, in FP64.
 // ----------------------------------------------------------------------------------
-struct AccCtx {
-  int i0, ni;   // block I: orbitals [i0, i0 + ni)
-  int j0, nj;   // block J (same as I for a diagonal block pair)
-  __device__ __forceinline__ int local(int o) const { return (o >= i0 && o - i0 < ni) ? o - i0 : ni + (o - j0); }
-};
-
-template <int R, typename C, typename T>
-__device__ __forceinline__ void y_last_acc(C* __restrict__ buf, const C* __restrict__ tw, int m, FastDiv zcdiv,
-                                           int zcn, T* __restrict__ acc, int tile_pts, const T* __restrict__ orb,
-                                           long long N, long long rowoff, int n3, int4 cp, const AccCtx& ac) {
-  // final inverse stage (stage 0: L = n2, one block, m = n2 / R), natural-order outputs
-  constexpr int ZC = ZChunk<T>::value;
-  const int total = ZC * m;
-  const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
-  const int la1 = hasa ? ac.local(cp.x) : 0, la2 = hasa ? ac.local(cp.y) : 0;
-  const int lb1 = hasb ? ac.local(cp.z) : 0, lb2 = hasb ? ac.local(cp.w) : 0;
-  const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * N + rowoff;
-  const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * N + rowoff;
-  const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * N + rowoff;
-  const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * N + rowoff;
-  const bool adiag = cp.x == cp.y, bdiag = cp.z == cp.w;
-  for (int id = threadIdx.x; id < total; id += blockDim.x) {
-    const int j1 = zcdiv.div(id);
-    const int zz = id - j1 * ZC;
-    C v[R];
-#pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = buf[(j1 + k * m) * ZC + zz];
-    if (m > 1) {
-#pragma unroll
-      for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], tw[j1 * k]);
-    }
-    Dft<R, 1, C>::run(v);
-    if (zz >= zcn) continue;
-#pragma unroll
-    for (int k = 0; k < R; ++k) {
-      const int y = j1 + k * m;
-      const int p = y * ZC + zz;
-      const long long go = (long long)y * n3 + zz;
-      if (hasa) {
-        const T fa1 = __ldg(pa1 + go), fa2 = __ldg(pa2 + go);
-        acc[la1 * tile_pts + p] += v[k].x * fa2;
-        if (!adiag) acc[la2 * tile_pts + p] += v[k].x * fa1;
-      }
-      if (hasb) {
-        const T fb1 = __ldg(pb1 + go), fb2 = __ldg(pb2 + go);
-        acc[lb1 * tile_pts + p] += v[k].y * fb2;
-        if (!bdiag) acc[lb2 * tile_pts + p] += v[k].y * fb1;
-      }
-    }
-  }
-}
-
-template <typename C, typename T>
-__device__ __forceinline__ void y_last_acc_rt(int R, C* buf, const C* tw, int m, FastDiv zcdiv, int zcn, T* acc,
-                                              int tp, const T* orb, long long N, long long ro, int n3, int4 cp,
-                                              const AccCtx& ac) {
-  switch (R) {
-    case 2: y_last_acc<2>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 3: y_last_acc<3>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 4: y_last_acc<4>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 5: y_last_acc<5>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 6: y_last_acc<6>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 8: y_last_acc<8>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 9: y_last_acc<9>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 10: y_last_acc<10>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 12: y_last_acc<12>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    case 16: y_last_acc<16>(buf, tw, m, zcdiv, zcn, acc, tp, orb, N, ro, n3, cp, ac); break;
-    default: break;
-  }
-}
+constexpr int kThreadsGen = 256;
+constexpr int kGenRing = 2;
 
 template <typename T>
-__global__ void __launch_bounds__(kThreadsAcc)
-k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, const int* __restrict__ slot_list,
-                const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int bsize, int n_orb,
-                int c0, const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g, double* __restrict__ V,
-                double vscale) {
+__global__ void __launch_bounds__(kThreadsGen)
+k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
+                const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
+                const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0, const cx<T>* __restrict__ W,
+                const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale, int grp, int phi_smem,
+                int cap_max) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
   constexpr int PER = 16 / int(sizeof(C));
+  constexpr int RPER = 16 / int(sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int z0 = blockIdx.x * ZC;
   const int zcn = min(ZC, n3 - z0);
   const int x = blockIdx.y;
   const int slot = slot_list[blockIdx.z];
-  const int tile_pts = n2 * ZC;
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tw2 = buf + tile_pts;
-  T* acc = reinterpret_cast<T*>(tw2 + n2);
+  const int pts = n2 * ZC;
+  const int LN = grp * ZC;
+  const int nloc_max = 2 * bsize;
+  C* tiles = reinterpret_cast<C*>(smem_raw);          // kGenRing x [n2][LN]
+  C* tw2 = tiles + kGenRing * n2 * LN;
+  T* acc = reinterpret_cast<T*>(tw2 + n2);             // [nloc][pts]
+  T* phi = acc + nloc_max * pts;                       // [nloc][pts] when phi_smem
+  int4* cloc = reinterpret_cast<int4*>(phi + (phi_smem ? nloc_max * pts : 0));  // [cap] local indices
 
   const int2 blk = slot_blocks[slot];
-  AccCtx ac;
-  ac.i0 = blk.x * bsize; ac.ni = min(bsize, n_orb - ac.i0);
-  ac.j0 = blk.y * bsize; ac.nj = min(bsize, n_orb - ac.j0);
-  const int nloc = (blk.x == blk.y) ? ac.ni : ac.ni + ac.nj;
-
-  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
-  for (int i = threadIdx.x; i < nloc * tile_pts; i += blockDim.x) acc[i] = T(0);
-
-  const int cs = slot_couple_base[slot], ce = slot_couple_base[slot + 1];
+  const int i0 = blk.x * bsize, ni = min(bsize, n_orb - i0);
+  const int j0 = blk.y * bsize, nj = min(bsize, n_orb - j0);
+  const bool same = blk.x == blk.y;
+  const int nloc = same ? ni : ni + nj;
+  auto local = [&](int o) { return (o >= i0 && o - i0 < ni) ? o - i0 : ni + (o - j0); };
+  auto orbital = [&](int lo) { return lo < ni ? i0 + lo : j0 + (lo - ni); };
+  const int cs = slot_couple_base[slot], nc = min(slot_couple_base[slot + 1] - cs, cap_max);
+  const int ngroups = (nc + grp - 1) / grp;
   const long long plane = (long long)n2 * n3;
   const long long rowoff = (long long)x * plane + z0;
-  const DimPlan& dy = g.d[1];
-  const FastDiv zcdiv = fastdiv_dev(ZC);
-  for (int c = cs; c < ce; ++c) {
-    const int4 cp = couples[c];
-    if (couple_empty(cp)) continue;
-    const C* src = W + ((long long)(c - c0) * n1 + x) * plane + z0;
-    __syncthreads();  // previous couple done with buf (and init complete)
-    for (int i = threadIdx.x; i < n2 * (ZC / PER); i += blockDim.x) {
-      const int yy = i / (ZC / PER), vv = i - yy * (ZC / PER);
-      int4 val = make_int4(0, 0, 0, 0);
-      if (vv * PER < zcn) val = __ldg(reinterpret_cast<const int4*>(src + (long long)yy * n3) + vv);
-      reinterpret_cast<int4*>(buf + yy * ZC)[vv] = val;
-    }
-    __syncthreads();
-    fft_inverse(dy, 1, dy.ns, buf, tw2, ZC, zcdiv, 1, ZC);
-    y_last_acc_rt(dy.r[0], buf, tw2, dy.m[0], zcdiv, zcn, acc, tile_pts, orb, g.N, rowoff, n3, cp, ac);
+
+  // couple table with local orbital indices (-1: absent half)
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    const int4 cp = couples[cs + c];
+    int4 l;
+    l.x = cp.x >= 0 ? local(cp.x) : -1;
+    l.y = cp.x >= 0 ? local(cp.y) : -1;
+    l.z = cp.z >= 0 ? local(cp.z) : -1;
+    l.w = cp.z >= 0 ? local(cp.w) : -1;
+    cloc[c] = l;
   }
+  // orbital tiles (first copy group)
+  if (phi_smem) {
+    const int VPR = ZC / RPER;
+    for (int i = threadIdx.x; i < nloc * n2 * VPR; i += blockDim.x) {
+      const int v = i % VPR;
+      const int rest = i / VPR;
+      const int y = rest % n2, lo = rest / n2;
+      const int valid = zcn - v * RPER;
+      const int bytes = valid >= RPER ? 16 : (valid > 0 ? valid * int(sizeof(T)) : 0);
+      const T* src = orb + (long long)orbital(lo) * g.N + rowoff + (long long)y * n3 + v * RPER;
+      cp_async16(phi + lo * pts + y * ZC + v * RPER, bytes ? (const void*)src : (const void*)orb, bytes);
+    }
+  }
+  __syncthreads();  // cloc ready for the copy issue below
+  auto issue_group = [&](int q) {
+    if (q < ngroups) {
+      C* dstb = tiles + (q % kGenRing) * n2 * LN;
+      const int VPR = ZC / PER;
+      for (int i = threadIdx.x; i < grp * n2 * VPR; i += blockDim.x) {
+        const int v = i % VPR;
+        const int rest = i / VPR;
+        const int t = rest % grp, y = rest / grp;
+        const int c = q * grp + t;
+        const bool live = c < nc && (cloc[c].x >= 0 || cloc[c].z >= 0) && v * PER < zcn;
+        const C* src = W + ((long long)(cs + c - c0) * n1 + x) * plane + (long long)y * n3 + z0 + v * PER;
+        cp_async16(dstb + y * LN + t * ZC + v * PER, live ? (const void*)src : (const void*)W, live ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+  for (int q = 0; q < kGenRing - 1; ++q) issue_group(q);
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
+  for (int i = threadIdx.x; i < nloc * pts; i += blockDim.x) acc[i] = T(0);
+
+  const FastDiv ldiv = fastdiv_dev(LN);
+  for (int q = 0; q < ngroups; ++q) {
+    issue_group(q + kGenRing - 1);
+    cp_async_wait<kGenRing - 1>();
+    __syncthreads();
+    C* buf = tiles + (q % kGenRing) * n2 * LN;
+    fft_inverse(g.d[1], 0, g.d[1].ns, buf, tw2, LN, ldiv, 1, LN);
+    for (int p = threadIdx.x; p < pts; p += blockDim.x) {
+      const int y = p / ZC, zz = p - y * ZC;
+      if (zz >= zcn) continue;
+      const long long go = rowoff + (long long)y * n3 + zz;
+      for (int t = 0; t < grp; ++t) {
+        const int c = q * grp + t;
+        if (c >= nc) break;
+        const int4 l = cloc[c];
+        const C v = buf[y * LN + t * ZC + zz];
+        if (l.x >= 0) {
+          const T f1 = phi_smem ? phi[l.x * pts + p] : __ldg(orb + (long long)orbital(l.x) * g.N + go);
+          const T f2 = phi_smem ? phi[l.y * pts + p] : __ldg(orb + (long long)orbital(l.y) * g.N + go);
+          acc[l.x * pts + p] += v.x * f2;
+          if (l.x != l.y) acc[l.y * pts + p] += v.x * f1;
+        }
+        if (l.z >= 0) {
+          const T f1 = phi_smem ? phi[l.z * pts + p] : __ldg(orb + (long long)orbital(l.z) * g.N + go);
+          const T f2 = phi_smem ? phi[l.w * pts + p] : __ldg(orb + (long long)orbital(l.w) * g.N + go);
+          acc[l.z * pts + p] += v.y * f2;
+          if (l.z != l.w) acc[l.w * pts + p] += v.y * f1;
+        }
+      }
+    }
+    __syncthreads();  // buffer q % kGenRing is refilled by the copies issued next
+  }
+  cp_async_wait<0>();
   __syncthreads();
   // flush: V[o][x][y][z0 + zz] += vscale * acc, in groups whose loads all precede their stores
-  constexpr int G = 8;
-  const int total = nloc * tile_pts;
-  for (int i0 = threadIdx.x; i0 < total; i0 += G * blockDim.x) {
-    double old[G];
-    long long off[G];
-    bool on[G];
+  constexpr int GF = 8;
+  const int total = nloc * pts;
+  for (int i0f = threadIdx.x; i0f < total; i0f += GF * blockDim.x) {
+    double old[GF];
+    long long off[GF];
+    bool on[GF];
 #pragma unroll
-    for (int u = 0; u < G; ++u) {
-      const int i = i0 + u * blockDim.x;
-      const int lo = i / tile_pts;
-      const int p = i - lo * tile_pts;
+    for (int u = 0; u < GF; ++u) {
+      const int i = i0f + u * blockDim.x;
+      const int lo = i / pts;
+      const int p = i - lo * pts;
       const int yy = p / ZC, zz = p - yy * ZC;
       on[u] = i < total && zz < zcn;
-      const int o = (lo < ac.ni) ? ac.i0 + lo : ac.j0 + (lo - ac.ni);
-      off[u] = (long long)o * g.N + rowoff + (long long)yy * n3 + zz;
+      off[u] = (long long)orbital(lo) * g.N + rowoff + (long long)yy * n3 + zz;
       old[u] = on[u] ? __ldcg(V + off[u]) : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < G; ++u)
-      if (on[u]) V[off[u]] = old[u] + vscale * double(acc[i0 + u * blockDim.x]);
+    for (int u = 0; u < GF; ++u)
+      if (on[u]) V[off[u]] = old[u] + vscale * double(acc[i0f + u * blockDim.x]);
   }
 }
 

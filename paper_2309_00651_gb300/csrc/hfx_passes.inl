@@ -62,9 +62,9 @@ template <>
 void Passes<Real>::y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const Real* orb,
                                  const int4* couples, const int* slot_list, const int* slot_couple_base,
                                  const int2* slot_blocks, int bsize, int n_orb, int c0, const cx<Real>* W,
-                                 const cx<Real>* tw2, double* V, double vscale) {
-  k_y_acc_generic<Real><<<grid, kThreadsAcc, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks,
-                                                        bsize, n_orb, c0, W, tw2, V, vscale);
+                                 const cx<Real>* tw2, double* V, double vscale, int grp, int phi_smem, int cap_max) {
+  k_y_acc_generic<Real><<<grid, kThreadsGen, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks,
+                                                        bsize, n_orb, c0, W, tw2, V, vscale, grp, phi_smem, cap_max);
 }
 
 template struct Passes<Real>;
