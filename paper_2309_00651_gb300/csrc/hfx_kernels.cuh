@@ -365,6 +365,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
 }
+// 8-byte variant, for rows that start on 8-byte boundaries only
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, int src_bytes) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -534,7 +539,6 @@ k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const 
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
   constexpr int PER = 16 / int(sizeof(C));
-  constexpr int RPER = 16 / int(sizeof(T));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
   const int z0 = blockIdx.x * ZC;
@@ -572,17 +576,19 @@ k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const 
     l.w = cp.z >= 0 ? local(cp.w) : -1;
     cloc[c] = l;
   }
-  // orbital tiles (first copy group)
+  // orbital tiles (first copy group), in 8-byte pieces: with n3 even every row of reals starts on
+  // an 8-byte boundary, but on a 16-byte one only when n3 is a multiple of 16 / sizeof(T)
   if (phi_smem) {
-    const int VPR = ZC / RPER;
+    constexpr int EPER = 8 / int(sizeof(T));  // reals per 8-byte copy
+    constexpr int VPR = ZC / EPER;
     for (int i = threadIdx.x; i < nloc * n2 * VPR; i += blockDim.x) {
       const int v = i % VPR;
       const int rest = i / VPR;
       const int y = rest % n2, lo = rest / n2;
-      const int valid = zcn - v * RPER;
-      const int bytes = valid >= RPER ? 16 : (valid > 0 ? valid * int(sizeof(T)) : 0);
-      const T* src = orb + (long long)orbital(lo) * g.N + rowoff + (long long)y * n3 + v * RPER;
-      cp_async16(phi + lo * pts + y * ZC + v * RPER, bytes ? (const void*)src : (const void*)orb, bytes);
+      const int valid = zcn - v * EPER;
+      const int bytes = valid >= EPER ? 8 : (valid > 0 ? valid * int(sizeof(T)) : 0);
+      const T* src = orb + (long long)orbital(lo) * g.N + rowoff + (long long)y * n3 + v * EPER;
+      cp_async8(phi + lo * pts + y * ZC + v * EPER, bytes ? (const void*)src : (const void*)orb, bytes);
     }
   }
   __syncthreads();  // cloc ready for the copy issue below
