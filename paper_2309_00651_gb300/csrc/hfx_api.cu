@@ -214,6 +214,10 @@ struct hfx_ctx {
   size_t transform_budget = size_t(1) << 30;
   int blocks_fwd = 1, blocks_x = 1;
   int gen_grp = 1, gen_phi = 0;  // generic accumulate pass: couples per group, orbital tiles on chip
+  // second stream and events: the forward and x passes of batch b+1 run beside the accumulate
+  // pass of batch b (double-buffered transforms)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_p2 = nullptr, ev_p3[2] = {nullptr, nullptr};
   // compile-time-geometry passes (FP32, cubic grid with an instantiated edge), else NULL
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
@@ -316,6 +320,12 @@ static bool dense_available(const hfx_ctx* c) {
 }
 
 static void free_ctx_tables(hfx_ctx* c) {
+  for (cudaEvent_t* e : {&c->ev_fork, &c->ev_p2, &c->ev_p3[0], &c->ev_p3[1]}) {
+    if (*e) cudaEventDestroy(*e);
+    *e = nullptr;
+  }
+  if (c->side) cudaStreamDestroy(c->side);
+  c->side = nullptr;
   if (c->d_twct) cudaFree(c->d_twct);
   c->d_twct = nullptr;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
@@ -466,6 +476,15 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   c->blocks_x = std::max(1, c->blocks_x);
   hfx_status st = build_tables(c.get());
   if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
+  {
+    cudaError_t es = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&c->ev_fork, &c->ev_p2, &c->ev_p3[0], &c->ev_p3[1]})
+      if (es == cudaSuccess) es = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (es != cudaSuccess) {
+      free_ctx_tables(c.get());
+      return fail(HFX_ERR_CUDA, "stream/event creation failed: %s", cudaGetErrorString(es));
+    }
+  }
   // compile-time-geometry passes for FP32 cubic grids with an instantiated edge
   const char* no_ct = std::getenv("HFX_NO_CT");
   if (prec == HFX_PREC_FP32 && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
@@ -508,7 +527,7 @@ extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes)
 // workspace layout
 // ------------------------------------------------------------------------------------
 struct Layout {
-  size_t orb32, W, epart, couples, total;
+  size_t orb32, W, W2, epart, couples, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -527,6 +546,8 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   const size_t orb32_bytes = (c->prec == HFX_PREC_FP32) ? (size_t)n_orb * c->N * 4 : 0;
   L.orb32 = take(orb32_bytes);
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
+  // a second transform buffer when batches are pipelined on two streams
+  L.W2 = take(S.nbatches > 1 ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
   L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
   L.total = off;
@@ -641,7 +662,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
                              double* vxphi, cudaStream_t st) {
   char* ws = (char*)c->ws;
   using C = cx<T>;
-  C* W = (C*)(ws + L.W);
+  const bool pipe = S.nbatches > 1 && c->side != nullptr;
+  C* Wbuf[2] = {(C*)(ws + L.W), (C*)(ws + (pipe ? L.W2 : L.W))};
   int4* couples = (int4*)(ws + L.couples);
   double* epart = (double*)(ws + L.epart);
   const Geo& g = c->geo;
@@ -653,33 +675,46 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
   const int dense_np = pts > 2 * DenseBounds<2>::threads ? 4 : 2;
   const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
                                      (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
+  // forward and x passes on `fs`, accumulate passes on the caller's stream `st`
+  cudaStream_t fs = pipe ? c->side : st;
+  if (pipe) {
+    HFX_CUDA_TRY(cudaEventRecord(c->ev_fork, st));
+    HFX_CUDA_TRY(cudaStreamWaitEvent(fs, c->ev_fork, 0));
+  }
   for (int b = 0; b < S.nbatches; ++b) {
+    C* W = Wbuf[b & 1];
+    // buffer b & 1 was last read by the accumulate pass of batch b - 2
+    if (pipe && b >= 2) HFX_CUDA_TRY(cudaStreamWaitEvent(fs, c->ev_p3[b & 1], 0));
     const int s0 = S.batch_slot_begin[b], s1 = S.batch_slot_begin[b + 1];
     const int c0 = S.slot_couple_base[s0], c1 = S.slot_couple_base[s1];
     const long long items1 = (long long)(c1 - c0) * g.n1, items2 = (long long)(c1 - c0) * g.n2;
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
     const CtFns* ct = std::is_same<T, float>::value ? c->ct : nullptr;
-    cudaEvent_t e0 = prof_mark(c, st);
+    cudaEvent_t e0 = prof_mark(c, fs);
     if (ct) {
       const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
-      ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), st, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
+      ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
                  (const float2*)c->d_twct);
     } else {
-      Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), st, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
+      Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), fs, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
                         (const C*)c->d_tw[2]);
     }
-    prof_close(c, kProfFwd, e0, st);
-    e0 = prof_mark(c, st);
+    prof_close(c, kProfFwd, e0, fs);
+    e0 = prof_mark(c, fs);
     if (ct) {
       const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
-      ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), st, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
+      ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
                     (const float2*)c->d_twct, epart, energy_only ? 1 : 0);
     } else {
-      Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), st, couples, c0, c1, W, (const T*)c->d_vtab,
+      Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), fs, couples, c0, c1, W, (const T*)c->d_vtab,
                            (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
     }
-    prof_close(c, kProfX, e0, st);
+    prof_close(c, kProfX, e0, fs);
+    if (pipe) {
+      HFX_CUDA_TRY(cudaEventRecord(c->ev_p2, fs));
+      HFX_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_p2, 0));
+    }
     if (!energy_only) {
       e0 = prof_mark(c, st);
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
@@ -701,6 +736,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
                                  gen_cap_max(c));
       if (ng > 0) prof_close(c, kProfAccGeneric, e0, st);
     }
+    if (pipe) HFX_CUDA_TRY(cudaEventRecord(c->ev_p3[b & 1], st));
   }
   return HFX_OK;
 }
