@@ -547,7 +547,7 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   L.orb32 = take(orb32_bytes);
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   // a second transform buffer when batches are pipelined on two streams
-  L.W2 = take(S.nbatches > 1 ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
+  L.W2 = take(S.nbatches > 1 && c->side ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
   L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
   L.total = off;
@@ -970,6 +970,20 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
     return HFX_OK;
   }
 
+  // the passes read the context's workspace and side stream: for this call the workspace is the
+  // scratch array and the batches run on the caller's stream alone (one transform buffer), with
+  // event timing off (it would create events); calls on one context never overlap
+  struct Restore {
+    hfx_ctx* c;
+    void* ws;
+    size_t bytes;
+    bool prof;
+    cudaStream_t side;
+    ~Restore() { c->ws = ws; c->ws_bytes = bytes; c->prof_on = prof; c->side = side; }
+  } restore{c, c->ws, c->ws_bytes, c->prof_on, c->side};
+  c->side = nullptr;
+  c->prof_on = false;
+
   // host schedule; its device tables go to the head of the scratch array, the workspace after them
   Schedule S = make_host_schedule(c, n_orb);
   size_t off = 0;
@@ -1003,18 +1017,8 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   S.d_dense_slots = (int*)(base + o_dense);
   S.d_generic_slots = (int*)(base + o_gen);
 
-  // the passes read the context's workspace: point it at the scratch for this call (calls on one
-  // context never overlap), with event timing off (it would create events)
-  struct Restore {
-    hfx_ctx* c;
-    void* ws;
-    size_t bytes;
-    bool prof;
-    ~Restore() { c->ws = ws; c->ws_bytes = bytes; c->prof_on = prof; }
-  } restore{c, c->ws, c->ws_bytes, c->prof_on};
   c->ws = base + off;
   c->ws_bytes = kNoallocScratchBytes - off;
-  c->prof_on = false;
   char* ws = (char*)c->ws;
 
   if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
