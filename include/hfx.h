@@ -168,6 +168,17 @@ hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
  * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST or HFX_ERR_TIMEOUT. */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
 
+/* hfx_set_tuning -- schedule parameters of the context (what an autotuner varies; results do
+ * not depend on them beyond rounding order):
+ *   block       : orbitals per block (1..32, default 8; 4 and 8 have register-accumulating
+ *                 kernels for full off-diagonal block pairs);
+ *   batch_bytes : device memory for one batch of packed transforms (default 1 GiB);
+ *   pipeline    : nonzero = the forward/x passes of the next batch run on a second stream beside
+ *                 the accumulate pass of the current one (two transform buffers), 0 = one stream.
+ * Synchronises the device when cached schedules have to be dropped; not during stream capture.
+ * The workspace size (hfx_workspace_bytes) changes with these settings. */
+hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_bytes, int32_t pipeline);
+
 /* hfx_plan_stats -- what hfx_apply(c, ..., n_orb, ..., n_pairs, flags, ...) will launch, from the
  * host schedule alone (no device work):
  *   out[0] = kernel launches per call, out[1] = batches, out[2] = orbital block size,

@@ -218,6 +218,7 @@ struct hfx_ctx {
   // pass of batch b (double-buffered transforms)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_p2 = nullptr, ev_p3[2] = {nullptr, nullptr};
+  bool pipeline = true;
   // compile-time-geometry passes (FP32, cubic grid with an instantiated edge), else NULL
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
@@ -455,6 +456,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   c->prec = prec;
   if (const char* s = std::getenv("HFX_BLOCK")) c->bsize = std::max(1, std::min(32, atoi(s)));
   if (const char* s = std::getenv("HFX_BATCH_MB")) c->transform_budget = (size_t)std::max(1, atoi(s)) << 20;
+  if (const char* s = std::getenv("HFX_PIPELINE")) c->pipeline = atoi(s) != 0;
 
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
@@ -547,7 +549,7 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   L.orb32 = take(orb32_bytes);
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   // a second transform buffer when batches are pipelined on two streams
-  L.W2 = take(S.nbatches > 1 && c->side ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
+  L.W2 = take(S.nbatches > 1 && c->side && c->pipeline ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
   L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
   L.total = off;
@@ -662,7 +664,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
                              double* vxphi, cudaStream_t st) {
   char* ws = (char*)c->ws;
   using C = cx<T>;
-  const bool pipe = S.nbatches > 1 && c->side != nullptr;
+  const bool pipe = S.nbatches > 1 && c->side != nullptr && c->pipeline;
   C* Wbuf[2] = {(C*)(ws + L.W), (C*)(ws + (pipe ? L.W2 : L.W))};
   int4* couples = (int4*)(ws + L.couples);
   double* epart = (double*)(ws + L.epart);
@@ -1053,5 +1055,35 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S.max_total_couples, c->grid[1], scale,
                                     accumulate ? 1 : 0, ex_dev);
   HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_bytes, int32_t pipeline) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (block < 1 || block > 32) return fail(HFX_ERR_INVALID_ARG, "block must be in [1, 32]");
+  if (batch_bytes == 0) return fail(HFX_ERR_INVALID_ARG, "batch_bytes must be > 0");
+  const int old_b = c->bsize, old_grp = c->gen_grp, old_phi = c->gen_phi;
+  c->bsize = block;
+  if (!choose_generic(c) || smem_dense(c) + 512 > (size_t)c->max_smem) {
+    c->bsize = old_b;
+    c->gen_grp = old_grp;
+    c->gen_phi = old_phi;
+    return fail(HFX_ERR_INVALID_ARG, "block %d does not fit this grid's shared-memory tiles", (int)block);
+  }
+  c->transform_budget = batch_bytes;
+  c->pipeline = pipeline != 0;
+  // cached schedules depend on the block size and the budget: drop them (device tables freed after
+  // the device is idle, since a call in flight may still read them)
+  if (!c->sched.empty()) {
+    cudaDeviceSynchronize();
+    for (auto& kv : c->sched) {
+      Schedule& S = *kv.second;
+      for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
+                      (void*)S.d_dense_slots, (void*)S.d_generic_slots})
+        if (p) cudaFree(p);
+    }
+    c->sched.clear();
+  }
   return HFX_OK;
 }

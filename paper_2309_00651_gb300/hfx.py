@@ -26,7 +26,8 @@ HFX_ORBITALS_F32 = 0x4
 
 # every symbol include/hfx.h declares
 EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
-            "hfx_apply_noalloc", "hfx_sync_status", "hfx_plan_stats", "hfx_profile_enable", "hfx_profile_read",
+            "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
+            "hfx_profile_read",
             "hfx_last_error", "hfx_destroy")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
@@ -76,6 +77,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_apply_batched.restype = ctypes.c_int
     L.hfx_sync_status.argtypes = [vp, vp]
     L.hfx_sync_status.restype = ctypes.c_int
+    L.hfx_set_tuning.argtypes = [vp, i32, sz, i32]
+    L.hfx_set_tuning.restype = ctypes.c_int
     L.hfx_plan_stats.argtypes = [vp, i32, i64, u32, ctypes.POINTER(i64)]
     L.hfx_plan_stats.restype = ctypes.c_int
     L.hfx_profile_enable.argtypes = [vp, ctypes.c_int]
@@ -160,6 +163,10 @@ def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) ->
 
 def hfx_sync_status(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
     _check(load_library().hfx_sync_status(ctx, _stream_handle(stream)))
+
+
+def hfx_set_tuning(ctx, block: int = 8, batch_bytes: int = 1 << 30, pipeline: bool = True) -> None:
+    _check(load_library().hfx_set_tuning(ctx, int(block), int(batch_bytes), 1 if pipeline else 0))
 
 
 def hfx_plan_stats(ctx, n_orb: int, n_pairs: int, flags: int = 0) -> dict:
@@ -254,6 +261,10 @@ class Exchange:
 
     def sync_status(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         hfx_sync_status(self.ctx, stream)
+
+    def set_tuning(self, block: int = 8, batch_bytes: int = 1 << 30, pipeline: bool = True) -> None:
+        hfx_set_tuning(self.ctx, block, batch_bytes, pipeline)
+        self.tuning = {"block": int(block), "batch_bytes": int(batch_bytes), "pipeline": bool(pipeline)}
 
     def close(self) -> None:
         if getattr(self, "ctx", None) is not None and self.ctx.value:
