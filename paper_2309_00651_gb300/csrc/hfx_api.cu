@@ -219,6 +219,9 @@ struct hfx_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_p2 = nullptr, ev_p3[2] = {nullptr, nullptr};
   bool pipeline = true;
+  // pencil form of the forward/x passes (a plane does not fit in shared memory): row-block size
+  bool pencil = false;
+  int rb = 0;
   // compile-time-geometry passes (FP32, cubic grid with an instantiated edge), else NULL
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
@@ -315,6 +318,14 @@ static std::vector<double> stage_twiddles(int n) {
   }
   return tw;
 }
+
+// pencil kernels: rows blocks of rb rows (padded stride n3 + 1) and single z-chunk columns
+static size_t smem_rows(const hfx_ctx* c, int rb) {
+  return (size_t)(rb * (c->grid[2] + 1) + c->grid[2]) * cplx_size(c);
+}
+static size_t smem_cols(const hfx_ctx* c, int n) { return (size_t)(n * zchunk(c) + n) * cplx_size(c); }
+// energy partial sums per couple: one per y-plane, or per (y-plane, z-chunk) in the pencil form
+static int eparts(const hfx_ctx* c) { return c->pencil ? c->grid[1] * (c->grid[2] / zchunk(c)) : c->grid[1]; }
 
 static bool dense_available(const hfx_ctx* c) {
   return c->prec == HFX_PREC_FP64 ? Passes<double>::has_dense(c->bsize) : Passes<float>::has_dense(c->bsize);
@@ -463,17 +474,32 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
   if (!choose_generic(c.get()))
     return fail(HFX_ERR_UNSUPPORTED_GRID, "the accumulation tile of this grid does not fit in shared memory");
-  const size_t need = std::max(std::max(smem_fwd(c.get()), smem_x(c.get())),
-                                std::max(smem_acc(c.get()), smem_dense(c.get()))) + 512;
+  const char* force_pencil = std::getenv("HFX_PENCIL");  // the pencil form on any grid (testing)
+  if (std::max(smem_fwd(c.get()), smem_x(c.get())) + 512 > (size_t)c->max_smem ||
+      (force_pencil && atoi(force_pencil) != 0)) {
+    // planes too large for one SM: the forward and x passes run as row blocks and z-chunk pencils
+    if (grid[2] % zchunk(c.get()) != 0)
+      return fail(HFX_ERR_UNSUPPORTED_GRID, "grid planes exceed shared memory and n3 = %d is not a multiple of %d",
+                  (int)grid[2], zchunk(c.get()));
+    c->pencil = true;
+    c->rb = std::max(1, std::min(grid[1], (int)((48 * 1024) / ((grid[2] + 1) * cplx_size(c.get())))));
+  }
+  const size_t plane_need = c->pencil ? std::max(smem_rows(c.get(), c->rb),
+                                                 std::max(smem_cols(c.get(), grid[0]), smem_cols(c.get(), grid[1])))
+                                      : std::max(smem_fwd(c.get()), smem_x(c.get()));
+  const size_t need = std::max(plane_need, std::max(smem_acc(c.get()), smem_dense(c.get()))) + 512;
   if (need > (size_t)c->max_smem)
-    return fail(HFX_ERR_UNSUPPORTED_GRID, "a grid plane needs %zu bytes of shared memory (limit %d) at this precision",
+    return fail(HFX_ERR_UNSUPPORTED_GRID, "a grid tile needs %zu bytes of shared memory (limit %d) at this precision",
                 need, c->max_smem);
   cudaError_t e = (prec == HFX_PREC_FP64) ? Passes<double>::set_smem_limit(c->max_smem - 512)
                                           : Passes<float>::set_smem_limit(c->max_smem - 512);
   if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-  e = (prec == HFX_PREC_FP64) ? Passes<double>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x)
-                              : Passes<float>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x);
-  if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+  if (!c->pencil) {
+    e = (prec == HFX_PREC_FP64)
+            ? Passes<double>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x)
+            : Passes<float>::occupancy(smem_fwd(c.get()), smem_x(c.get()), &c->blocks_fwd, &c->blocks_x);
+    if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "occupancy query: %s", cudaGetErrorString(e));
+  }
   c->blocks_fwd = std::max(1, c->blocks_fwd);
   c->blocks_x = std::max(1, c->blocks_x);
   hfx_status st = build_tables(c.get());
@@ -489,7 +515,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   }
   // compile-time-geometry passes for FP32 cubic grids with an instantiated edge
   const char* no_ct = std::getenv("HFX_NO_CT");
-  if (prec == HFX_PREC_FP32 && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
+  if (prec == HFX_PREC_FP32 && !c->pencil && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
     const CtFns* f = ct_fns(grid[0]);
     const int n = grid[0];
     if (f && std::max(smem_plane_ct(n), smem_dense_ct(n, 8)) + 512 <= (size_t)c->max_smem) {
@@ -550,7 +576,7 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   // a second transform buffer when batches are pipelined on two streams
   L.W2 = take(S.nbatches > 1 && c->side && c->pipeline ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
-  L.epart = take((size_t)S.max_total_couples * c->grid[1] * sizeof(double));
+  L.epart = take((size_t)S.max_total_couples * eparts(c) * sizeof(double));
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
   L.total = off;
   return L;
@@ -694,6 +720,22 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
     const CtFns* ct = std::is_same<T, float>::value ? c->ct : nullptr;
     cudaEvent_t e0 = prof_mark(c, fs);
+    if (c->pencil) {
+      const int nzc3 = g.n3 / zc, nrb = (g.n2 + c->rb - 1) / c->rb;
+      const long long cap = (long long)c->sm_count * 16;
+      const int gr = (int)std::max<long long>(1, std::min<long long>((long long)(c1 - c0) * g.n1 * nrb, cap));
+      const int gy = (int)std::max<long long>(1, std::min<long long>((long long)(c1 - c0) * g.n1 * nzc3, cap));
+      const int gx = (int)std::max<long long>(1, std::min<long long>((long long)(c1 - c0) * g.n2 * nzc3, cap));
+      Passes<T>::fwd_z_rows(g, gr, smem_rows(c, c->rb), fs, orb, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
+      Passes<T>::fwd_y_cols(g, gy, smem_cols(c, g.n2), fs, couples, c0, c1, W, (const C*)c->d_tw[1]);
+      prof_close(c, kProfFwd, e0, fs);
+      e0 = prof_mark(c, fs);
+      Passes<T>::x_cols(g, gx, smem_cols(c, g.n1), fs, couples, c0, c1, W, (const T*)c->d_vtab,
+                        (const C*)c->d_tw[0], epart, energy_only ? 1 : 0);
+      if (!energy_only)
+        Passes<T>::inv_z_rows(g, gr, smem_rows(c, c->rb), fs, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
+      prof_close(c, kProfX, e0, fs);
+    } else {
     if (ct) {
       const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
       ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
@@ -713,6 +755,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
                            (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
     }
     prof_close(c, kProfX, e0, fs);
+    }
     if (pipe) {
       HFX_CUDA_TRY(cudaEventRecord(c->ev_p2, fs));
       HFX_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_p2, 0));
@@ -810,7 +853,7 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
   cudaEvent_t e_en = prof_mark(c, st);
-  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S->max_total_couples, c->grid[1],
+  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S->max_total_couples, eparts(c),
                                     scale, accumulate ? 1 : 0, ex_dev);
   prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
@@ -1052,7 +1095,7 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   }
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
-  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S.max_total_couples, c->grid[1], scale,
+  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), scale,
                                     accumulate ? 1 : 0, ex_dev);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;

@@ -21,6 +21,15 @@ struct Passes {
                      int c1, cx<T>* W, const cx<T>* tw2, const cx<T>* tw3);
   static void x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
                         cx<T>* W, const T* vtab, const cx<T>* tw1, const cx<T>* tw3, double* epart, int energy_only);
+  // pencil form of the forward/x passes (planes too large for shared memory)
+  static void fwd_z_rows(const Geo& g, int grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples, int c0,
+                         int c1, int rb, cx<T>* W, const cx<T>* tw3);
+  static void fwd_y_cols(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                         cx<T>* W, const cx<T>* tw2);
+  static void x_cols(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                     cx<T>* W, const T* vtab, const cx<T>* tw1, double* epart, int energy_only);
+  static void inv_z_rows(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                         int rb, cx<T>* W, const cx<T>* tw3);
   static void y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b, const T* orb,
                           const int4* couples, const int* slot_list, const int* slot_couple_base,
                           const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);

@@ -359,6 +359,168 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
 }
 
 // ----------------------------------------------------------------------------------
+// Pencil form of passes 1 and 2, for grids whose planes do not fit in one SM's shared memory
+// (FP64 on 128^3): the same transforms one or two axes at a time.
+//   k_fwd_z_rows   (couple, x, row block)   pair product + forward FFT along z of rows -> W
+//   k_fwd_y_cols   (couple, x, z-chunk)     forward FFT along y -> W
+//   k_x_cols       (couple, y, z-chunk)     forward FFT along x, Coulomb + energy, inverse FFT
+//                                           along x -> W
+//   k_inv_z_rows   (couple, x, row block)   inverse FFT along z -> W
+// The energy partials are per (couple, y, z-chunk).  Requires n3 % ZChunk == 0.
+// ----------------------------------------------------------------------------------
+constexpr int kThreadsPencil = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsPencil)
+k_fwd_z_rows(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, int c0, int c1,
+             int rb, cx<T>* __restrict__ W, const cx<T>* __restrict__ tw3g) {
+  using C = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [rb][S]
+  C* tw3 = buf + rb * S;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
+  const int nrb = (n2 + rb - 1) / rb;
+  const long long items = (long long)(c1 - c0) * n1 * nrb;
+  const long long plane = (long long)n2 * n3;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = int(it / ((long long)n1 * nrb));
+    const int rem = int(it - (long long)cl * n1 * nrb);
+    const int x = rem / nrb, y0 = (rem - x * nrb) * rb;
+    const int rows = min(rb, n2 - y0);
+    const int4 cp = couples[c0 + cl];
+    if (couple_empty(cp)) continue;
+    const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+    const long long off = (long long)x * plane + (long long)y0 * n3;
+    const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * g.N + off;
+    const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * g.N + off;
+    const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * g.N + off;
+    const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
+    __syncthreads();
+    for (int p = threadIdx.x; p < rows * n3; p += blockDim.x) {
+      const int r = g.d[2].ndiv.div(p), z = p - r * n3;
+      const T a = hasa ? __ldg(pa1 + p) * __ldg(pa2 + p) : T(0);
+      const T b = hasb ? __ldg(pb1 + p) * __ldg(pb2 + p) : T(0);
+      buf[r * S + z] = mk<C>(a, b);
+    }
+    __syncthreads();
+    fft_forward(g.d[2], 0, g.d[2].ns, buf, tw3, rows, fastdiv_dev(rows), S, 1);
+    plane_s2g(W + ((long long)cl * n1 + x) * plane + (long long)y0 * n3, n3, buf, S, rows, n3, g.d[2].ndiv);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsPencil)
+k_inv_z_rows(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, int rb,
+             cx<T>* __restrict__ W, const cx<T>* __restrict__ tw3g) {
+  using C = cx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tw3 = buf + rb * S;
+  for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
+  const int nrb = (n2 + rb - 1) / rb;
+  const long long items = (long long)(c1 - c0) * n1 * nrb;
+  const long long plane = (long long)n2 * n3;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = int(it / ((long long)n1 * nrb));
+    const int rem = int(it - (long long)cl * n1 * nrb);
+    const int x = rem / nrb, y0 = (rem - x * nrb) * rb;
+    const int rows = min(rb, n2 - y0);
+    if (couple_empty(couples[c0 + cl])) continue;
+    C* base = W + ((long long)cl * n1 + x) * plane + (long long)y0 * n3;
+    __syncthreads();
+    plane_g2s(buf, S, base, n3, rows, n3, g.d[2].ndiv);
+    __syncthreads();
+    fft_inverse(g.d[2], 0, g.d[2].ns, buf, tw3, rows, fastdiv_dev(rows), S, 1);
+    plane_s2g(base, n3, buf, S, rows, n3, g.d[2].ndiv);
+  }
+}
+
+// tile [n][ZC] of one z-chunk: load / store rows of ZC complex values (stride gstride apart)
+template <typename C, int ZC>
+__device__ __forceinline__ void chunk_g2s(C* __restrict__ buf, const C* __restrict__ src, long long gstride, int n) {
+  for (int i = threadIdx.x; i < n * ZC; i += blockDim.x) {
+    const int r = i / ZC, zz = i - r * ZC;
+    buf[i] = __ldg(src + r * gstride + zz);
+  }
+}
+template <typename C, int ZC>
+__device__ __forceinline__ void chunk_s2g(C* __restrict__ dst, long long gstride, const C* __restrict__ buf, int n) {
+  for (int i = threadIdx.x; i < n * ZC; i += blockDim.x) {
+    const int r = i / ZC, zz = i - r * ZC;
+    dst[r * gstride + zz] = buf[i];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsPencil)
+k_fwd_y_cols(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W,
+             const cx<T>* __restrict__ tw2g) {
+  using C = cx<T>;
+  constexpr int ZC = ZChunk<T>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [n2][ZC]
+  C* tw2 = buf + n2 * ZC;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
+  const int nzc = n3 / ZC;
+  const long long items = (long long)(c1 - c0) * n1 * nzc;
+  const long long plane = (long long)n2 * n3;
+  const FastDiv zcdiv = fastdiv_dev(ZC);
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = int(it / ((long long)n1 * nzc));
+    const int rem = int(it - (long long)cl * n1 * nzc);
+    const int x = rem / nzc, z0 = (rem - x * nzc) * ZC;
+    if (couple_empty(couples[c0 + cl])) continue;
+    C* base = W + ((long long)cl * n1 + x) * plane + z0;
+    __syncthreads();
+    chunk_g2s<C, ZC>(buf, base, n3, n2);
+    __syncthreads();
+    fft_forward(g.d[1], 0, g.d[1].ns, buf, tw2, ZC, zcdiv, 1, ZC);
+    chunk_s2g<C, ZC>(base, n3, buf, n2);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsPencil)
+k_x_cols(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W,
+         const T* __restrict__ vtab, const cx<T>* __restrict__ tw1g, double* __restrict__ epart, int energy_only) {
+  using C = cx<T>;
+  constexpr int ZC = ZChunk<T>::value;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [n1][ZC]
+  C* tw1 = buf + n1 * ZC;
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = tw1g[i];
+  const int nzc = n3 / ZC;
+  const long long items = (long long)(c1 - c0) * n2 * nzc;
+  const long long plane = (long long)n2 * n3;
+  const FastDiv zcdiv = fastdiv_dev(ZC);
+  const DimPlan& dx = g.d[0];
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+    const int cl = int(it / ((long long)n2 * nzc));
+    const int rem = int(it - (long long)cl * n2 * nzc);
+    const int y = rem / nzc, zc = rem - y * nzc, z0 = zc * ZC;
+    if (couple_empty(couples[c0 + cl])) continue;
+    C* base = W + (long long)cl * n1 * plane + (long long)y * n3 + z0;
+    __syncthreads();
+    chunk_g2s<C, ZC>(buf, base, plane, n1);
+    __syncthreads();
+    fft_forward(dx, 0, dx.ns - 1, buf, tw1, ZC, zcdiv, 1, ZC);
+    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, ZC, n1, ZC, zcdiv, vtab + (long long)y * n3 + z0,
+                                       plane, energy_only != 0);
+    const double es = block_sum(e, red);
+    if (threadIdx.x == 0) epart[((long long)(c0 + cl) * n2 + y) * nzc + zc] = es;
+    if (energy_only) continue;
+    __syncthreads();
+    fft_inverse(dx, 0, dx.ns - 1, buf, tw1, ZC, zcdiv, 1, ZC);
+    chunk_s2g<C, ZC>(base, plane, buf, n1);
+  }
+}
+
+// ----------------------------------------------------------------------------------
 // asynchronous 16-byte global -> shared copies (zero-filled when src_bytes == 0)
 // ----------------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {

@@ -9,7 +9,9 @@ cudaError_t Passes<Real>::set_smem_limit(int bytes) {
   const void* ks[] = {(const void*)k_fwd_yz<Real>,           (const void*)k_x_coulomb<Real>,
                       (const void*)k_y_acc_dense<Real, 4, 2>, (const void*)k_y_acc_dense<Real, 4, 4>,
                       (const void*)k_y_acc_dense<Real, 8, 2>, (const void*)k_y_acc_dense<Real, 8, 4>,
-                      (const void*)k_y_acc_generic<Real>};
+                      (const void*)k_y_acc_generic<Real>,      (const void*)k_fwd_z_rows<Real>,
+                      (const void*)k_fwd_y_cols<Real>,         (const void*)k_x_cols<Real>,
+                      (const void*)k_inv_z_rows<Real>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -65,6 +67,30 @@ void Passes<Real>::y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStrea
                                  const cx<Real>* tw2, double* V, double vscale, int grp, int phi_smem, int cap_max) {
   k_y_acc_generic<Real><<<grid, kThreadsGen, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks,
                                                         bsize, n_orb, c0, W, tw2, V, vscale, grp, phi_smem, cap_max);
+}
+
+template <>
+void Passes<Real>::fwd_z_rows(const Geo& g, int grid, size_t smem, cudaStream_t st, const Real* orb, const int4* couples,
+                              int c0, int c1, int rb, cx<Real>* W, const cx<Real>* tw3) {
+  k_fwd_z_rows<Real><<<grid, kThreadsPencil, smem, st>>>(g, orb, couples, c0, c1, rb, W, tw3);
+}
+
+template <>
+void Passes<Real>::fwd_y_cols(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                              cx<Real>* W, const cx<Real>* tw2) {
+  k_fwd_y_cols<Real><<<grid, kThreadsPencil, smem, st>>>(g, couples, c0, c1, W, tw2);
+}
+
+template <>
+void Passes<Real>::x_cols(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                          cx<Real>* W, const Real* vtab, const cx<Real>* tw1, double* epart, int energy_only) {
+  k_x_cols<Real><<<grid, kThreadsPencil, smem, st>>>(g, couples, c0, c1, W, vtab, tw1, epart, energy_only);
+}
+
+template <>
+void Passes<Real>::inv_z_rows(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
+                              int rb, cx<Real>* W, const cx<Real>* tw3) {
+  k_inv_z_rows<Real><<<grid, kThreadsPencil, smem, st>>>(g, couples, c0, c1, rb, W, tw3);
 }
 
 template struct Passes<Real>;

@@ -260,6 +260,38 @@ def test_cuda_graph_capture_and_replay():
     ex.close()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_pencil_form(prec, monkeypatch):
+    """The row-block / z-chunk pencil form of the forward and x passes (used when a grid plane does
+    not fit in shared memory, e.g. FP64 on 128^3), forced here on small grids."""
+    monkeypatch.setenv("HFX_PENCIL", "1")
+    for grid, Ls, n_orb in [((24, 16, 32), (9.0, 7.5, 11.0), 11), ((40, 40, 40), (12.0, 12.0, 12.0), 17)]:
+        lat = np.diag(Ls)
+        raw = I.random_pw_orbitals(n_orb, Ls[0], grid[0], ecut=1.0, seed=18) if grid[0] == grid[2] else None
+        if raw is None or raw.shape[1:] != grid:
+            raw = np.random.default_rng(19).standard_normal((n_orb,) + grid)
+        phi, _ = I.loewdin(raw, float(np.prod(Ls)))
+        pairs = I.all_pairs(n_orb)
+        E_ref, V_ref = O.exchange(phi, pairs, lat)
+        E, V = run_gpu(phi, pairs, lat, prec)
+        assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+        assert rel(V, V_ref) <= TOL[prec]
+        Ee, _ = run_gpu(phi, pairs, lat, prec, energy_only=True)
+        assert abs(Ee - E_ref) <= TOL[prec] * abs(E_ref)
+
+
+def test_fp64_on_128_grid_uses_pencils_and_matches_oracle():
+    """FP64 on a 128^3 grid (planes larger than shared memory), checked on a few pairs."""
+    n, L, n_orb = 128, 29.6, 6
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=20, frac=0.1)
+    pairs = I.all_pairs(n_orb)[::2]
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, "fp64")
+    assert abs(E - E_ref) <= 1e-8 * abs(E_ref)
+    assert rel(V, V_ref) <= 1e-8
+
+
 def test_bad_pairs_are_reported_and_skipped():
     from paper_2309_00651_gb300 import hfx
     n, L, n_orb = 16, 8.0, 6
