@@ -297,8 +297,8 @@ static size_t smem_dense(const hfx_ctx* c) {
 }
 static size_t smem_plane_ct(int n) { return (size_t)(n * (n + 1) + stage_plan(n).twtotal) * sizeof(float2); }
 static size_t smem_dense_ct(int n, int b) {
-  const int zc = 8, ln = (b / 2) * zc, pts = n * zc;
-  return (size_t)(kDenseRing * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
+  const int zc = 8, ln = kDenseRowsCt * (b / 2) * zc, pts = n * zc;
+  return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
 }
 
 // per-stage twiddle tables of one edge: stage s with m > 1 holds w_L^{j1 k}, j1 < m, k < r, L = r m

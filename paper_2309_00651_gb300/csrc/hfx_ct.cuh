@@ -232,7 +232,7 @@ k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ 
 // pass 2: forward FFT along x, Coulomb multiply + energy, inverse along x and z
 // ----------------------------------------------------------------------------------
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreadsPlane, 3)
+__global__ void __launch_bounds__(kThreadsPlane, 4)
 k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
                const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only) {
   using C = cx<T>;
@@ -319,7 +319,11 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   using G = DenseGeo<T, N>;
   constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
   constexpr int HB = B / 2;
-  constexpr int LN = HB * ZC;
+  constexpr int RPI = kDenseRowsCt;  // orbital rows per iteration
+  constexpr int RING = kDenseRingCt;
+  constexpr int LN = RPI * HB * ZC;  // lines of the interleaved tile [y][u][t][zz]
+  constexpr int ITERS = B / RPI;
+  static_assert(B % RPI == 0, "rows per iteration must divide the block");
   constexpr int PER = 16 / int(sizeof(C));
   constexpr int PLANE = N * N;
   constexpr StagePlan P = Plan<N>::p;
@@ -328,8 +332,8 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   const int zcn = min(ZC, N - z0);
   const int x = blockIdx.y;
   const int slot = slot_list[blockIdx.z];
-  C* tiles = reinterpret_cast<C*>(smem_raw);  // kDenseRing x [N][LN]
-  C* tw = tiles + kDenseRing * N * LN;
+  C* tiles = reinterpret_cast<C*>(smem_raw);  // RING x [N][LN]
+  C* tw = tiles + RING * N * LN;
   T* phiI = reinterpret_cast<T*>(tw + P.twtotal);  // [B][PTS]
   T* accI = phiI + B * PTS;                         // [B][PTS]
 
@@ -367,23 +371,25 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     }
   }
 
-  auto issue_row = [&](int r) {
-    if (r >= B) { cp_async_commit(); return; }
-    C* dstb = tiles + (r % kDenseRing) * N * LN;
+  // the couple tiles of orbital rows k*RPI .. k*RPI+RPI-1 -> ring buffer k % RING (empty couples and
+  // columns past N read as zero); an iteration past the block commits an empty group
+  auto issue_it = [&](int k) {
+    if (k >= ITERS) { cp_async_commit(); return; }
+    C* dstb = tiles + (k % RING) * N * LN;
     constexpr int VPR = ZC / PER;
-    for (int i = threadIdx.x; i < HB * N * VPR; i += NT) {
+    for (int i = threadIdx.x; i < RPI * HB * N * VPR; i += NT) {
       const int v = i % VPR;
       const int rest = i / VPR;
-      const int t = rest % HB, y = rest / HB;
-      const int c = cs + r * HB + t;
-      const bool ok_c = ((live >> (r * HB + t)) & 1u) && v * PER < zcn;
-      const C* src = W + ((long long)(c - c0) * N + x) * PLANE + (long long)y * N + z0 + v * PER;
-      cp_async16(dstb + y * LN + t * ZC + v * PER, ok_c ? (const void*)src : (const void*)W, ok_c ? 16 : 0);
+      const int ut = rest % (RPI * HB), y = rest / (RPI * HB);  // ut = u * HB + t
+      const int cr = k * RPI * HB + ut;                          // couple within the block pair
+      const bool ok_c = ((live >> cr) & 1u) && v * PER < zcn;
+      const C* src = W + ((long long)(cs + cr - c0) * N + x) * PLANE + (long long)y * N + z0 + v * PER;
+      cp_async16(dstb + y * LN + ut * ZC + v * PER, ok_c ? (const void*)src : (const void*)W, ok_c ? 16 : 0);
     }
     cp_async_commit();
   };
 #pragma unroll
-  for (int r = 0; r < kDenseRing - 1; ++r) issue_row(r);
+  for (int k = 0; k < RING - 1; ++k) issue_it(k);
 
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
 
@@ -400,11 +406,11 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     for (int j = 0; j < B; ++j) accJ[k][j] = T(0);
   }
 
-  for (int r = 0; r < B; ++r) {
-    issue_row(r + kDenseRing - 1);
-    cp_async_wait<kDenseRing - 1>();
+  for (int kk = 0; kk < ITERS; ++kk) {
+    issue_it(kk + RING - 1);
+    cp_async_wait<RING - 1>();
     __syncthreads();
-    if (r == 0) {
+    if (kk == 0) {
       // phi_J to registers (the staging area becomes accI after the barriers of the first row)
 #pragma unroll
       for (int k = 0; k < NP; ++k) {
@@ -413,24 +419,28 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
         for (int j = 0; j < B; ++j) phiJ[k][j] = ok[k] ? accI[j * PTS + p] : T(0);
       }
     }
-    C* buf = tiles + (r % kDenseRing) * N * LN;
+    C* buf = tiles + (kk % RING) * N * LN;
     stages<N, true, 0, P.ns, LN, 1, LN, NT>(buf, tw);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
       const int p = threadIdx.x + k * NT;
       if (!ok[k]) continue;
       const int y = p / ZC, zz = p - y * ZC;
-      const C* vp = buf + y * LN + zz;
-      const T phii = phiI[r * PTS + p];
-      T acci = T(0);
 #pragma unroll
-      for (int t = 0; t < HB; ++t) {
-        const C v = vp[t * ZC];
-        acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
-        accJ[k][2 * t] += v.x * phii;
-        accJ[k][2 * t + 1] += v.y * phii;
+      for (int u = 0; u < RPI; ++u) {
+        const int r = kk * RPI + u;
+        const C* vp = buf + y * LN + u * HB * ZC + zz;
+        const T phii = phiI[r * PTS + p];
+        T acci = T(0);
+#pragma unroll
+        for (int t = 0; t < HB; ++t) {
+          const C v = vp[t * ZC];
+          acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
+          accJ[k][2 * t] += v.x * phii;
+          accJ[k][2 * t + 1] += v.y * phii;
+        }
+        accI[r * PTS + p] = acci;
       }
-      accI[r * PTS + p] = acci;
     }
     __syncthreads();
   }
