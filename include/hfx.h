@@ -50,7 +50,9 @@ typedef enum {
   HFX_ERR_BAD_PAIR_LIST = -5,    /* (device-detected) an entry outside 0 <= i <= j < n_orb
                                     or more copies of a pair than fit; those entries were
                                     skipped                                               */
-  HFX_ERR_TIMEOUT = -6           /* (device-detected) a bounded device-side wait gave up  */
+  HFX_ERR_TIMEOUT = -6,          /* (device-detected) a bounded device-side wait gave up  */
+  HFX_ERR_NOT_POSITIVE_DEFINITE = -7 /* (device-detected) ACE construction: -M had a pivot
+                                    <= 0 in its Cholesky factorisation (include/hfx_ace.h) */
 } hfx_status;
 
 typedef enum {
@@ -165,7 +167,8 @@ hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
                              void* cuda_stream);
 
 /* hfx_sync_status -- wait for `cuda_stream` and return (then clear) the device-side error
- * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST or HFX_ERR_TIMEOUT. */
+ * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST, HFX_ERR_TIMEOUT or
+ * HFX_ERR_NOT_POSITIVE_DEFINITE. */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
 
 /* hfx_set_tuning -- schedule parameters of the context (what an autotuner varies; results do
