@@ -1,0 +1,60 @@
+// Internal interface between the host library (hfx_api.cu) and the ACE / screen kernels
+// (hfx_ace.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace hfx {
+namespace ace {
+
+constexpr int kFormGram = 0;  // C[a][b] = sum_p X[a][p] Y[b][p], split over p, FP64 partials
+constexpr int kFormLmul = 1;  // C[m][p] = scale sum_k T[m][k] Y[k][p] (+ C)
+
+// device error-word bit of a failed factorisation (the exchange path uses bits 0 and 1)
+constexpr int kErrNotPosDef = 4;
+
+struct MmArgs {
+  const double* x;     // Gram: X [nx][K] (row stride ldx); lmul: T [nx][K] (row stride ldx, even)
+  const double* y;     // Gram: Y [ny][K] (row stride ldy); lmul: Y [K][N] (row stride ldy)
+  double* out;         // Gram: partials [splits][nx][ny]; lmul: C [nx][N] (row stride ldo)
+  long long K;         // contraction length
+  long long ldx, ldy, ldo;
+  int nx, ny;          // rows of X / T and of Y (Gram)
+  long long N;         // lmul: columns
+  long long chunk;     // Gram: grid points per split (a multiple of 16)
+  int tiles_x, tiles_y, njobs;
+  int lower;           // lmul: T is lower triangular (skip k beyond the row tile)
+  int accumulate;      // lmul: C += ...
+  double scale;        // lmul
+};
+
+// Plan of a split contraction over the grid (Gram form) on `sm_count` SMs.
+struct GramPlan {
+  int tiles_x, tiles_y, splits, njobs;
+  long long chunk;
+};
+GramPlan gram_plan(int nx, int ny, long long K, int sm_count);
+size_t gram_partial_bytes(const GramPlan& p, int nx, int ny);
+
+// Launchers; all asynchronous on `st`, returning the launch error.  `fp32` selects FP32
+// products (operands rounded once to FP32), else FP64.
+cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx, const double* y, long long ldy,
+                 int ny, long long K, const GramPlan& plan, double* partials, int sm_count, cudaStream_t st);
+// out[a][b] = scale * sum_s partials[s][a][b] (fixed order), row stride ldo
+cudaError_t gram_reduce(const double* partials, int splits, int nx, int ny, double scale, double* out, long long ldo,
+                        cudaStream_t st);
+cudaError_t lmul(bool fp32, const double* t, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
+                 long long n, double scale, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st);
+// L (row-major n x n, zeros above the diagonal) with L L^T = -(M + M^T)/2; `work` holds n*n
+// doubles when the matrix does not fit in shared memory
+cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, double* work, int* err,
+                             int max_smem, cudaStream_t st);
+// linv = L^-1 (lower triangular, zeros above), row stride ldi
+cudaError_t tri_inverse(const double* l, int n, double* linv, long long ldi, cudaStream_t st);
+// screen compaction: keep i <= j with s[i][j] > cut or i == j, row-major; rowbuf holds n + 1 ints
+cudaError_t screen_compact(const double* s, int n, double cut, int32_t* pairs, int64_t* n_pairs, int* rowbuf,
+                           cudaStream_t st);
+
+}  // namespace ace
+}  // namespace hfx

@@ -16,6 +16,8 @@
 #include <vector>
 
 #include "../../include/hfx.h"
+#include "../../include/hfx_ace.h"
+#include "hfx_ace_internal.h"
 #include "hfx_internal.h"
 
 using namespace hfx;
@@ -893,6 +895,8 @@ extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
     HFX_CUDA_TRY(cudaStreamSynchronize(st));
   }
   if (h & kErrTimeout) return fail(HFX_ERR_TIMEOUT, "a device-side wait timed out");
+  if (h & ace::kErrNotPosDef)
+    return fail(HFX_ERR_NOT_POSITIVE_DEFINITE, "ACE construction: -(M + M^T)/2 is not positive definite; L and P are undefined");
   if (h & kErrBadPair) return fail(HFX_ERR_BAD_PAIR_LIST, "pair list had entries outside 0 <= i <= j < n_orb or too many copies of a pair; they were skipped");
   return HFX_OK;
 }
@@ -1128,5 +1132,158 @@ extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_byt
     }
     c->sched.clear();
   }
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// ACE operator and overlap screen (include/hfx_ace.h)
+// ------------------------------------------------------------------------------------
+static_assert((ace::kErrNotPosDef & (kErrBadPair | kErrTimeout)) == 0, "device error bits overlap");
+
+namespace {
+
+constexpr size_t kAceAlign = 256;
+size_t ace_round(size_t b) { return (b + kAceAlign - 1) / kAceAlign * kAceAlign; }
+long long even_ld(long long n) { return (n + 1) & ~1LL; }
+
+// workspace carve-up of one ACE / screen call; offsets in bytes from the workspace base
+struct AceWs {
+  size_t partials = 0, mat_a = 0, mat_b = 0, mat_c = 0, mat_d = 0, total = 0;
+};
+
+// build: partials | M | L | Cholesky work | L^-1
+AceWs ace_ws_build(const hfx_ctx* c, int n) {
+  AceWs w;
+  const ace::GramPlan gp = ace::gram_plan(n, n, c->N, c->sm_count);
+  const size_t sq = ace_round((size_t)n * n * sizeof(double));
+  w.partials = 0;
+  w.mat_a = ace_round(ace::gram_partial_bytes(gp, n, n));
+  w.mat_b = w.mat_a + sq;
+  w.mat_c = w.mat_b + sq;
+  w.mat_d = w.mat_c + sq;
+  w.total = w.mat_d + ace_round((size_t)n * even_ld(n) * sizeof(double));
+  return w;
+}
+// apply: partials | X [n_psi][even(n_orb)]
+AceWs ace_ws_apply(const hfx_ctx* c, int n_orb, int n_psi) {
+  AceWs w;
+  const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, c->N, c->sm_count);
+  w.mat_a = ace_round(ace::gram_partial_bytes(gp, n_psi, n_orb));
+  w.total = w.mat_a + ace_round((size_t)n_psi * even_ld(n_orb) * sizeof(double));
+  return w;
+}
+// screen: partials | s | row offsets
+AceWs ace_ws_screen(const hfx_ctx* c, int n) {
+  AceWs w;
+  const ace::GramPlan gp = ace::gram_plan(n, n, c->N, c->sm_count);
+  w.mat_a = ace_round(ace::gram_partial_bytes(gp, n, n));
+  w.mat_b = w.mat_a + ace_round((size_t)n * n * sizeof(double));
+  w.total = w.mat_b + ace_round((size_t)(n + 1) * sizeof(int));
+  return w;
+}
+
+bool misaligned8(const void* p) { return ((uintptr_t)p & 7u) != 0; }
+
+hfx_status ace_check_ws(const void* ws, size_t have, size_t need) {
+  if (!ws || have < need)
+    return fail(HFX_ERR_OOM, "ACE workspace too small: have %zu bytes, need %zu (hfx_ace_workspace_bytes)", have, need);
+  if (((uintptr_t)ws & (kAceAlign - 1)) != 0) return fail(HFX_ERR_INVALID_ARG, "ACE workspace must be 256-byte aligned");
+  return HFX_OK;
+}
+
+}  // namespace
+
+#define HFX_ACE_TRY(expr)                                                                           \
+  do {                                                                                              \
+    cudaError_t e_ = (expr);                                                                        \
+    if (e_ != cudaSuccess) return fail(HFX_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" size_t hfx_ace_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int32_t n_psi) {
+  if (!c || n_orb < 1 || n_psi < 0) return 0;
+  size_t need = std::max(ace_ws_build(c, n_orb).total, ace_ws_screen(c, n_orb).total);
+  if (n_psi > 0) need = std::max(need, ace_ws_apply(c, n_orb, n_psi).total);
+  return need;
+}
+
+extern "C" hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const double* w, int32_t n_orb, double* m,
+                                    double* l, double* p, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (!orbitals || !w || !p) return fail(HFX_ERR_INVALID_ARG, "orbitals, w and p must be non-NULL");
+  if (n_orb < 1) return fail(HFX_ERR_INVALID_ARG, "n_orb must be >= 1");
+  if (misaligned8(orbitals) || misaligned8(w) || misaligned8(p) || misaligned8(m) || misaligned8(l))
+    return fail(HFX_ERR_INVALID_ARG, "pointers must be 8-byte aligned");
+  const AceWs lay = ace_ws_build(c, n_orb);
+  if (hfx_status s = ace_check_ws(workspace, workspace_bytes, lay.total)) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* base = (char*)workspace;
+  double* part = (double*)(base + lay.partials);
+  double* M = m ? m : (double*)(base + lay.mat_a);
+  double* L = l ? l : (double*)(base + lay.mat_b);
+  double* work = (double*)(base + lay.mat_c);
+  double* Linv = (double*)(base + lay.mat_d);
+  const bool fp32 = c->prec == HFX_PREC_FP32;
+  const long long N = c->N;
+  const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
+  // M_kl = <psi_k | W_l> = (Omega/N) sum_p psi_k(p) W_l(p)
+  HFX_ACE_TRY(ace::gram(fp32, false, orbitals, N, n_orb, w, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_orb, n_orb, c->omega / (double)N, M, n_orb, st));
+  // L L^T = -(M + M^T)/2, then P_rows = L^-1 W_rows (P = W L^-T)
+  HFX_ACE_TRY(ace::cholesky_neg_sym(M, n_orb, n_orb, L, work, c->d_err, c->max_smem, st));
+  HFX_ACE_TRY(ace::tri_inverse(L, n_orb, Linv, even_ld(n_orb), st));
+  HFX_ACE_TRY(ace::lmul(fp32, Linv, even_ld(n_orb), n_orb, n_orb, true, w, N, N, 1.0, false, p, N, c->sm_count, st));
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_ace_apply(hfx_ctx* c, const double* p, int32_t n_orb, const double* psi, int32_t n_psi,
+                                    uint32_t flags, double* out, void* workspace, size_t workspace_bytes,
+                                    void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (!p || !psi || !out) return fail(HFX_ERR_INVALID_ARG, "p, psi and out must be non-NULL");
+  if (n_orb < 1 || n_psi < 1) return fail(HFX_ERR_INVALID_ARG, "n_orb and n_psi must be >= 1");
+  if (flags & ~HFX_ACCUMULATE) return fail(HFX_ERR_INVALID_ARG, "only HFX_ACCUMULATE is accepted in flags");
+  if (misaligned8(p) || misaligned8(psi) || misaligned8(out)) return fail(HFX_ERR_INVALID_ARG, "pointers must be 8-byte aligned");
+  const AceWs lay = ace_ws_apply(c, n_orb, n_psi);
+  if (hfx_status s = ace_check_ws(workspace, workspace_bytes, lay.total)) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* base = (char*)workspace;
+  double* part = (double*)(base + lay.partials);
+  double* X = (double*)(base + lay.mat_a);
+  const bool fp32 = c->prec == HFX_PREC_FP32;
+  const long long N = c->N;
+  const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, N, c->sm_count);
+  // X[i][k] = -<psi_i | P_k>, then out_i (+)= sum_k X[i][k] P_k
+  HFX_ACE_TRY(ace::gram(fp32, false, psi, N, n_psi, p, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_psi, n_orb, -c->omega / (double)N, X, even_ld(n_orb), st));
+  HFX_ACE_TRY(ace::lmul(fp32, X, even_ld(n_orb), n_psi, n_orb, false, p, N, N, 1.0, (flags & HFX_ACCUMULATE) != 0,
+                        out, N, c->sm_count, st));
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32_t n_orb, double cut, double* s,
+                                       int32_t* pairs, int64_t* n_pairs, void* workspace, size_t workspace_bytes,
+                                       void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (!orbitals || !pairs || !n_pairs) return fail(HFX_ERR_INVALID_ARG, "orbitals, pairs and n_pairs must be non-NULL");
+  if (n_orb < 1) return fail(HFX_ERR_INVALID_ARG, "n_orb must be >= 1");
+  if (!std::isfinite(cut) || cut < 0.0) return fail(HFX_ERR_INVALID_ARG, "cut must be finite and >= 0");
+  if (misaligned8(orbitals) || misaligned8(s) || misaligned8(n_pairs) || ((uintptr_t)pairs & 3u))
+    return fail(HFX_ERR_INVALID_ARG, "misaligned pointer");
+  const AceWs lay = ace_ws_screen(c, n_orb);
+  if (hfx_status st_ = ace_check_ws(workspace, workspace_bytes, lay.total)) return st_;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  char* base = (char*)workspace;
+  double* part = (double*)(base + lay.partials);
+  double* S = s ? s : (double*)(base + lay.mat_a);
+  int* rowbuf = (int*)(base + lay.mat_b);
+  const bool fp32 = c->prec == HFX_PREC_FP32;
+  const long long N = c->N;
+  const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
+  HFX_ACE_TRY(ace::gram(fp32, true, orbitals, N, n_orb, orbitals, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, st));
+  HFX_ACE_TRY(ace::screen_compact(S, n_orb, cut, pairs, n_pairs, rowbuf, st));
   return HFX_OK;
 }

@@ -1,4 +1,4 @@
-"""ctypes binding of libhfx (include/hfx.h): same entry points, torch tensors in, no compute here.
+"""ctypes binding of libhfx (include/hfx.h, include/hfx_ace.h): same entry points, torch tensors in, no compute here.
 
 Every step of the exchange path runs in the CUDA library; this module only marshals device
 pointers, sizes and the current CUDA stream.  If libhfx.so is missing it raises: there is no
@@ -17,18 +17,20 @@ LIB_PATH = os.path.join(_PKG, "libhfx.so")
 
 HFX_OK = 0
 STATUS_NAMES = {0: "HFX_OK", -1: "HFX_ERR_INVALID_ARG", -2: "HFX_ERR_UNSUPPORTED_GRID", -3: "HFX_ERR_OOM",
-                -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT"}
+                -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT",
+                -7: "HFX_ERR_NOT_POSITIVE_DEFINITE"}
 PRECISION = {"fp64": 0, "fp32": 1}
 KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
 HFX_ENERGY_ONLY = 0x1
 HFX_ACCUMULATE = 0x2
 HFX_ORBITALS_F32 = 0x4
 
-# every symbol include/hfx.h declares
+# every symbol include/hfx.h and include/hfx_ace.h declare
 EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
             "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
             "hfx_profile_read",
-            "hfx_last_error", "hfx_destroy")
+            "hfx_last_error", "hfx_destroy",
+            "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 
@@ -89,6 +91,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_last_error.restype = ctypes.c_char_p
     L.hfx_destroy.argtypes = [vp]
     L.hfx_destroy.restype = None
+    L.hfx_ace_workspace_bytes.argtypes = [vp, i32, i32]
+    L.hfx_ace_workspace_bytes.restype = sz
+    L.hfx_ace_build.argtypes = [vp, vp, vp, i32, vp, vp, vp, vp, sz, vp]
+    L.hfx_ace_build.restype = ctypes.c_int
+    L.hfx_ace_apply.argtypes = [vp, vp, i32, vp, i32, u32, vp, vp, sz, vp]
+    L.hfx_ace_apply.restype = ctypes.c_int
+    L.hfx_screen_pairs.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, sz, vp]
+    L.hfx_screen_pairs.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -196,6 +206,33 @@ def hfx_destroy(ctx) -> None:
     load_library().hfx_destroy(ctx)
 
 
+def hfx_ace_workspace_bytes(ctx, n_orb: int, n_psi: int = 0) -> int:
+    return int(load_library().hfx_ace_workspace_bytes(ctx, int(n_orb), int(n_psi)))
+
+
+def _nbytes(t: torch.Tensor) -> int:
+    return t.numel() * t.element_size()
+
+
+def hfx_ace_build(ctx, orbitals: torch.Tensor, w: torch.Tensor, m: Optional[torch.Tensor], l: Optional[torch.Tensor],
+                  p: torch.Tensor, workspace: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_ace_build(ctx, _ptr(orbitals), _ptr(w), int(orbitals.shape[0]), _ptr(m), _ptr(l), _ptr(p),
+                                        _ptr(workspace), _nbytes(workspace), _stream_handle(stream)))
+
+
+def hfx_ace_apply(ctx, p: torch.Tensor, psi: torch.Tensor, out: torch.Tensor, workspace: torch.Tensor,
+                  flags: int = 0, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_ace_apply(ctx, _ptr(p), int(p.shape[0]), _ptr(psi), int(psi.shape[0]), int(flags),
+                                        _ptr(out), _ptr(workspace), _nbytes(workspace), _stream_handle(stream)))
+
+
+def hfx_screen_pairs(ctx, orbitals: torch.Tensor, cut: float, s: Optional[torch.Tensor], pairs: torch.Tensor,
+                     n_pairs: torch.Tensor, workspace: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_screen_pairs(ctx, _ptr(orbitals), int(orbitals.shape[0]), float(cut), _ptr(s),
+                                           _ptr(pairs), _ptr(n_pairs), _ptr(workspace), _nbytes(workspace),
+                                           _stream_handle(stream)))
+
+
 # ---------------------------------------------------------------------------------------
 # convenience wrapper: one context + a torch-owned workspace
 # ---------------------------------------------------------------------------------------
@@ -261,6 +298,57 @@ class Exchange:
 
     def sync_status(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         hfx_sync_status(self.ctx, stream)
+
+    # ---- ACE operator and overlap screen (include/hfx_ace.h)
+
+    def _grid_rows(self, name: str, t: torch.Tensor) -> None:
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape[1:]) != self.grid:
+            raise ValueError(f"{name} must be a contiguous float64 CUDA tensor [n, {self.grid[0]}, {self.grid[1]}, "
+                             f"{self.grid[2]}]")
+
+    def _ace_workspace(self, n_orb: int, n_psi: int) -> torch.Tensor:
+        need = hfx_ace_workspace_bytes(self.ctx, n_orb, n_psi)
+        ws = getattr(self, "_ace_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._ace_ws = ws
+        return ws
+
+    def ace_build(self, phi: torch.Tensor, w: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
+        """(M, L, P) of the ACE operator built from orbitals phi and W = V_x phi (both FP64)."""
+        self._grid_rows("phi", phi)
+        self._grid_rows("w", w)
+        if w.shape != phi.shape:
+            raise ValueError("w must have the shape of phi")
+        n = phi.shape[0]
+        m = torch.empty((n, n), dtype=torch.float64, device=phi.device)
+        l = torch.empty((n, n), dtype=torch.float64, device=phi.device)
+        p = torch.empty_like(phi)
+        hfx_ace_build(self.ctx, phi, w, m, l, p, self._ace_workspace(n, 0), stream)
+        return m, l, p
+
+    def ace_apply(self, p: torch.Tensor, psi: torch.Tensor, out: Optional[torch.Tensor] = None,
+                  accumulate: bool = False, stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+        """V_x^ACE psi for every row of psi (FP64)."""
+        self._grid_rows("p", p)
+        self._grid_rows("psi", psi)
+        if out is None:
+            out = torch.zeros_like(psi) if accumulate else torch.empty_like(psi)
+        hfx_ace_apply(self.ctx, p, psi, out, self._ace_workspace(p.shape[0], psi.shape[0]),
+                      HFX_ACCUMULATE if accumulate else 0, stream)
+        return out
+
+    def screen_pairs(self, phi: torch.Tensor, cut: float, stream: Optional[torch.cuda.Stream] = None):
+        """(pairs int32 [P, 2] device tensor, s [n, n]) of the overlap screen s_ij > cut (diagonal kept).
+
+        Reads the pair count back to size the result, so it synchronises with `stream`."""
+        self._grid_rows("phi", phi)
+        n = phi.shape[0]
+        s = torch.empty((n, n), dtype=torch.float64, device=phi.device)
+        pairs = torch.empty((n * (n + 1) // 2, 2), dtype=torch.int32, device=phi.device)
+        count = torch.zeros(1, dtype=torch.int64, device=phi.device)
+        hfx_screen_pairs(self.ctx, phi, cut, s, pairs, count, self._ace_workspace(n, 0), stream)
+        return pairs[: int(count.item())], s
 
     def set_tuning(self, block: int = 8, batch_bytes: int = 1 << 30, pipeline: bool = True) -> None:
         hfx_set_tuning(self.ctx, block, batch_bytes, pipeline)

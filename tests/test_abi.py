@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads, exports every symbol include/hfx.h declares, and rejects
+"""The C-ABI library builds, loads, exports every symbol include/*.h declare, and rejects
 bad arguments on the host before touching a GPU (no compute calls here)."""
 import ctypes
 import os
@@ -17,8 +17,12 @@ def lib():
 
 
 def declared_symbols():
-    with open(os.path.join(ROOT, "include", "hfx.h")) as f:
-        text = f.read()
+    text = ""
+    inc = os.path.join(ROOT, "include")
+    for name in sorted(os.listdir(inc)):
+        if name.endswith(".h"):
+            with open(os.path.join(inc, name)) as f:
+                text += f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(hfx_[a-z_]+)\s*\(", text)))
 
@@ -26,7 +30,8 @@ def declared_symbols():
 def test_header_declares_the_boundary():
     names = declared_symbols()
     for n in ("hfx_create", "hfx_apply", "hfx_apply_batched", "hfx_set_workspace", "hfx_workspace_bytes",
-              "hfx_sync_status", "hfx_last_error", "hfx_destroy"):
+              "hfx_sync_status", "hfx_last_error", "hfx_destroy", "hfx_ace_workspace_bytes", "hfx_ace_build",
+              "hfx_ace_apply", "hfx_screen_pairs"):
         assert n in names
 
 
@@ -67,6 +72,10 @@ def test_host_side_argument_errors(lib):
     assert lib.hfx_apply(None, None, 16, None, 0, 0, None, None, None) == -1
     assert lib.hfx_sync_status(None, None) == -1
     assert lib.hfx_set_workspace(None, None, 0) == -1
+    assert lib.hfx_ace_workspace_bytes(None, 16, 0) == 0
+    assert lib.hfx_ace_build(None, None, None, 16, None, None, None, None, 0, None) == -1
+    assert lib.hfx_ace_apply(None, None, 16, None, 4, 0, None, None, 0, None) == -1
+    assert lib.hfx_screen_pairs(None, None, 16, 1e-6, None, None, None, None, 0, None) == -1
     lib.hfx_destroy(None)
 
 
