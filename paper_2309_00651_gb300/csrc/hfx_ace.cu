@@ -6,7 +6,7 @@
 //     over orbitals (<= a few hundred) and p over N grid points; each job takes one 128 x 128
 //     output tile and one run of grid points and writes an FP64 partial, and a second kernel
 //     sums the partials in a fixed order (deterministic, no atomics);
-//   * left multiply by a small matrix ("lmul"): C[m][p] = s T[m][k] Y[k][p] (+ C), k over
+//   * left multiply by a small matrix ("lmul"): C[m][p] = T[m][k] Y[k][p] (+ C), k over
 //     orbitals, p over the grid, one 128 x 128 output tile per job.
 // Both read FP64 operands through a three-deep cp.async ring of raw staging buffers, round
 // them once to the compute type in a double-buffered shared tile, and run an 8 x 8 register
@@ -51,7 +51,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // FP64 -> FP32, round to nearest even, from the IEEE-754 binary64/binary32 layouts with integer
 // operations: keep sign, rebias the exponent (1023 -> 127), round the 52-bit fraction to 23
-// bits.  Magnitudes below 2^-126 flush to zero, above the FP32 range go to infinity.
+// bits.  Magnitudes below 2^-126 flush to zero, above the FP32 range go to infinity.  (Measured
+// faster inside the contraction kernel than the hardware conversion.)
 __device__ __forceinline__ float f64_to_f32_rn(double v) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(v);
   const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
@@ -63,6 +64,27 @@ __device__ __forceinline__ float f64_to_f32_rn(double v) {
   f = (mag >= 0x47f00000u) ? 0x7f800000u : f;   // e > 1150: beyond it
   return __uint_as_float(f | (hi & 0x80000000u));
 }
+
+// FP32 -> FP64, exact for normal numbers (and +-0): keep sign, rebias the exponent
+// (127 -> 1023), widen the fraction.  FP32 subnormals flush to zero, infinities and NaNs map to
+// infinity.  Integer operations only, so the reduced-rate FP64 pipe is not touched.
+__device__ __forceinline__ double f32_to_f64_exact(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned mag = u & 0x7fffffffu;
+  unsigned hi = ((mag >> 3) + 0x38000000u) | (u & 0x80000000u);  // (e + 896) << 20 | top 20 fraction bits
+  unsigned lo = mag << 29;                                         // low 3 fraction bits
+  const bool tiny = mag < 0x00800000u, huge = mag >= 0x7f800000u;
+  hi = tiny ? (u & 0x80000000u) : (huge ? (0x7ff00000u | (u & 0x80000000u)) : hi);
+  lo = (tiny || huge) ? 0u : lo;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+template <typename T>
+__device__ __forceinline__ double to_double(T v);
+template <>
+__device__ __forceinline__ double to_double<float>(float v) { return f32_to_f64_exact(v); }
+template <>
+__device__ __forceinline__ double to_double<double>(double v) { return v; }
 
 template <typename T>
 __device__ __forceinline__ T to_compute(double v);
@@ -89,10 +111,14 @@ struct Vec4<double> {
   }
 };
 
-// Job of one block: an output tile and a stage count.  Gram jobs: tile (ta, tb) of split s,
-// job = s * tiles + tb * tiles_x + ta.  lmul jobs: tile (tm, tp), job = tp * tiles_x + tm.
+// A job is one output tile and its run of stages.  Gram jobs: tile (ta, tb) of split s,
+// job = s * tiles + tb * tiles_x + ta (the tiles of one split are neighbours, so they run
+// together and share the split's operand rows in L2).  lmul jobs: tile (tm, tp),
+// job = tp * tiles_x + tm.
 struct Cursor {
   int job, ks, nst;
+  int t0, t1;        // Gram: (ta, tb); lmul: (tm, tp)
+  long long p0, p1;  // Gram: the split's grid points [p0, p1)
 };
 
 }  // namespace
@@ -103,7 +129,7 @@ struct Cursor {
 template <typename T, int FORM, bool VEC16, bool ABS>
 __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* rawx = reinterpret_cast<double*>(smem_raw);  // [kStages][128][kRawStride]
+  double* rawx = reinterpret_cast<double*>(smem_raw);  // Gram: [kStages][128][kRawStride]; lmul: [kStages][16][128] T
   double* rawy = reinterpret_cast<double*>(smem_raw + kStages * kRawRowsBytes);
   // Gram: y staged like x ([128][kRawStride]); lmul: y staged as [16][128]
   constexpr size_t ybytes = FORM == kFormGram ? kRawRowsBytes : kRawColsBytes;
@@ -113,97 +139,90 @@ __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
 
-  auto stages_of = [&](int job) -> int {
-    if (job >= a.njobs) return 0;
+  auto decode = [&](Cursor& c) {
+    c.ks = 0;
+    c.nst = 0;
+    if (c.job >= a.njobs) return;
     if (FORM == kFormGram) {
-      const int s = job / (a.tiles_x * a.tiles_y);
-      const long long p0 = (long long)s * a.chunk;
-      const long long p1 = min(a.K, p0 + a.chunk);
-      return (int)((p1 - p0 + kBK - 1) / kBK);
+      const int tiles = a.tiles_x * a.tiles_y;
+      const int s = c.job / tiles, t = c.job - s * tiles;
+      c.t0 = t % a.tiles_x;
+      c.t1 = t / a.tiles_x;
+      c.p0 = (long long)s * a.chunk;
+      c.p1 = min(a.K, c.p0 + a.chunk);
+      c.nst = (int)((c.p1 - c.p0 + kBK - 1) / kBK);
     } else {
-      const int tm = job % a.tiles_x;
-      const long long k1 = a.lower ? min(a.K, (long long)(tm + 1) * kT) : a.K;
-      return (int)((k1 + kBK - 1) / kBK);
+      c.t0 = c.job % a.tiles_x;
+      c.t1 = c.job / a.tiles_x;
+      const long long k1 = a.lower ? min(a.K, (long long)(c.t0 + 1) * kT) : a.K;
+      c.nst = (int)((k1 + kBK - 1) / kBK);
     }
   };
   auto next = [&](Cursor& c) {
     if (++c.ks >= c.nst) {
       c.job += gridDim.x;
-      c.ks = 0;
-      c.nst = stages_of(c.job);
+      decode(c);
     }
   };
 
   // issue the cp.async copies of stage (job, ks) into ring slot `slot`
   auto issue = [&](const Cursor& c, int slot) {
     if (c.job >= a.njobs) return;
-    double* rx = rawx + (size_t)slot * kT * kRawStride;
     if (FORM == kFormGram) {
+      double* rx = rawx + (size_t)slot * kT * kRawStride;
       double* ry = rawy + (size_t)slot * kT * kRawStride;
-      const int tiles = a.tiles_x * a.tiles_y;
-      const int s = c.job / tiles, t = c.job % tiles;
-      const int ta = t % a.tiles_x, tb = t / a.tiles_x;
-      const long long p0 = (long long)s * a.chunk + (long long)c.ks * kBK;
-      const long long pend = min(a.K, (long long)(s + 1) * a.chunk);
-      const long long valid = pend - p0;  // >= 1
+      const long long p = c.p0 + (long long)c.ks * kBK;
+      const long long valid = c.p1 - p;  // >= 1
+      const double* X = reinterpret_cast<const double*>(a.x);
       if (VEC16) {
-        // 128 rows x 8 pieces of 16 B per operand
+        // 128 rows x 8 pieces of 16 B per operand; this thread: rows r0 + 32 q, piece pc
+        const int r0 = tid >> 3, pc = tid & 7;
+        const long long left = valid - 2 * pc;
+        const int bytes_in = left >= 2 ? 16 : (left == 1 ? 8 : 0);
+        const int gx = c.t0 * kT + r0, gy = c.t1 * kT + r0;
+        const double* sx = X + (long long)gx * a.ldx + p + 2 * pc;
+        const double* sy = a.y + (long long)gy * a.ldy + p + 2 * pc;
 #pragma unroll
-        for (int q = 0; q < (kT * 8) / kThreads; ++q) {
-          const int e = tid + q * kThreads;
-          const int row = e >> 3, pc = e & 7;
-          const long long left = valid - 2 * pc;
-          const int bytes_in = left >= 2 ? 16 : (left == 1 ? 8 : 0);
-          {
-            const int ga = ta * kT + row;
-            const int bx = ga < a.nx ? bytes_in : 0;
-            const double* src = a.x + (long long)(ga < a.nx ? ga : 0) * a.ldx + (bx ? p0 + 2 * pc : 0);
-            cp_async_zfill16(rx + row * kRawStride + 2 * pc, src, bx);
-          }
-          {
-            const int gb = tb * kT + row;
-            const int by = gb < a.ny ? bytes_in : 0;
-            const double* src = a.y + (long long)(gb < a.ny ? gb : 0) * a.ldy + (by ? p0 + 2 * pc : 0);
-            cp_async_zfill16(ry + row * kRawStride + 2 * pc, src, by);
-          }
+        for (int q = 0; q < 4; ++q) {
+          const bool vx = gx + 32 * q < a.nx, vy = gy + 32 * q < a.ny;
+          cp_async_zfill16(rx + (r0 + 32 * q) * kRawStride + 2 * pc, vx ? sx + q * 32 * a.ldx : X, vx ? bytes_in : 0);
+          cp_async_zfill16(ry + (r0 + 32 * q) * kRawStride + 2 * pc, vy ? sy + q * 32 * a.ldy : a.y, vy ? bytes_in : 0);
         }
       } else {
-#pragma unroll 4
-        for (int q = 0; q < (kT * kBK) / kThreads; ++q) {
-          const int e = tid + q * kThreads;
-          const int row = e >> 4, pc = e & 15;
-          const int bytes_in = pc < valid ? 8 : 0;
-          {
-            const int ga = ta * kT + row;
-            const int bx = ga < a.nx ? bytes_in : 0;
-            const double* src = a.x + (long long)(ga < a.nx ? ga : 0) * a.ldx + (bx ? p0 + pc : 0);
-            cp_async_zfill8(rx + row * kRawStride + pc, src, bx);
-          }
-          {
-            const int gb = tb * kT + row;
-            const int by = gb < a.ny ? bytes_in : 0;
-            const double* src = a.y + (long long)(gb < a.ny ? gb : 0) * a.ldy + (by ? p0 + pc : 0);
-            cp_async_zfill8(ry + row * kRawStride + pc, src, by);
-          }
+        // 128 rows x 16 pieces of 8 B per operand; this thread: rows r0 + 16 q, piece pc
+        const int r0 = tid >> 4, pc = tid & 15;
+        const int bytes_in = pc < valid ? 8 : 0;
+        const int gx = c.t0 * kT + r0, gy = c.t1 * kT + r0;
+        const double* sx = X + (long long)gx * a.ldx + p + pc;
+        const double* sy = a.y + (long long)gy * a.ldy + p + pc;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const bool vx = gx + 16 * q < a.nx, vy = gy + 16 * q < a.ny;
+          cp_async_zfill8(rx + (r0 + 16 * q) * kRawStride + pc, vx ? sx + q * 16 * a.ldx : X, vx ? bytes_in : 0);
+          cp_async_zfill8(ry + (r0 + 16 * q) * kRawStride + pc, vy ? sy + q * 16 * a.ldy : a.y, vy ? bytes_in : 0);
         }
       }
     } else {
-      double* ry = rawy + (size_t)slot * kBK * kT;
-      const int tm = c.job % a.tiles_x, tp = c.job / a.tiles_x;
+      // x: rows k0..k0+15 of the transposed, pre-rounded T, 128 entries each (16-byte pieces)
+      T* rx = reinterpret_cast<T*>(rawx + (size_t)slot * kT * kRawStride);
+      const T* Xt = reinterpret_cast<const T*>(a.x);
       const long long k0 = (long long)c.ks * kBK;
-      // x: T rows [128][16] (T has an even row stride and a 16-byte aligned base)
+      constexpr int EPP = 16 / sizeof(T);     // entries per piece
+      constexpr int PPR = kT / EPP;           // pieces per row
+      constexpr int PPT = kBK * PPR / kThreads;
 #pragma unroll
-      for (int q = 0; q < (kT * 8) / kThreads; ++q) {
+      for (int q = 0; q < PPT; ++q) {
         const int e = tid + q * kThreads;
-        const int row = e >> 3, pc = e & 7;
-        const int gm = tm * kT + row;
-        const long long left = a.K - (k0 + 2 * pc);
-        const int bytes_in = gm < a.nx ? (left >= 2 ? 16 : (left == 1 ? 8 : 0)) : 0;
-        const double* src = a.x + (long long)(gm < a.nx ? gm : 0) * a.ldx + (bytes_in ? k0 + 2 * pc : 0);
-        cp_async_zfill16(rx + row * kRawStride + 2 * pc, src, bytes_in);
+        const int kk = e / PPR, pc = e % PPR;
+        const int m = c.t0 * kT + pc * EPP;
+        const int left = a.nx - m;
+        const int bytes_in = (k0 + kk < a.K && left > 0) ? min(left, EPP) * (int)sizeof(T) : 0;
+        const T* src = bytes_in ? Xt + (k0 + kk) * a.ldx + m : Xt;
+        cp_async_zfill16(rx + kk * kT + pc * EPP, src, bytes_in);
       }
       // y: grid rows [16][128]
-      const long long p0 = (long long)tp * kT;
+      double* ry = rawy + (size_t)slot * kBK * kT;
+      const long long p0 = (long long)c.t1 * kT;
       if (VEC16) {
 #pragma unroll
         for (int q = 0; q < (kBK * 64) / kThreads; ++q) {
@@ -229,38 +248,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
     }
   };
 
-  // round ring slot `slot` into compute buffer `buf`
+  // ring slot `slot` -> compute buffer `buf` (rounded to T)
   auto convert = [&](int slot, int buf) {
-    const double* rx = rawx + (size_t)slot * kT * kRawStride;
     T* ox = cx + buf * kBK * kT;
     T* oy = cy + buf * kBK * kT;
-    {
+    if (FORM == kFormGram) {
       // transpose [128][16] -> [16][128]: thread (row, half) reads 8 consecutive doubles
       const int row = tid & (kT - 1), half = tid >> 7;
-      const double* src = rx + row * kRawStride + half * 8;
+      const double* srcx = rawx + (size_t)slot * kT * kRawStride + row * kRawStride + half * 8;
+      const double* srcy = rawy + (size_t)slot * kT * kRawStride + row * kRawStride + half * 8;
 #pragma unroll
       for (int j = 0; j < 8; j += 2) {
-        const double2 v = *reinterpret_cast<const double2*>(src + j);
-        double v0 = v.x, v1 = v.y;
-        if (ABS) { v0 = fabs(v0); v1 = fabs(v1); }
-        ox[(half * 8 + j) * kT + row] = to_compute<T>(v0);
-        ox[(half * 8 + j + 1) * kT + row] = to_compute<T>(v1);
-      }
-    }
-    if (FORM == kFormGram) {
-      const double* ry = rawy + (size_t)slot * kT * kRawStride;
-      const int row = tid & (kT - 1), half = tid >> 7;
-      const double* src = ry + row * kRawStride + half * 8;
-#pragma unroll
-      for (int j = 0; j < 8; j += 2) {
-        const double2 v = *reinterpret_cast<const double2*>(src + j);
-        double v0 = v.x, v1 = v.y;
-        if (ABS) { v0 = fabs(v0); v1 = fabs(v1); }
-        oy[(half * 8 + j) * kT + row] = to_compute<T>(v0);
-        oy[(half * 8 + j + 1) * kT + row] = to_compute<T>(v1);
+        const double2 u = *reinterpret_cast<const double2*>(srcx + j);
+        const double2 v = *reinterpret_cast<const double2*>(srcy + j);
+        ox[(half * 8 + j) * kT + row] = to_compute<T>(ABS ? fabs(u.x) : u.x);
+        ox[(half * 8 + j + 1) * kT + row] = to_compute<T>(ABS ? fabs(u.y) : u.y);
+        oy[(half * 8 + j) * kT + row] = to_compute<T>(ABS ? fabs(v.x) : v.x);
+        oy[(half * 8 + j + 1) * kT + row] = to_compute<T>(ABS ? fabs(v.y) : v.y);
       }
     } else {
-      // [16][128] -> [16][128]: thread (p, half) converts 8 rows of one column
+      // x is already in compute layout: a 16-byte copy
+      const uint4* srcx = reinterpret_cast<const uint4*>(rawx + (size_t)slot * kT * kRawStride);
+      uint4* dstx = reinterpret_cast<uint4*>(ox);
+      constexpr int NV = kBK * kT * (int)sizeof(T) / 16;
+#pragma unroll
+      for (int q = 0; q < NV / kThreads; ++q) dstx[tid + q * kThreads] = srcx[tid + q * kThreads];
+      // y: [16][128] doubles -> T, thread (p, half) converts 8 rows of one column
       const double* ry = rawy + (size_t)slot * kBK * kT;
       const int p = tid & (kT - 1), half = tid >> 7;
 #pragma unroll
@@ -284,34 +297,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
 
   auto store = [&](const Cursor& c) {
     if (FORM == kFormGram) {
-      const int tiles = a.tiles_x * a.tiles_y;
-      const int s = c.job / tiles, t = c.job % tiles;
-      const int ta = t % a.tiles_x, tb = t / a.tiles_x;
+      const int s = (int)(c.p0 / a.chunk);
       double* out = a.out + (size_t)s * a.nx * a.ny;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int ga = ta * kT + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        const int ga = c.t0 * kT + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
         if (ga >= a.nx) continue;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const int gb = tb * kT + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
-          if (gb < a.ny) out[(size_t)ga * a.ny + gb] = (double)acc2[i][j] + (double)acc[i][j];
+          const int gb = c.t1 * kT + (j < 4 ? tx * 4 + j : 64 + tx * 4 + j - 4);
+          if (gb < a.ny) out[(size_t)ga * a.ny + gb] = to_double<T>(acc2[i][j] + acc[i][j]);
         }
       }
     } else {
-      const int tm = c.job % a.tiles_x, tp = c.job / a.tiles_x;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        const int gm = tm * kT + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
+        const int gm = c.t0 * kT + (i < 4 ? ty * 4 + i : 64 + ty * 4 + i - 4);
         if (gm >= a.nx) continue;
         double* orow = a.out + (size_t)gm * a.ldo;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const long long p = (long long)tp * kT + h * 64 + tx * 4;
+          const long long p = (long long)c.t1 * kT + h * 64 + tx * 4;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if (p + j >= a.N) break;
-            double v = a.scale * ((double)acc2[i][h * 4 + j] + (double)acc[i][h * 4 + j]);
+            double v = to_double<T>(acc2[i][h * 4 + j] + acc[i][h * 4 + j]);
             if (a.accumulate) v += orow[p + j];
             orow[p + j] = v;
           }
@@ -324,10 +334,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
       for (int j = 0; j < 8; ++j) { acc[i][j] = T(0); acc2[i][j] = T(0); }
   };
 
-  Cursor cmp{(int)blockIdx.x, 0, 0};
-  cmp.nst = stages_of(cmp.job);
+  Cursor cmp;
+  cmp.job = (int)blockIdx.x;
+  decode(cmp);
   if (cmp.job >= a.njobs) return;
-  Cursor cnv = cmp, ld = cmp;
+  // stages of this block over all its jobs
+  int total = 0;
+  {
+    Cursor t;
+    t.job = cmp.job;
+    decode(t);
+    while (t.job < a.njobs) {
+      total += t.nst;
+      t.job += gridDim.x;
+      decode(t);
+    }
+  }
+  Cursor ld = cmp;
 
   // prologue: stages 0 .. kStages-2 in flight, stage 0 converted, stage kStages-1 in flight
 #pragma unroll
@@ -342,15 +365,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_ace_mm(const MmArgs a) {
   issue(ld, kStages - 1);
   cp_async_commit();
   next(ld);
-  next(cnv);
 
-  for (int it = 0; cmp.job < a.njobs; ++it) {
+  for (int it = 0; it < total; ++it) {
     cp_async_wait<kStages - 2>();  // stage it+1 landed (this thread's copies)
     __syncthreads();               // ... everyone's; buffer (it+1)&1 and slot it%kStages free
-    if (cnv.job < a.njobs) {
-      convert((it + 1) % kStages, (it + 1) & 1);
-      next(cnv);
-    }
+    if (it + 1 < total) convert((it + 1) % kStages, (it + 1) & 1);
     issue(ld, it % kStages);
     cp_async_commit();
     next(ld);
@@ -385,9 +404,13 @@ namespace ace {
 
 // ------------------------------------------------------------------------------------
 // fixed-order sum of the split partials: lane -> output element, warp w -> splits w, w+8, ...
+// Writes scale * sum to out[a][b] (FP64, row stride ldo) and/or to the transposed, rounded
+// copy outt[b][a] (compute type, row stride ldt) that the left multiply reads.
 // ------------------------------------------------------------------------------------
+template <typename T>
 __global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ part, int splits, int nx, int ny,
-                                                     double scale, double* __restrict__ out, long long ldo) {
+                                                     double scale, double* __restrict__ out, long long ldo,
+                                                     T* __restrict__ outt, long long ldt) {
   __shared__ double red[8][33];
   const long long total = (long long)nx * ny;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -407,66 +430,86 @@ __global__ void __launch_bounds__(256) k_gram_reduce(const double* __restrict__ 
     double t = 0.0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) t += red[q][lane];
+    t *= scale;
     const long long a = idx / ny, b = idx % ny;
-    out[a * ldo + b] = scale * t;
+    if (out) out[a * ldo + b] = t;
+    if (outt) outt[b * ldt + a] = to_compute<T>(t);
   }
 }
 
 // ------------------------------------------------------------------------------------
 // Cholesky factor of A = -(M + M^T)/2, right-looking, one block; A in shared memory when it
-// fits, else in `gwork`.  Step k: column k of L from column k of the updated A, then the
-// rank-one update of the trailing lower triangle (which never writes column k).
+// fits, else in `gwork`.  Step k: one thread takes the pivot's square root and reciprocals,
+// then column k of L and the rank-one update of the trailing lower triangle (which never
+// writes column k).
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ m, long long ldm, int n,
                                                    double* __restrict__ l, double* gwork, int use_smem, int* err) {
-  extern __shared__ __align__(16) double sw[];
+  extern __shared__ __align__(16) double sw[];  // [n][n] lower triangle of A (when it fits), then col[n]
+  __shared__ double piv[2];
+  __shared__ int bad;
   double* A = use_smem ? sw : gwork;
+  double* col = use_smem ? sw + (size_t)n * n : gwork + (size_t)n * n;
   const int tid = threadIdx.y * 32 + threadIdx.x;
   const int nthr = blockDim.x * blockDim.y;
+  if (tid == 0) bad = 0;
   for (long long idx = tid; idx < (long long)n * n; idx += nthr) {
     const int i = (int)(idx / n), j = (int)(idx % n);
     if (j <= i) A[idx] = -0.5 * (m[(long long)i * ldm + j] + m[(long long)j * ldm + i]);
     else l[idx] = 0.0;
   }
   __syncthreads();
-  bool bad = false;
   for (int k = 0; k < n; ++k) {
-    const double d = A[(long long)k * n + k];
-    bad |= !(d > 0.0);
-    const double sd = sqrt(d), inv_d = 1.0 / d;
-    for (int i = k + tid; i < n; i += nthr) l[(long long)i * n + k] = A[(long long)i * n + k] / sd;
+    // column k of the updated A into a vector (read along rows of A: one pass per step)
+    for (int i = k + tid; i < n; i += nthr) col[i] = A[(long long)i * n + k];
+    if (tid == 0) {
+      const double d = A[(long long)k * n + k];
+      if (!(d > 0.0)) bad = 1;
+      const double r = rsqrt(d);
+      piv[0] = r;      // column scale 1/sqrt(d)
+      piv[1] = r * r;  // update scale 1/d
+    }
+    __syncthreads();
+    const double inv_sd = piv[0], inv_d = piv[1];
+    for (int i = k + tid; i < n; i += nthr) l[(long long)i * n + k] = col[i] * inv_sd;
     for (int i = k + 1 + threadIdx.y; i < n; i += blockDim.y) {
-      const double aik = A[(long long)i * n + k] * inv_d;
-      for (int j = k + 1 + threadIdx.x; j <= i; j += 32) A[(long long)i * n + j] -= aik * A[(long long)j * n + k];
+      const double aik = col[i] * inv_d;
+      for (int j = k + 1 + threadIdx.x; j <= i; j += 32) A[(long long)i * n + j] -= aik * col[j];
     }
     __syncthreads();
   }
-  if (bad && tid == 0) atomicOr(err, kErrNotPosDef);
+  if (tid == 0 && bad) atomicOr(err, kErrNotPosDef);
 }
 
 // ------------------------------------------------------------------------------------
 // L^-1 by forward substitution, one block per column j; L's rows j..n-1 are staged in shared
-// memory when they fit.
+// memory when they fit.  Column j of L^-1 is row j of the transposed output linvt (compute
+// type, row stride ldt), which the left multiply reads as its small operand.
 // ------------------------------------------------------------------------------------
-template <bool SMEM_L>
-__global__ void __launch_bounds__(128) k_tri_inverse(const double* __restrict__ l, int n, double* __restrict__ linv,
-                                                     long long ldi) {
+template <bool SMEM_L, typename T>
+__global__ void __launch_bounds__(128) k_tri_inverse(const double* __restrict__ l, int n, T* __restrict__ linvt,
+                                                     long long ldt) {
   extern __shared__ __align__(16) double sm[];
   double* x = sm;            // [n]
-  double* Ls = sm + n;       // [n][n] when staged
+  double* dinv = sm + n;     // [n] reciprocal diagonal
+  double* Ls = sm + 2 * n;   // [n][n] when staged
   const int j = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = (i == j) ? 1.0 : 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    x[i] = (i == j) ? 1.0 : 0.0;
+    if (i >= j) dinv[i] = 1.0 / l[(long long)i * n + i];
+  }
   if (SMEM_L)
     for (long long idx = (long long)j * n + threadIdx.x; idx < (long long)n * n; idx += blockDim.x) Ls[idx] = l[idx];
   const double* L = SMEM_L ? Ls : l;
   __syncthreads();
+  T* row = linvt + (long long)j * ldt;
   for (int k = j; k < n; ++k) {
-    const double xk = x[k] / L[(long long)k * n + k];
-    if (threadIdx.x == 0) linv[(long long)k * ldi + j] = xk;
+    const double xk = x[k] * dinv[k];
+    if (threadIdx.x == 0) row[k] = to_compute<T>(xk);
     for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) x[i] -= L[(long long)i * n + k] * xk;
     __syncthreads();
   }
-  for (int i = threadIdx.x; i < j; i += blockDim.x) linv[(long long)i * ldi + j] = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) row[i] = T(0);
 }
 
 // ------------------------------------------------------------------------------------
@@ -588,7 +631,7 @@ cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx,
   a.nx = nx; a.ny = ny; a.N = 0;
   a.chunk = plan.chunk;
   a.tiles_x = plan.tiles_x; a.tiles_y = plan.tiles_y; a.njobs = plan.njobs;
-  a.lower = 0; a.accumulate = 0; a.scale = 1.0;
+  a.lower = 0; a.accumulate = 0;
   const bool v16 = (ldx % 2 == 0) && (ldy % 2 == 0) && aligned16(x) && aligned16(y);
 #define HFX_ACE_GRAM(TT, V, AB) return launch_mm<TT, kFormGram, V, AB>(a, sm_count, st)
   if (fp32) {
@@ -601,25 +644,30 @@ cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx,
 #undef HFX_ACE_GRAM
 }
 
-cudaError_t gram_reduce(const double* partials, int splits, int nx, int ny, double scale, double* out, long long ldo,
-                        cudaStream_t st) {
+cudaError_t gram_reduce(bool fp32, const double* partials, int splits, int nx, int ny, double scale, double* out,
+                        long long ldo, void* outt, long long ldt, cudaStream_t st) {
   const long long total = (long long)nx * ny;
   const int grid = (int)((total + 31) / 32);
-  k_gram_reduce<<<grid, 256, 0, st>>>(partials, splits, nx, ny, scale, out, ldo);
+  if (fp32)
+    k_gram_reduce<float><<<grid, 256, 0, st>>>(partials, splits, nx, ny, scale, out, ldo, (float*)outt, ldt);
+  else
+    k_gram_reduce<double><<<grid, 256, 0, st>>>(partials, splits, nx, ny, scale, out, ldo, (double*)outt, ldt);
   return cudaGetLastError();
 }
 
-cudaError_t lmul(bool fp32, const double* t, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
-                 long long n, double scale, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st) {
+long long lmul_ldt(bool fp32, int m) { return fp32 ? (m + 3) / 4 * 4 : (m + 1) / 2 * 2; }
+
+cudaError_t lmul(bool fp32, const void* tt, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
+                 long long n, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st) {
   MmArgs a{};
-  a.x = t; a.y = y; a.out = out;
+  a.x = tt; a.y = y; a.out = out;
   a.K = k; a.ldx = ldt; a.ldy = ldy; a.ldo = ldo;
   a.nx = m; a.ny = 0; a.N = n;
   a.chunk = 0;
   a.tiles_x = (m + kT - 1) / kT;
   a.tiles_y = (int)((n + kT - 1) / kT);
   a.njobs = a.tiles_x * a.tiles_y;
-  a.lower = lower ? 1 : 0; a.accumulate = accumulate ? 1 : 0; a.scale = scale;
+  a.lower = lower ? 1 : 0; a.accumulate = accumulate ? 1 : 0;
   const bool v16 = (ldy % 2 == 0) && aligned16(y);
   if (fp32) {
     if (v16) return launch_mm<float, kFormLmul, true, false>(a, sm_count, st);
@@ -631,8 +679,8 @@ cudaError_t lmul(bool fp32, const double* t, long long ldt, int m, int k, bool l
 
 cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, double* work, int* err, int max_smem,
                              cudaStream_t st) {
-  const size_t need = (size_t)n * n * sizeof(double);
-  const bool use_smem = need <= (size_t)max_smem;
+  const size_t need = ((size_t)n * n + n) * sizeof(double);
+  const bool use_smem = need + 64 <= (size_t)max_smem;
   if (use_smem) {
     const cudaError_t e = cudaFuncSetAttribute(k_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e != cudaSuccess) return e;
@@ -641,21 +689,23 @@ cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, d
   return cudaGetLastError();
 }
 
-cudaError_t tri_inverse(const double* l, int n, double* linv, long long ldi, cudaStream_t st) {
-  int dev = 0, max_smem = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  const size_t full = ((size_t)n * n + n) * sizeof(double);
+template <typename T>
+static cudaError_t tri_inverse_t(const double* l, int n, T* linvt, long long ldt, int max_smem, cudaStream_t st) {
+  const size_t full = ((size_t)n * n + 2 * n) * sizeof(double);
   if (full <= (size_t)max_smem) {
-    e = cudaFuncSetAttribute(k_tri_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_tri_inverse<true, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
     if (e != cudaSuccess) return e;
-    k_tri_inverse<true><<<n, 128, full, st>>>(l, n, linv, ldi);
+    k_tri_inverse<true, T><<<n, 128, full, st>>>(l, n, linvt, ldt);
   } else {
-    k_tri_inverse<false><<<n, 128, n * sizeof(double), st>>>(l, n, linv, ldi);
+    k_tri_inverse<false, T><<<n, 128, 2 * n * sizeof(double), st>>>(l, n, linvt, ldt);
   }
   return cudaGetLastError();
+}
+
+cudaError_t tri_inverse(bool fp32, const double* l, int n, void* linvt, long long ldt, int max_smem, cudaStream_t st) {
+  return fp32 ? tri_inverse_t(l, n, (float*)linvt, ldt, max_smem, st)
+              : tri_inverse_t(l, n, (double*)linvt, ldt, max_smem, st);
 }
 
 cudaError_t screen_compact(const double* s, int n, double cut, int32_t* pairs, int64_t* n_pairs, int* rowbuf,

@@ -9,13 +9,14 @@ namespace hfx {
 namespace ace {
 
 constexpr int kFormGram = 0;  // C[a][b] = sum_p X[a][p] Y[b][p], split over p, FP64 partials
-constexpr int kFormLmul = 1;  // C[m][p] = scale sum_k T[m][k] Y[k][p] (+ C)
+constexpr int kFormLmul = 1;  // C[m][p] = sum_k T[m][k] Y[k][p] (+ C)
 
 // device error-word bit of a failed factorisation (the exchange path uses bits 0 and 1)
 constexpr int kErrNotPosDef = 4;
 
 struct MmArgs {
-  const double* x;     // Gram: X [nx][K] (row stride ldx); lmul: T [nx][K] (row stride ldx, even)
+  const void* x;       // Gram: X [nx][K] FP64 (row stride ldx); lmul: T^T [K][ldx] in the compute type,
+                       //   rows 16-byte aligned
   const double* y;     // Gram: Y [ny][K] (row stride ldy); lmul: Y [K][N] (row stride ldy)
   double* out;         // Gram: partials [splits][nx][ny]; lmul: C [nx][N] (row stride ldo)
   long long K;         // contraction length
@@ -26,7 +27,6 @@ struct MmArgs {
   int tiles_x, tiles_y, njobs;
   int lower;           // lmul: T is lower triangular (skip k beyond the row tile)
   int accumulate;      // lmul: C += ...
-  double scale;        // lmul
 };
 
 // Plan of a split contraction over the grid (Gram form) on `sm_count` SMs.
@@ -41,17 +41,21 @@ size_t gram_partial_bytes(const GramPlan& p, int nx, int ny);
 // products (operands rounded once to FP32), else FP64.
 cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx, const double* y, long long ldy,
                  int ny, long long K, const GramPlan& plan, double* partials, int sm_count, cudaStream_t st);
-// out[a][b] = scale * sum_s partials[s][a][b] (fixed order), row stride ldo
-cudaError_t gram_reduce(const double* partials, int splits, int nx, int ny, double scale, double* out, long long ldo,
-                        cudaStream_t st);
-cudaError_t lmul(bool fp32, const double* t, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
-                 long long n, double scale, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st);
-// L (row-major n x n, zeros above the diagonal) with L L^T = -(M + M^T)/2; `work` holds n*n
-// doubles when the matrix does not fit in shared memory
+// v = scale * sum_s partials[s][a][b] (fixed order) to out[a][b] (FP64, row stride ldo) and/or
+// to outt[b][a] (FP32 if fp32 else FP64, row stride ldt); either may be NULL
+cudaError_t gram_reduce(bool fp32, const double* partials, int splits, int nx, int ny, double scale, double* out,
+                        long long ldo, void* outt, long long ldt, cudaStream_t st);
+// row stride of a transposed small operand with m columns (16-byte rows)
+long long lmul_ldt(bool fp32, int m);
+// out[i][p] (+)= sum_k T[i][k] Y[k][p] with T given transposed, tt[k][i] (compute type)
+cudaError_t lmul(bool fp32, const void* tt, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
+                 long long n, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st);
+// L (row-major n x n, zeros above the diagonal) with L L^T = -(M + M^T)/2; `work` holds
+// n*n + n doubles when the matrix does not fit in shared memory
 cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, double* work, int* err,
                              int max_smem, cudaStream_t st);
-// linv = L^-1 (lower triangular, zeros above), row stride ldi
-cudaError_t tri_inverse(const double* l, int n, double* linv, long long ldi, cudaStream_t st);
+// linvt = (L^-1)^T in the compute type (upper triangular, zeros below), row stride ldt
+cudaError_t tri_inverse(bool fp32, const double* l, int n, void* linvt, long long ldt, int max_smem, cudaStream_t st);
 // screen compaction: keep i <= j with s[i][j] > cut or i == j, row-major; rowbuf holds n + 1 ints
 cudaError_t screen_compact(const double* s, int n, double cut, int32_t* pairs, int64_t* n_pairs, int* rowbuf,
                            cudaStream_t st);

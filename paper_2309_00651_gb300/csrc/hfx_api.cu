@@ -1144,7 +1144,6 @@ namespace {
 
 constexpr size_t kAceAlign = 256;
 size_t ace_round(size_t b) { return (b + kAceAlign - 1) / kAceAlign * kAceAlign; }
-long long even_ld(long long n) { return (n + 1) & ~1LL; }
 
 // workspace carve-up of one ACE / screen call; offsets in bytes from the workspace base
 struct AceWs {
@@ -1155,21 +1154,21 @@ struct AceWs {
 AceWs ace_ws_build(const hfx_ctx* c, int n) {
   AceWs w;
   const ace::GramPlan gp = ace::gram_plan(n, n, c->N, c->sm_count);
-  const size_t sq = ace_round((size_t)n * n * sizeof(double));
+  const size_t sq = ace_round(((size_t)n * n + n) * sizeof(double));
   w.partials = 0;
   w.mat_a = ace_round(ace::gram_partial_bytes(gp, n, n));
   w.mat_b = w.mat_a + sq;
   w.mat_c = w.mat_b + sq;
   w.mat_d = w.mat_c + sq;
-  w.total = w.mat_d + ace_round((size_t)n * even_ld(n) * sizeof(double));
+  w.total = w.mat_d + ace_round((size_t)n * ace::lmul_ldt(false, n) * sizeof(double));
   return w;
 }
-// apply: partials | X [n_psi][even(n_orb)]
+// apply: partials | X^T [n_orb][ldt(n_psi)]
 AceWs ace_ws_apply(const hfx_ctx* c, int n_orb, int n_psi) {
   AceWs w;
   const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, c->N, c->sm_count);
   w.mat_a = ace_round(ace::gram_partial_bytes(gp, n_psi, n_orb));
-  w.total = w.mat_a + ace_round((size_t)n_psi * even_ld(n_orb) * sizeof(double));
+  w.total = w.mat_a + ace_round((size_t)n_orb * ace::lmul_ldt(false, n_psi) * sizeof(double));
   return w;
 }
 // screen: partials | s | row offsets
@@ -1222,17 +1221,18 @@ extern "C" hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const do
   double* M = m ? m : (double*)(base + lay.mat_a);
   double* L = l ? l : (double*)(base + lay.mat_b);
   double* work = (double*)(base + lay.mat_c);
-  double* Linv = (double*)(base + lay.mat_d);
+  void* Linvt = base + lay.mat_d;
   const bool fp32 = c->prec == HFX_PREC_FP32;
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
   // M_kl = <psi_k | W_l> = (Omega/N) sum_p psi_k(p) W_l(p)
   HFX_ACE_TRY(ace::gram(fp32, false, orbitals, N, n_orb, w, N, n_orb, N, gp, part, c->sm_count, st));
-  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_orb, n_orb, c->omega / (double)N, M, n_orb, st));
+  HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, M, n_orb, nullptr, 0, st));
   // L L^T = -(M + M^T)/2, then P_rows = L^-1 W_rows (P = W L^-T)
   HFX_ACE_TRY(ace::cholesky_neg_sym(M, n_orb, n_orb, L, work, c->d_err, c->max_smem, st));
-  HFX_ACE_TRY(ace::tri_inverse(L, n_orb, Linv, even_ld(n_orb), st));
-  HFX_ACE_TRY(ace::lmul(fp32, Linv, even_ld(n_orb), n_orb, n_orb, true, w, N, N, 1.0, false, p, N, c->sm_count, st));
+  const long long ldt = ace::lmul_ldt(fp32, n_orb);
+  HFX_ACE_TRY(ace::tri_inverse(fp32, L, n_orb, Linvt, ldt, c->max_smem, st));
+  HFX_ACE_TRY(ace::lmul(fp32, Linvt, ldt, n_orb, n_orb, true, w, N, N, false, p, N, c->sm_count, st));
   return HFX_OK;
 }
 
@@ -1250,15 +1250,16 @@ extern "C" hfx_status hfx_ace_apply(hfx_ctx* c, const double* p, int32_t n_orb, 
   cudaStream_t st = (cudaStream_t)cuda_stream;
   char* base = (char*)workspace;
   double* part = (double*)(base + lay.partials);
-  double* X = (double*)(base + lay.mat_a);
+  void* Xt = base + lay.mat_a;
   const bool fp32 = c->prec == HFX_PREC_FP32;
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, N, c->sm_count);
-  // X[i][k] = -<psi_i | P_k>, then out_i (+)= sum_k X[i][k] P_k
+  // X[i][k] = -<psi_i | P_k> (held transposed), then out_i (+)= sum_k X[i][k] P_k
   HFX_ACE_TRY(ace::gram(fp32, false, psi, N, n_psi, p, N, n_orb, N, gp, part, c->sm_count, st));
-  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_psi, n_orb, -c->omega / (double)N, X, even_ld(n_orb), st));
-  HFX_ACE_TRY(ace::lmul(fp32, X, even_ld(n_orb), n_psi, n_orb, false, p, N, N, 1.0, (flags & HFX_ACCUMULATE) != 0,
-                        out, N, c->sm_count, st));
+  const long long ldt = ace::lmul_ldt(fp32, n_psi);
+  HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_psi, n_orb, -c->omega / (double)N, nullptr, 0, Xt, ldt, st));
+  HFX_ACE_TRY(ace::lmul(fp32, Xt, ldt, n_psi, n_orb, false, p, N, N, (flags & HFX_ACCUMULATE) != 0, out, N, c->sm_count,
+                        st));
   return HFX_OK;
 }
 
@@ -1283,7 +1284,7 @@ extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
   HFX_ACE_TRY(ace::gram(fp32, true, orbitals, N, n_orb, orbitals, N, n_orb, N, gp, part, c->sm_count, st));
-  HFX_ACE_TRY(ace::gram_reduce(part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, st));
+  HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, nullptr, 0, st));
   HFX_ACE_TRY(ace::screen_compact(S, n_orb, cut, pairs, n_pairs, rowbuf, st));
   return HFX_OK;
 }
