@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-ace", action="store_true", help="skip the ACE / screen rows")
     return ap.parse_args()
 
 
@@ -140,6 +141,73 @@ def oracle_rate(phi, pairs, lattice, n_sample, seed=0):
     E, V = O.exchange(phi, sub, lattice, alpha=0.25)
     dt = time.perf_counter() - t0
     return len(sub) / dt, dt, sub, E, V
+
+
+FP32_FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
+FP64_PEAK_TFLOPS = 1.25                                  # nominal FP64 rate of this part
+
+
+def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
+    """ACE construction / application (Sec. 2.1, Eq. vx_ace) and the overlap screen on this
+    workload, W = V_x phi from the exchange call: call times, per-kernel roofline of the split
+    grid contraction and of the left multiply, identities that hold at any size.  Returns the
+    row and (M, P) for the oracle comparison of the CPU-baseline leg."""
+    import torch
+    n_orb, N = phi.shape[0], phi[0].numel()
+    M, Lf, Pm = ex.ace_build(phi, V)
+    Y = ex.ace_apply(Pm, phi)
+    ex.sync_status()
+    out = torch.empty_like(phi)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_build = timed(lambda: ex.ace_build(phi, V))
+    t_apply = timed(lambda: ex.ace_apply(Pm, phi, out=out))
+    t_screen = timed(lambda: ex.screen_pairs(phi, 1e-6))
+    # per-kernel device time over `reps` applications (CUDA events around each launch)
+    hfx.hfx_profile_enable(ex.ctx, True)
+    hfx.hfx_ace_profile_read(ex.ctx)
+    for _ in range(reps):
+        ex.ace_apply(Pm, phi, out=out)
+    torch.cuda.synchronize()
+    hfx.hfx_profile_enable(ex.ctx, False)
+    kp = hfx.hfx_ace_profile_read(ex.ctx)
+    g_ms = kp["ace_gram"]["ms"] / max(1, kp["ace_gram"]["launches"])
+    l_ms = kp["ace_lmul"]["ms"] / max(1, kp["ace_lmul"]["launches"])
+    flops = 2.0 * n_orb * n_orb * N            # one contraction over the grid, n_psi = n_orb
+    gram_bytes = 2.0 * n_orb * N * 8           # both FP64 operands read once
+    lmul_bytes = 2.0 * n_orb * N * 8           # Y read once, C written once
+    peak_tf = FP32_FFMA_PEAK_TFLOPS if precision == "fp32" else FP64_PEAK_TFLOPS
+    hbm = measured_peak_hbm()[0]
+
+    def roof(ms, nbytes, kernel):
+        tf = flops / (ms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": kernel, "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": tf / peak_tf, "avg_launch_ms": ms, "alg_flops_per_launch": flops,
+                "alg_bytes_per_launch": nbytes, "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                "peak_kind": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if precision == "fp32"
+                              else "nominal FP64 rate")}
+
+    row = {
+        "ms": {"build": t_build, "apply": t_apply, "screen": t_screen},
+        "apply_vs_exchange_call": None,
+        "roofline": roof(g_ms, gram_bytes, "k_ace_mm (split grid contraction, <psi|P>)"),
+        "roofline_lmul": roof(l_ms, lmul_bytes, "k_ace_mm (left multiply, -X P)"),
+        "kernel_ms_per_apply": {k: v["ms"] / reps for k, v in kp.items()},
+        "checks": {"span_rel_err": float(torch.linalg.norm(Y - V) / torch.linalg.norm(V)),
+                   "half_trace_M_vs_E_rel": abs(0.5 * float(torch.trace(M)) - E) / abs(E)},
+        "n_orb": n_orb, "n_psi": n_orb, "precision": precision,
+    }
+    return row, (M, Pm)
 
 
 def run_reference(args):
@@ -356,6 +424,11 @@ def main():
         "checks": checks,
     }
 
+    ace_out = None
+    if rank == 0 and not args.no_ace:
+        line["ace"], ace_out = ace_rows(ex, phi, V, E_val, w, args.precision, hfx)
+        line["ace"]["apply_vs_exchange_call"] = ms_step / line["ace"]["ms"]["apply"]
+
     if rank == 0 and args.precision == "fp32" and not args.no_fp64_compare:
         ex64 = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision="fp64")
         ex64.ensure_workspace(n_orb, P)
@@ -398,6 +471,21 @@ def main():
                                     "E_rel": abs(Es.item() - E_o) / abs(E_o),
                                     "V_rel": float(np.linalg.norm(Vs_np - V_o) / np.linalg.norm(V_o))},
         }
+        if ace_out is not None:
+            # the ACE oracle at full size on the same phi and W (numpy FP64, default BLAS threads)
+            from oracle import ace_oracle as AO
+            M_g, P_g = ace_out
+            t0 = time.time()
+            M0, _, P0 = AO.ace_build(phi_np, V.cpu().numpy(), np.asarray(w.lattice))
+            dt_ace = time.time() - t0
+
+            def rel(a, b):
+                return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+            line["cpu_baseline"]["ace_build"] = {
+                "seconds": dt_ace, "gpu_ms": line["ace"]["ms"]["build"],
+                "sample": f"full ACE construction, {n_orb} orbitals on {N} points",
+                "M_rel_gpu_vs_oracle": rel(M_g.cpu().numpy(), M0), "P_rel_gpu_vs_oracle": rel(P_g.cpu().numpy(), P0)}
 
     if rank == 0:
         print(json.dumps(line), flush=True)

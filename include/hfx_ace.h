@@ -73,6 +73,13 @@ hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32_t n_orb, d
                             int32_t* pairs, int64_t* n_pairs, void* workspace, size_t workspace_bytes,
                             void* cuda_stream);
 
+/* hfx_ace_profile_read -- per-kernel device time of the calls above while hfx_profile_enable
+ * is on (CUDA events around each launch on the call's stream): summed milliseconds and launch
+ * counts since the last read, then reset; index 0 the split grid contractions (M, <psi|P>, s),
+ * 1 the left multiplies (P, V_x^ACE psi), 2 the small steps (partial-sum reduction, Cholesky
+ * factorisation, triangular inverse, pair compaction).  Not for use inside stream capture. */
+hfx_status hfx_ace_profile_read(hfx_ctx* c, double ms[3], int64_t launches[3]);
+
 #ifdef __cplusplus
 }
 #endif

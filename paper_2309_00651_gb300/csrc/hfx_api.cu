@@ -233,9 +233,13 @@ struct hfx_ctx {
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double prof_ms[9] = {};
+  long long prof_n[9] = {};
 };
 
-enum { kProfStage = 0, kProfFwd = 1, kProfX = 2, kProfAcc = 3, kProfEnergy = 4, kProfAccGeneric = 5, kProfSlots = 6 };
+// slots 0..5: exchange passes (hfx_profile_read); 6..8: ACE / screen kernels (hfx_ace_profile_read)
+enum { kProfStage = 0, kProfFwd = 1, kProfX = 2, kProfAcc = 3, kProfEnergy = 4, kProfAccGeneric = 5, kProfSlots = 6,
+       kProfAceGram = 6, kProfAceLmul = 7, kProfAceSmall = 8, kProfAllSlots = 9 };
 
 static cudaEvent_t prof_event(hfx_ctx* c) {
   if (c->ev_pool.empty()) {
@@ -934,23 +938,44 @@ extern "C" hfx_status hfx_profile_enable(hfx_ctx* c, int on) {
   return HFX_OK;
 }
 
-extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]) {
-  g_last_error.clear();
-  if (!c || !ms || !launches) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
-  for (int k = 0; k < kProfSlots; ++k) { ms[k] = 0.0; launches[k] = 0; }
+// waits for the recorded events and adds their times into the context's per-slot sums
+static hfx_status prof_drain(hfx_ctx* c) {
   hfx_status st = HFX_OK;
   for (auto& pe : c->ev_pending) {
     float t = 0.f;
     cudaError_t e = cudaEventSynchronize(pe.second.second);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, pe.second.first, pe.second.second);
     if (e != cudaSuccess && st == HFX_OK) st = fail(HFX_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
-    ms[pe.first] += t;
-    launches[pe.first] += 1;
+    c->prof_ms[pe.first] += t;
+    c->prof_n[pe.first] += 1;
     c->ev_pool.push_back(pe.second.first);
     c->ev_pool.push_back(pe.second.second);
   }
   c->ev_pending.clear();
   return st;
+}
+
+static hfx_status prof_take(hfx_ctx* c, int first, int count, double* ms, int64_t* launches) {
+  const hfx_status st = prof_drain(c);
+  for (int k = 0; k < count; ++k) {
+    ms[k] = c->prof_ms[first + k];
+    launches[k] = c->prof_n[first + k];
+    c->prof_ms[first + k] = 0.0;
+    c->prof_n[first + k] = 0;
+  }
+  return st;
+}
+
+extern "C" hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]) {
+  g_last_error.clear();
+  if (!c || !ms || !launches) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
+  return prof_take(c, 0, kProfSlots, ms, launches);
+}
+
+extern "C" hfx_status hfx_ace_profile_read(hfx_ctx* c, double ms[3], int64_t launches[3]) {
+  g_last_error.clear();
+  if (!c || !ms || !launches) return fail(HFX_ERR_INVALID_ARG, "bad arguments");
+  return prof_take(c, kProfAceGram, kProfAllSlots - kProfAceGram, ms, launches);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1226,13 +1251,19 @@ extern "C" hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const do
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
   // M_kl = <psi_k | W_l> = (Omega/N) sum_p psi_k(p) W_l(p)
+  cudaEvent_t t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram(fp32, false, orbitals, N, n_orb, w, N, n_orb, N, gp, part, c->sm_count, st));
+  prof_close(c, kProfAceGram, t0, st);
+  t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, M, n_orb, nullptr, 0, st));
   // L L^T = -(M + M^T)/2, then P_rows = L^-1 W_rows (P = W L^-T)
   HFX_ACE_TRY(ace::cholesky_neg_sym(M, n_orb, n_orb, L, work, c->d_err, c->max_smem, st));
   const long long ldt = ace::lmul_ldt(fp32, n_orb);
   HFX_ACE_TRY(ace::tri_inverse(fp32, L, n_orb, Linvt, ldt, c->max_smem, st));
+  prof_close(c, kProfAceSmall, t0, st);
+  t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::lmul(fp32, Linvt, ldt, n_orb, n_orb, true, w, N, N, false, p, N, c->sm_count, st));
+  prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
 }
 
@@ -1255,11 +1286,17 @@ extern "C" hfx_status hfx_ace_apply(hfx_ctx* c, const double* p, int32_t n_orb, 
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, N, c->sm_count);
   // X[i][k] = -<psi_i | P_k> (held transposed), then out_i (+)= sum_k X[i][k] P_k
+  cudaEvent_t t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram(fp32, false, psi, N, n_psi, p, N, n_orb, N, gp, part, c->sm_count, st));
+  prof_close(c, kProfAceGram, t0, st);
+  t0 = prof_mark(c, st);
   const long long ldt = ace::lmul_ldt(fp32, n_psi);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_psi, n_orb, -c->omega / (double)N, nullptr, 0, Xt, ldt, st));
+  prof_close(c, kProfAceSmall, t0, st);
+  t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::lmul(fp32, Xt, ldt, n_psi, n_orb, false, p, N, N, (flags & HFX_ACCUMULATE) != 0, out, N, c->sm_count,
                         st));
+  prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
 }
 
@@ -1283,8 +1320,12 @@ extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32
   const bool fp32 = c->prec == HFX_PREC_FP32;
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
+  cudaEvent_t t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram(fp32, true, orbitals, N, n_orb, orbitals, N, n_orb, N, gp, part, c->sm_count, st));
+  prof_close(c, kProfAceGram, t0, st);
+  t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, nullptr, 0, st));
   HFX_ACE_TRY(ace::screen_compact(S, n_orb, cut, pairs, n_pairs, rowbuf, st));
+  prof_close(c, kProfAceSmall, t0, st);
   return HFX_OK;
 }

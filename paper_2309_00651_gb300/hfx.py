@@ -30,9 +30,10 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
             "hfx_profile_read",
             "hfx_last_error", "hfx_destroy",
-            "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs")
+            "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
+ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
 
 
 class HfxBox(ctypes.Structure):
@@ -99,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_ace_apply.restype = ctypes.c_int
     L.hfx_screen_pairs.argtypes = [vp, vp, i32, dbl, vp, vp, vp, vp, sz, vp]
     L.hfx_screen_pairs.restype = ctypes.c_int
+    L.hfx_ace_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
+    L.hfx_ace_profile_read.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -195,6 +198,13 @@ def hfx_profile_read(ctx) -> dict:
     n = (ctypes.c_int64 * 6)()
     _check(load_library().hfx_profile_read(ctx, ms, n))
     return {name: {"ms": float(ms[k]), "launches": int(n[k])} for k, name in enumerate(PASS_NAMES)}
+
+
+def hfx_ace_profile_read(ctx) -> dict:
+    ms = (ctypes.c_double * 3)()
+    n = (ctypes.c_int64 * 3)()
+    _check(load_library().hfx_ace_profile_read(ctx, ms, n))
+    return {name: {"ms": float(ms[k]), "launches": int(n[k])} for k, name in enumerate(ACE_KERNEL_NAMES)}
 
 
 def hfx_last_error() -> str:

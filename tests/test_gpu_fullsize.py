@@ -97,3 +97,33 @@ def test_uneven_batch_through_apply_batched():
         V_row = O.exchange_rows(phi, pairs, [k], w.lattice)[0]
         assert rel(V[k].cpu().numpy(), V_row) <= 1e-6
         ex.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_ace_full_workload(precision):
+    """ACE at full size (water32_n72, W from the exchange call itself): M against the oracle's
+    full grid contraction, L against its Cholesky factor, the first rows of P against forward
+    substitution, the occupied-span identity and 1/2 tr M = E_x on the whole result."""
+    import scipy.linalg
+    from oracle import ace_oracle as A
+    from paper_2309_00651_gb300 import hfx
+    w = I.WORKLOADS["water32_n72"]
+    phi, pairs, _ = I.make_workload(w)
+    phi_d = torch.from_numpy(phi).cuda()
+    ex = hfx.Exchange(w.lattice, w.grid, precision=precision)
+    E, V = ex.apply(phi_d, torch.from_numpy(pairs).cuda())
+    M, Lf, P = ex.ace_build(phi_d, V)
+    Y = ex.ace_apply(P, phi_d)
+    ex.sync_status()
+    tol = TOL[precision]
+    Vh = V.cpu().numpy()
+    M0 = A.grid_inner(phi, Vh, w.lattice)
+    L0 = np.linalg.cholesky(-0.5 * (M0 + M0.T))
+    assert rel(M.cpu().numpy(), M0) <= tol
+    assert rel(Lf.cpu().numpy(), L0) <= 10 * tol
+    k = 4
+    P0 = scipy.linalg.solve_triangular(L0[:k, :k], Vh[:k].reshape(k, -1), lower=True)
+    assert rel(P[:k].cpu().numpy().reshape(k, -1), P0) <= 10 * tol
+    assert float(torch.linalg.norm(Y - V) / torch.linalg.norm(V)) <= 10 * tol
+    assert 0.5 * float(torch.trace(M)) == pytest.approx(E.item(), rel=10 * tol)
+    ex.close()
