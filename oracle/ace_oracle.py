@@ -26,6 +26,10 @@ Screening (Sec. 2.1, the s-MTACE overlap cut): s_ij = (Omega/N) sum_p |phi_i(r_p
 a pair i <= j is kept when s_ij > cut; diagonal pairs are always kept.  Pairs come out in
 row-major (i, then j) order.
 
+SCDM localisation (the method the paper cites for its localised orbitals, Sec. 2.1; the paper
+prints no algorithm, so this follows the published method): column-pivoted QR of Psi^T by greedy
+residual-norm pivoting picks n grid points; Phi = Psi Q with Q from Psi(C, :)^T = Q R.
+
 Linear algebra steps use numpy/scipy library routines (a matrix product, a Cholesky
 factorisation, a triangular solve); nothing is blocked, fused or reordered.
 """
@@ -83,3 +87,74 @@ def screen_pairs(phi: np.ndarray, lattice: np.ndarray, cut: float) -> Tuple[np.n
     n = s.shape[0]
     out = [(i, j) for i in range(n) for j in range(i, n) if i == j or s[i, j] > cut]
     return np.array(out, dtype=np.int32).reshape(-1, 2), s
+
+
+# ---------------------------------------------------------------------------------------------
+# SCDM localisation (the selected-columns-of-the-density-matrix method the paper cites for its
+# localised orbitals, Sec. 2.1): a column-pivoted QR factorisation of Psi^T picks n grid points
+# C; the localised orthonormal orbitals are Phi = Psi Q with Q from the QR factorisation of the
+# selected columns, Psi(C, :)^T = Q R (Q orthogonal, R upper triangular with positive diagonal).
+# ---------------------------------------------------------------------------------------------
+
+def scdm_pivots(phi: np.ndarray) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Column-pivoted QR of A = Psi^T ([n][N], column p = the n orbital values at grid point p) by
+    greedy pivoting on residual column norms (Businger-Golub): at step j take the column of largest
+    residual norm (lowest index on a tie), orthogonalise it against q_0..q_{j-1}, normalise to q_j,
+    and remove its q_j component from every column.
+
+    Returns (pivots [n] int64, Q [n][n] with columns q_j, diag(R) [n] = residual norms at the picks).
+    """
+    A = _rows(phi).copy()          # [n][N]; A[:, p] is column p
+    n = A.shape[0]
+    nu = np.sum(A * A, axis=0)     # squared residual column norms
+    Q = np.zeros((n, n))
+    piv = np.zeros(n, dtype=np.int64)
+    rdiag = np.zeros(n)
+    for j in range(n):
+        p = int(np.argmax(nu))     # first maximum
+        r = A[:, p].copy()
+        rn = float(np.linalg.norm(r))
+        q = r / rn
+        Q[:, j] = q
+        piv[j] = p
+        rdiag[j] = rn
+        A -= np.outer(q, q @ A)    # residual of every column
+        nu = np.sum(A * A, axis=0)
+        nu[piv[: j + 1]] = -1.0    # picked columns are exhausted
+    return piv, Q, rdiag
+
+
+def scdm_q_from_pivots(phi: np.ndarray, piv: np.ndarray) -> np.ndarray:
+    """Q of the QR factorisation Psi(C, :)^T = Q R with diag(R) > 0, for given pivots C."""
+    B = _rows(phi)[:, np.asarray(piv)]   # [n][n]: column j = orbital values at pivot j
+    Q, R = np.linalg.qr(B)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s[None, :]
+
+
+def scdm_localise(phi: np.ndarray, piv: np.ndarray = None) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """SCDM-localised orthonormal orbitals Phi = Psi Q (rows: Phi_j = sum_i Q[i][j] psi_i).
+
+    Returns (pivots, Q, Phi [n, n1, n2, n3]); with `piv` given, Q is formed from those pivots."""
+    if piv is None:
+        piv, _, _ = scdm_pivots(phi)
+    Q = scdm_q_from_pivots(phi, piv)
+    Phi = (Q.T @ _rows(phi)).reshape(np.shape(phi))
+    return np.asarray(piv), Q, Phi
+
+
+def scdm_pivot_slack(phi: np.ndarray, piv: np.ndarray) -> np.ndarray:
+    """For a proposed pivot sequence, the FP64 squared residual norm of each pick relative to the
+    largest one available at that step (1 = a greedy choice; below 1 = how far from it)."""
+    A = _rows(phi).copy()
+    out = np.zeros(len(piv))
+    taken = []
+    for j, p in enumerate(piv):
+        nu = np.sum(A * A, axis=0)
+        nu[taken] = -1.0
+        out[j] = nu[p] / nu.max()
+        q = A[:, p] / np.linalg.norm(A[:, p])
+        A -= np.outer(q, q @ A)
+        taken.append(int(p))
+    return out

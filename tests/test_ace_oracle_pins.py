@@ -146,3 +146,53 @@ def test_screen_bounds_and_order():
     assert np.array_equal(pairs, I.screened_pairs(phi, L ** 3, cut))
     key = pairs[:, 0] * 7 + pairs[:, 1]
     assert np.all(np.diff(key) > 0)
+
+
+# ----------------------------------------------------------------------------- SCDM localisation
+
+def test_scdm_pivots_match_library_qrcp():
+    import scipy.linalg
+    L, n = 6.0, 8
+    phi = small_orbitals(7, n, L, seed=21)
+    piv, Q, rdiag = A.scdm_pivots(phi)
+    At = phi.reshape(7, -1)
+    Ql, Rl, Pl = scipy.linalg.qr(At, pivoting=True, mode="economic")
+    assert np.array_equal(piv, Pl[:7])
+    assert np.allclose(rdiag, np.abs(np.diag(Rl)), rtol=1e-12, atol=0)
+    sgn = np.sign(np.diag(Rl))
+    assert np.allclose(Q, Ql * sgn[None, :], atol=1e-12)
+    # the greedy factor is the QR factor of the selected columns
+    assert np.allclose(A.scdm_q_from_pivots(phi, piv), Q, atol=1e-12)
+    assert np.all(A.scdm_pivot_slack(phi, piv) == 1.0)
+
+
+def test_scdm_recovers_disjoint_localised_orbitals():
+    # orthonormal indicator functions of disjoint boxes, mixed by an orthogonal rotation: SCDM
+    # returns the boxes again (up to sign and order)
+    n, L = 8, 6.0
+    w = L ** 3 / n ** 3
+    boxes = [(slice(0, 2), slice(0, 3), slice(0, 4)), (slice(3, 6), slice(0, 2), slice(0, 8)),
+             (slice(6, 8), slice(4, 8), slice(2, 5)), (slice(0, 4), slice(5, 8), slice(6, 8))]
+    loc = np.zeros((4, n, n, n))
+    for k, b in enumerate(boxes):
+        loc[k][b] = 1.0
+        loc[k] /= np.sqrt(w * np.sum(loc[k] ** 2))
+    U, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((4, 4)))
+    psi = np.einsum("ki,k...->i...", U, loc)
+    piv, Q, Phi = A.scdm_localise(psi)
+    O = w * Phi.reshape(4, -1) @ loc.reshape(4, -1).T   # overlaps with the boxes
+    assert np.allclose(np.sort(np.abs(O), axis=1)[:, -1], 1.0, atol=1e-12)
+    assert np.allclose(np.sort(np.abs(O), axis=1)[:, :-1], 0.0, atol=1e-12)
+
+
+def test_scdm_orthonormal_same_span():
+    L, n = 6.5, 8
+    lat = np.diag([L, L, L])
+    phi = small_orbitals(6, n, L, seed=22)
+    piv, Q, Phi = A.scdm_localise(phi)
+    assert np.allclose(Q.T @ Q, np.eye(6), atol=1e-13)
+    S = A.grid_inner(Phi, Phi, lat)
+    assert np.allclose(S, np.eye(6), atol=1e-12)
+    # same occupied projector: sum_i |phi_i><phi_i| = sum_j |Phi_j><Phi_j|
+    f, F = phi.reshape(6, -1), Phi.reshape(6, -1)
+    assert np.allclose(f.T @ f, F.T @ F, atol=1e-12)
