@@ -173,6 +173,7 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
     t_build = timed(lambda: ex.ace_build(phi, V))
     t_apply = timed(lambda: ex.ace_apply(Pm, phi, out=out))
     t_screen = timed(lambda: ex.screen_pairs(phi, 1e-6))
+    t_scdm = timed(lambda: ex.scdm_localise(phi))
     # per-kernel device time over `reps` applications (CUDA events around each launch)
     hfx.hfx_profile_enable(ex.ctx, True)
     hfx.hfx_ace_profile_read(ex.ctx)
@@ -198,7 +199,7 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
                               else "nominal FP64 rate")}
 
     row = {
-        "ms": {"build": t_build, "apply": t_apply, "screen": t_screen},
+        "ms": {"build": t_build, "apply": t_apply, "screen": t_screen, "scdm": t_scdm},
         "apply_vs_exchange_call": None,
         "roofline": roof(g_ms, gram_bytes, "k_ace_mm (split grid contraction, <psi|P>)"),
         "roofline_lmul": roof(l_ms, lmul_bytes, "k_ace_mm (left multiply, -X P)"),

@@ -51,8 +51,10 @@ typedef enum {
                                     or more copies of a pair than fit; those entries were
                                     skipped                                               */
   HFX_ERR_TIMEOUT = -6,          /* (device-detected) a bounded device-side wait gave up  */
-  HFX_ERR_NOT_POSITIVE_DEFINITE = -7 /* (device-detected) ACE construction: -M had a pivot
+  HFX_ERR_NOT_POSITIVE_DEFINITE = -7, /* (device-detected) ACE construction: -M had a pivot
                                     <= 0 in its Cholesky factorisation (include/hfx_ace.h) */
+  HFX_ERR_RANK_DEFICIENT = -8    /* (device-detected) SCDM: no grid point with a positive
+                                    residual norm was left to pick (include/hfx_ace.h)     */
 } hfx_status;
 
 typedef enum {
@@ -167,8 +169,8 @@ hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
                              void* cuda_stream);
 
 /* hfx_sync_status -- wait for `cuda_stream` and return (then clear) the device-side error
- * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST, HFX_ERR_TIMEOUT or
- * HFX_ERR_NOT_POSITIVE_DEFINITE. */
+ * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST, HFX_ERR_TIMEOUT,
+ * HFX_ERR_NOT_POSITIVE_DEFINITE or HFX_ERR_RANK_DEFICIENT. */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
 
 /* hfx_set_tuning -- schedule parameters of the context (what an autotuner varies; results do

@@ -73,11 +73,34 @@ hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32_t n_orb, d
                             int32_t* pairs, int64_t* n_pairs, void* workspace, size_t workspace_bytes,
                             void* cuda_stream);
 
+/* hfx_scdm_workspace_bytes -- device workspace of hfx_scdm_localise for n_orb orbitals
+ * (residual norms, per-block maxima, Q in the compute type; FP32 contexts also an FP32 copy of
+ * the orbitals).  0 when the sizes are invalid. */
+size_t hfx_scdm_workspace_bytes(const hfx_ctx* c, int32_t n_orb);
+
+/* hfx_scdm_localise -- SCDM localisation (the selected-columns-of-the-density-matrix method the
+ * paper's localised-orbital variant uses, Sec. 2.1): a column-pivoted QR factorisation of Psi^T
+ * (greedy: at step j the grid point whose orbital-value column has the largest residual norm
+ * after removing q_0..q_{j-1}, lowest index on a tie) picks n_orb grid points, q_j is the unit
+ * residual of the picked column, and the localised orthonormal orbitals are Phi = Psi Q
+ * (Phi_j = sum_i Q[i][j] psi_i).
+ *   orbitals : [n_orb][N] FP64, read only, 1 <= n_orb <= min(N, 768).
+ *   pivots   : device int64 [n_orb] out, the picked grid points in order (flat index, z fastest).
+ *   q        : [n_orb][n_orb] FP64 out (columns q_j), or NULL.
+ *   phi_loc  : [n_orb][N] FP64 out; must not overlap the orbitals.
+ * FP32 contexts round the orbitals once to FP32 for the residual updates (residual norms in
+ * FP64), so a pick may differ from the FP64 one where two residual norms agree to ~1e-6;
+ * HFX_ERR_RANK_DEFICIENT (via hfx_sync_status) when the orbitals span fewer than n_orb grid
+ * columns. */
+hfx_status hfx_scdm_localise(hfx_ctx* c, const double* orbitals, int32_t n_orb, int64_t* pivots, double* q,
+                             double* phi_loc, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
 /* hfx_ace_profile_read -- per-kernel device time of the calls above while hfx_profile_enable
  * is on (CUDA events around each launch on the call's stream): summed milliseconds and launch
  * counts since the last read, then reset; index 0 the split grid contractions (M, <psi|P>, s),
- * 1 the left multiplies (P, V_x^ACE psi), 2 the small steps (partial-sum reduction, Cholesky
- * factorisation, triangular inverse, pair compaction).  Not for use inside stream capture. */
+ * 1 the left multiplies (P, V_x^ACE psi, Phi = Psi Q), 2 the other steps (partial-sum
+ * reduction, Cholesky factorisation, triangular inverse, pair compaction, the SCDM picks and
+ * residual updates).  Not for use inside stream capture. */
 hfx_status hfx_ace_profile_read(hfx_ctx* c, double ms[3], int64_t launches[3]);
 
 #ifdef __cplusplus

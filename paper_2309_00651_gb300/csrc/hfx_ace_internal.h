@@ -11,8 +11,10 @@ namespace ace {
 constexpr int kFormGram = 0;  // C[a][b] = sum_p X[a][p] Y[b][p], split over p, FP64 partials
 constexpr int kFormLmul = 1;  // C[m][p] = sum_k T[m][k] Y[k][p] (+ C)
 
-// device error-word bit of a failed factorisation (the exchange path uses bits 0 and 1)
+// device error-word bits of a failed factorisation and of a rank-deficient SCDM pick (the
+// exchange path uses bits 0 and 1)
 constexpr int kErrNotPosDef = 4;
+constexpr int kErrRankDeficient = 8;
 
 struct MmArgs {
   const void* x;       // Gram: X [nx][K] FP64 (row stride ldx); lmul: T^T [K][ldx] in the compute type,
@@ -59,6 +61,13 @@ cudaError_t tri_inverse(bool fp32, const double* l, int n, void* linvt, long lon
 // screen compaction: keep i <= j with s[i][j] > cut or i == j, row-major; rowbuf holds n + 1 ints
 cudaError_t screen_compact(const double* s, int n, double cut, int32_t* pairs, int64_t* n_pairs, int* rowbuf,
                            cudaStream_t st);
+
+// SCDM: pivots (greedy column-pivoted QR of Psi^T) and qt[i][j] = Q[i][j] in the compute type
+// (row stride ldt, the transposed small operand of lmul for Phi = Psi Q); q64 (n x n FP64) may be
+// NULL; `scratch` holds scdm_scratch_bytes
+size_t scdm_scratch_bytes(bool fp32, int n, long long N, int sm_count);
+cudaError_t scdm_pivots_q(bool fp32, const double* psi, long long N, int n, void* scratch, long long* piv, void* qt,
+                          long long ldt, double* q64, int* err, int sm_count, cudaStream_t st);
 
 }  // namespace ace
 }  // namespace hfx

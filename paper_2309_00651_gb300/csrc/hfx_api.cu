@@ -901,6 +901,8 @@ extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
   if (h & kErrTimeout) return fail(HFX_ERR_TIMEOUT, "a device-side wait timed out");
   if (h & ace::kErrNotPosDef)
     return fail(HFX_ERR_NOT_POSITIVE_DEFINITE, "ACE construction: -(M + M^T)/2 is not positive definite; L and P are undefined");
+  if (h & ace::kErrRankDeficient)
+    return fail(HFX_ERR_RANK_DEFICIENT, "SCDM: no grid point with a positive residual norm was left to pick");
   if (h & kErrBadPair) return fail(HFX_ERR_BAD_PAIR_LIST, "pair list had entries outside 0 <= i <= j < n_orb or too many copies of a pair; they were skipped");
   return HFX_OK;
 }
@@ -1163,7 +1165,9 @@ extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_byt
 // ------------------------------------------------------------------------------------
 // ACE operator and overlap screen (include/hfx_ace.h)
 // ------------------------------------------------------------------------------------
-static_assert((ace::kErrNotPosDef & (kErrBadPair | kErrTimeout)) == 0, "device error bits overlap");
+static_assert(((ace::kErrNotPosDef | ace::kErrRankDeficient) & (kErrBadPair | kErrTimeout)) == 0 &&
+                  (ace::kErrNotPosDef & ace::kErrRankDeficient) == 0,
+              "device error bits overlap");
 
 namespace {
 
@@ -1327,5 +1331,50 @@ extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, nullptr, 0, st));
   HFX_ACE_TRY(ace::screen_compact(S, n_orb, cut, pairs, n_pairs, rowbuf, st));
   prof_close(c, kProfAceSmall, t0, st);
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// SCDM localisation (include/hfx_ace.h)
+// ------------------------------------------------------------------------------------
+namespace {
+constexpr int kScdmMaxOrb = 768;  // the pick kernel keeps 34 n values of the compute type on chip
+size_t scdm_ws(const hfx_ctx* c, int n) {
+  const bool fp32 = c->prec == HFX_PREC_FP32;
+  return ace_round(ace::scdm_scratch_bytes(fp32, n, c->N, c->sm_count)) +
+         ace_round((size_t)n * ace::lmul_ldt(fp32, n) * sizeof(double));
+}
+}  // namespace
+
+extern "C" size_t hfx_scdm_workspace_bytes(const hfx_ctx* c, int32_t n_orb) {
+  if (!c || n_orb < 1 || n_orb > kScdmMaxOrb || n_orb > c->N) return 0;
+  return scdm_ws(c, n_orb);
+}
+
+extern "C" hfx_status hfx_scdm_localise(hfx_ctx* c, const double* orbitals, int32_t n_orb, int64_t* pivots, double* q,
+                                        double* phi_loc, void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (!orbitals || !pivots || !phi_loc) return fail(HFX_ERR_INVALID_ARG, "orbitals, pivots and phi_loc must be non-NULL");
+  if (n_orb < 1 || n_orb > kScdmMaxOrb || n_orb > c->N)
+    return fail(HFX_ERR_INVALID_ARG, "n_orb must be in [1, min(N, %d)]", kScdmMaxOrb);
+  if (misaligned8(orbitals) || misaligned8(pivots) || misaligned8(q) || misaligned8(phi_loc))
+    return fail(HFX_ERR_INVALID_ARG, "pointers must be 8-byte aligned");
+  const size_t need = scdm_ws(c, n_orb);
+  if (hfx_status s = ace_check_ws(workspace, workspace_bytes, need)) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool fp32 = c->prec == HFX_PREC_FP32;
+  const long long N = c->N;
+  char* base = (char*)workspace;
+  void* scratch = base;
+  void* qt = base + ace_round(ace::scdm_scratch_bytes(fp32, n_orb, N, c->sm_count));
+  const long long ldt = ace::lmul_ldt(fp32, n_orb);
+  cudaEvent_t t0 = prof_mark(c, st);
+  HFX_ACE_TRY(ace::scdm_pivots_q(fp32, orbitals, N, n_orb, scratch, (long long*)pivots, qt, ldt, q, c->d_err,
+                                 c->sm_count, st));
+  prof_close(c, kProfAceSmall, t0, st);
+  t0 = prof_mark(c, st);
+  HFX_ACE_TRY(ace::lmul(fp32, qt, ldt, n_orb, n_orb, false, orbitals, N, N, false, phi_loc, N, c->sm_count, st));
+  prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
 }

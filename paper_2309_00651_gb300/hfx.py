@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libhfx.so")
 HFX_OK = 0
 STATUS_NAMES = {0: "HFX_OK", -1: "HFX_ERR_INVALID_ARG", -2: "HFX_ERR_UNSUPPORTED_GRID", -3: "HFX_ERR_OOM",
                 -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT",
-                -7: "HFX_ERR_NOT_POSITIVE_DEFINITE"}
+                -7: "HFX_ERR_NOT_POSITIVE_DEFINITE", -8: "HFX_ERR_RANK_DEFICIENT"}
 PRECISION = {"fp64": 0, "fp32": 1}
 KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
 HFX_ENERGY_ONLY = 0x1
@@ -30,7 +30,8 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
             "hfx_profile_read",
             "hfx_last_error", "hfx_destroy",
-            "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read")
+            "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
+            "hfx_scdm_workspace_bytes", "hfx_scdm_localise")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
@@ -102,6 +103,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_screen_pairs.restype = ctypes.c_int
     L.hfx_ace_profile_read.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64)]
     L.hfx_ace_profile_read.restype = ctypes.c_int
+    L.hfx_scdm_workspace_bytes.argtypes = [vp, i32]
+    L.hfx_scdm_workspace_bytes.restype = sz
+    L.hfx_scdm_localise.argtypes = [vp, vp, i32, vp, vp, vp, vp, sz, vp]
+    L.hfx_scdm_localise.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -198,6 +203,16 @@ def hfx_profile_read(ctx) -> dict:
     n = (ctypes.c_int64 * 6)()
     _check(load_library().hfx_profile_read(ctx, ms, n))
     return {name: {"ms": float(ms[k]), "launches": int(n[k])} for k, name in enumerate(PASS_NAMES)}
+
+
+def hfx_scdm_workspace_bytes(ctx, n_orb: int) -> int:
+    return int(load_library().hfx_scdm_workspace_bytes(ctx, int(n_orb)))
+
+
+def hfx_scdm_localise(ctx, orbitals: torch.Tensor, pivots: torch.Tensor, q: Optional[torch.Tensor],
+                      phi_loc: torch.Tensor, workspace: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_scdm_localise(ctx, _ptr(orbitals), int(orbitals.shape[0]), _ptr(pivots), _ptr(q),
+                                            _ptr(phi_loc), _ptr(workspace), _nbytes(workspace), _stream_handle(stream)))
 
 
 def hfx_ace_profile_read(ctx) -> dict:
@@ -347,6 +362,23 @@ class Exchange:
         hfx_ace_apply(self.ctx, p, psi, out, self._ace_workspace(p.shape[0], psi.shape[0]),
                       HFX_ACCUMULATE if accumulate else 0, stream)
         return out
+
+    def scdm_localise(self, phi: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
+        """(pivots int64 [n], Q [n, n], Phi = Psi Q [n, n1, n2, n3]) of the SCDM localisation."""
+        self._grid_rows("phi", phi)
+        n = phi.shape[0]
+        need = hfx_scdm_workspace_bytes(self.ctx, n)
+        if need == 0:
+            raise ValueError(f"SCDM needs 1 <= n_orb <= min(N, 768); got {n}")
+        ws = getattr(self, "_scdm_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self._scdm_ws = ws
+        piv = torch.empty(n, dtype=torch.int64, device=phi.device)
+        q = torch.empty((n, n), dtype=torch.float64, device=phi.device)
+        out = torch.empty_like(phi)
+        hfx_scdm_localise(self.ctx, phi, piv, q, out, ws, stream)
+        return piv, q, out
 
     def screen_pairs(self, phi: torch.Tensor, cut: float, stream: Optional[torch.cuda.Stream] = None):
         """(pairs int32 [P, 2] device tensor, s [n, n]) of the overlap screen s_ij > cut (diagonal kept).

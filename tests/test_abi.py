@@ -76,6 +76,8 @@ def test_host_side_argument_errors(lib):
     assert lib.hfx_ace_build(None, None, None, 16, None, None, None, None, 0, None) == -1
     assert lib.hfx_ace_apply(None, None, 16, None, 4, 0, None, None, 0, None) == -1
     assert lib.hfx_screen_pairs(None, None, 16, 1e-6, None, None, None, None, 0, None) == -1
+    assert lib.hfx_scdm_workspace_bytes(None, 16) == 0
+    assert lib.hfx_scdm_localise(None, None, 16, None, None, None, None, 0, None) == -1
     lib.hfx_destroy(None)
 
 

@@ -218,3 +218,68 @@ def test_screen_parity(precision, n_orb, n):
         assert np.all(np.diff(k) > 0) and np.all(got[:, 0] <= got[:, 1])
         assert all((i, i) in {(int(a), int(b)) for a, b in got} for i in range(n_orb))
     ex.close()
+
+
+# ----------------------------------------------------------------------------- SCDM localisation
+# Pivots: FP64 picks equal the oracle's greedy picks; FP32 picks are checked for validity (each is
+# within a relative 1e-4 of the largest FP64 residual norm available at its step, given the
+# earlier picks).  Q and Phi are compared with the oracle's, formed from the GPU's own pivots.
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n_orb,n,seed", [(6, 10, 31), (40, 12, 32), (130, 18, 33)])
+def test_scdm_parity(precision, n_orb, n, seed):
+    L = 8.0
+    lat = np.diag([L, L, L])
+    phi = small_orbitals(n_orb, n, L, seed)
+    ex = make_exchange(L, n, precision)
+    piv, Q, Phi = ex.scdm_localise(dev(phi))
+    ex.sync_status()
+    piv = piv.cpu().numpy()
+    assert len(set(piv.tolist())) == n_orb and piv.min() >= 0 and piv.max() < n ** 3
+    slack = A.scdm_pivot_slack(phi, piv)
+    if precision == "fp64":
+        ref_piv, _, _ = A.scdm_pivots(phi)
+        assert np.array_equal(piv, ref_piv)
+    else:
+        assert slack.min() >= 1 - 1e-4
+    _, Q0, Phi0 = A.scdm_localise(phi, piv)
+    tol = TOL[precision]
+    assert rel(Q.cpu().numpy(), Q0) < 10 * tol
+    assert rel(Phi.cpu().numpy(), Phi0) < 10 * tol
+    S = A.grid_inner(Phi.cpu().numpy(), Phi.cpu().numpy(), lat)
+    assert np.max(np.abs(S - np.eye(n_orb))) < 10 * tol
+    ex.close()
+
+
+def test_scdm_recovers_disjoint_boxes():
+    n, L = 8, 6.0
+    w = L ** 3 / n ** 3
+    boxes = [(slice(0, 2), slice(0, 3), slice(0, 4)), (slice(3, 6), slice(0, 2), slice(0, 8)),
+             (slice(6, 8), slice(4, 8), slice(2, 5)), (slice(0, 4), slice(5, 8), slice(6, 8))]
+    loc = np.zeros((4, n, n, n))
+    for k, b in enumerate(boxes):
+        loc[k][b] = 1.0
+        loc[k] /= np.sqrt(w * np.sum(loc[k] ** 2))
+    U, _ = np.linalg.qr(np.random.default_rng(3).standard_normal((4, 4)))
+    psi = np.einsum("ki,k...->i...", U, loc)
+    for precision in ("fp64", "fp32"):
+        ex = make_exchange(L, n, precision)
+        _, _, Phi = ex.scdm_localise(dev(psi))
+        ex.sync_status()
+        O = w * Phi.cpu().numpy().reshape(4, -1) @ loc.reshape(4, -1).T
+        assert np.allclose(np.sort(np.abs(O), axis=1)[:, -1], 1.0, atol=1e-6)
+        assert np.allclose(np.sort(np.abs(O), axis=1)[:, :-1], 0.0, atol=1e-6)
+        ex.close()
+
+
+def test_scdm_rank_deficient_is_reported():
+    from paper_2309_00651_gb300 import hfx
+    n, L = 8, 6.0
+    phi = small_orbitals(5, n, L, 34)
+    phi = np.concatenate([phi, phi[:1]])  # a repeated orbital: rank 5 of 6
+    ex = make_exchange(L, n, "fp64")
+    ex.scdm_localise(dev(phi))
+    with pytest.raises(hfx.HFXError) as e:
+        ex.sync_status()
+    assert e.value.status == -8
+    ex.close()

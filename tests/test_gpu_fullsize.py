@@ -127,3 +127,29 @@ def test_ace_full_workload(precision):
     assert float(torch.linalg.norm(Y - V) / torch.linalg.norm(V)) <= 10 * tol
     assert 0.5 * float(torch.trace(M)) == pytest.approx(E.item(), rel=10 * tol)
     ex.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_scdm_full_workload(precision):
+    """SCDM at full size (water32_n72, 128 orbitals on 72^3): every pick is a greedy choice within
+    the stated slack of the FP64 residual norms, Q matches the oracle's QR of the picked columns,
+    sampled rows of Phi match, Phi is orthonormal."""
+    from oracle import ace_oracle as A
+    from paper_2309_00651_gb300 import hfx
+    w = I.WORKLOADS["water32_n72"]
+    phi, _, _ = I.make_workload(w)
+    ex = hfx.Exchange(w.lattice, w.grid, precision=precision)
+    piv, Q, Phi = ex.scdm_localise(torch.from_numpy(phi).cuda())
+    ex.sync_status()
+    piv = piv.cpu().numpy()
+    slack = A.scdm_pivot_slack(phi, piv)
+    assert slack.min() >= (1 - 1e-9 if precision == "fp64" else 1 - 1e-4)
+    Q0 = A.scdm_q_from_pivots(phi, piv)
+    tol = TOL[precision]
+    assert rel(Q.cpu().numpy(), Q0) <= 10 * tol
+    rows = [0, 63, 127]
+    Phi0 = Q0[:, rows].T @ phi.reshape(128, -1)
+    assert rel(Phi[rows].cpu().numpy().reshape(3, -1), Phi0) <= 10 * tol
+    G = (w.volume / w.n ** 3) * (Phi.reshape(128, -1) @ Phi.reshape(128, -1).T)
+    assert float(torch.max(torch.abs(G - torch.eye(128, dtype=G.dtype, device=G.device)))) <= 10 * tol
+    ex.close()
