@@ -198,8 +198,16 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
                 "peak_kind": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if precision == "fp32"
                               else "nominal FP64 rate")}
 
+    # SCDM: n - 1 residual updates, each a pass over the orbital copy in the compute type plus the
+    # FP64 residual norms (read + write); the picks between them are latency-bound single blocks
+    esize = 4 if precision == "fp32" else 8
+    scdm_bytes = (n_orb - 1) * (n_orb * N * esize + 16 * N)
+    scdm_gbs = scdm_bytes / (t_scdm / 1e3) / 1e9
     row = {
         "ms": {"build": t_build, "apply": t_apply, "screen": t_screen, "scdm": t_scdm},
+        "scdm_roofline": {"bound": "hbm", "achieved": scdm_gbs, "peak": hbm, "unit": "GB/s", "frac": scdm_gbs / hbm,
+                          "alg_bytes_per_call": scdm_bytes,
+                          "measured": "whole call (picks included) with CUDA events"},
         "apply_vs_exchange_call": None,
         "roofline": roof(g_ms, gram_bytes, "k_ace_mm (split grid contraction, <psi|P>)"),
         "roofline_lmul": roof(l_ms, lmul_bytes, "k_ace_mm (left multiply, -X P)"),
