@@ -101,12 +101,13 @@ def xi_respa_inner(X, V, v1, v2, M, F_fast, kT, Q1, Q2, L, gamma, dt, R, n_res=1
     """One inner factor of eq. trotter-sinr, updates applied in the order
     N(dt/2) V(dt/2) [X(dt/2) OU(dt) X(dt/2) = C] V(dt/2) N(dt/2).  F_fast is a callable of X; the
     slow kick n_MTS F_slow enters the first velocity update of the outer step's first inner step
-    (F_first) and the second velocity update of its last one (F_last)."""
+    (F_first, an array) and the second velocity update of its last one (F_last, a callable of the
+    position after C)."""
     V, v1, v2 = update_n_half_step(V, v1, v2, M, kT, Q1, Q2, L, dt, n_res, n_sy)
     F = F_fast(X) if F_first is None else F_fast(X) + F_first
     V, v1 = update_v(V, v1, F, M, kT, L, dt)
     X, v2 = update_x(X, V, v2, R, kT, Q2, gamma, dt)
-    F = F_fast(X) if F_last is None else F_fast(X) + F_last
+    F = F_fast(X) if F_last is None else F_fast(X) + F_last(X)
     V, v1 = update_v(V, v1, F, M, kT, L, dt)
     V, v1, v2 = update_n_half_step(V, v1, v2, M, kT, Q1, Q2, L, dt, n_res, n_sy)
     return X, V, v1, v2

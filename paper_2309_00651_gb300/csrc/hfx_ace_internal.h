@@ -1,5 +1,6 @@
-// Internal interface between the host library (hfx_api.cu) and the ACE / screen kernels
-// (hfx_ace.cu).
+// Internal interface between the host library (hfx_api.cu) and the kernels of the rows that
+// surround the exchange evaluation: ACE and the overlap screen (hfx_ace.cu), SCDM (hfx_scdm.cu),
+// the SIN(R) integrator updates (hfx_sinr.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -70,4 +71,28 @@ cudaError_t scdm_pivots_q(bool fp32, const double* psi, long long N, int n, void
                           long long ldt, double* q64, int* err, int sm_count, cudaStream_t st);
 
 }  // namespace ace
+}  // namespace hfx
+
+namespace hfx {
+namespace sinr {
+
+constexpr int kMaxChain = 16;  // longest thermostat chain (registers per degree of freedom)
+
+struct SinrArgs {
+  double kT, Q1, Q2, gamma;
+  int L;
+};
+struct SyWeights {
+  double w[5];
+};
+
+// SIN(R) updates A, B, C (hfx_sinr.cu); asynchronous on `st`, returning the launch error
+cudaError_t update_n(const SinrArgs& a, long long n_dof, double dt, int n_res, const SyWeights& w, int n_sy,
+                     const double* mass, double* V, double* v1, double* v2, cudaStream_t st);
+cudaError_t update_v(const SinrArgs& a, long long n_dof, double dt, const double* mass, const double* force,
+                     const double* force_extra, double* V, double* v1, cudaStream_t st);
+cudaError_t update_x(const SinrArgs& a, long long n_dof, double dt, const double* V, double* X, double* v2,
+                     const double* R, cudaStream_t st);
+
+}  // namespace sinr
 }  // namespace hfx

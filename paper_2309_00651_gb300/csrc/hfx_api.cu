@@ -17,6 +17,7 @@
 
 #include "../../include/hfx.h"
 #include "../../include/hfx_ace.h"
+#include "../../include/hfx_sinr.h"
 #include "hfx_ace_internal.h"
 #include "hfx_internal.h"
 
@@ -1376,5 +1377,74 @@ extern "C" hfx_status hfx_scdm_localise(hfx_ctx* c, const double* orbitals, int3
   t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::lmul(fp32, qt, ldt, n_orb, n_orb, false, orbitals, N, N, false, phi_loc, N, c->sm_count, st));
   prof_close(c, kProfAceLmul, t0, st);
+  return HFX_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// SIN(R) integrator updates (include/hfx_sinr.h)
+// ------------------------------------------------------------------------------------
+namespace {
+hfx_status sinr_check(const hfx_sinr_params* p, int64_t n_dof, bool need_gamma, sinr::SinrArgs* a) {
+  if (!p) return fail(HFX_ERR_INVALID_ARG, "params is NULL");
+  if (n_dof < 0) return fail(HFX_ERR_INVALID_ARG, "n_dof must be >= 0");
+  if (p->L < 1 || p->L > sinr::kMaxChain) return fail(HFX_ERR_INVALID_ARG, "L must be in [1, %d]", sinr::kMaxChain);
+  if (!(p->kT > 0.0) || !(p->Q1 > 0.0) || !(p->Q2 > 0.0)) return fail(HFX_ERR_INVALID_ARG, "kT, Q1 and Q2 must be > 0");
+  if (need_gamma && !(p->gamma > 0.0)) return fail(HFX_ERR_INVALID_ARG, "gamma must be > 0");
+  a->kT = p->kT;
+  a->Q1 = p->Q1;
+  a->Q2 = p->Q2;
+  a->gamma = p->gamma;
+  a->L = p->L;
+  return HFX_OK;
+}
+bool bad_ptr(const void* q, int64_t n_dof) { return n_dof > 0 && (!q || ((uintptr_t)q & 7u)); }
+}  // namespace
+
+extern "C" hfx_status hfx_sinr_update_n(const hfx_sinr_params* p, int64_t n_dof, double dt, int32_t n_res,
+                                        int32_t n_sy, const double* mass, double* V, double* v1, double* v2,
+                                        void* cuda_stream) {
+  g_last_error.clear();
+  sinr::SinrArgs a;
+  if (hfx_status s = sinr_check(p, n_dof, false, &a)) return s;
+  if (n_res < 1) return fail(HFX_ERR_INVALID_ARG, "n_res must be >= 1");
+  sinr::SyWeights w{};
+  if (n_sy == 1) {
+    w.w[0] = 1.0;
+  } else if (n_sy == 3) {
+    const double w1 = 1.0 / (2.0 - std::pow(2.0, 1.0 / 3.0));
+    w.w[0] = w1; w.w[1] = 1.0 - 2.0 * w1; w.w[2] = w1;
+  } else if (n_sy == 5) {
+    const double w1 = 1.0 / (4.0 - std::pow(4.0, 1.0 / 3.0));
+    w.w[0] = w1; w.w[1] = w1; w.w[2] = 1.0 - 4.0 * w1; w.w[3] = w1; w.w[4] = w1;
+  } else {
+    return fail(HFX_ERR_INVALID_ARG, "n_sy must be 1, 3 or 5");
+  }
+  if (bad_ptr(mass, n_dof) || bad_ptr(V, n_dof) || bad_ptr(v1, n_dof) || bad_ptr(v2, n_dof))
+    return fail(HFX_ERR_INVALID_ARG, "mass, V, v1 and v2 must be non-NULL 8-byte aligned device arrays");
+  HFX_ACE_TRY(sinr::update_n(a, n_dof, dt, n_res, w, n_sy, mass, V, v1, v2, (cudaStream_t)cuda_stream));
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_sinr_update_v(const hfx_sinr_params* p, int64_t n_dof, double dt, const double* mass,
+                                        const double* force, const double* force_extra, double* V, double* v1,
+                                        void* cuda_stream) {
+  g_last_error.clear();
+  sinr::SinrArgs a;
+  if (hfx_status s = sinr_check(p, n_dof, false, &a)) return s;
+  if (bad_ptr(mass, n_dof) || bad_ptr(force, n_dof) || bad_ptr(V, n_dof) || bad_ptr(v1, n_dof) ||
+      (force_extra && bad_ptr(force_extra, n_dof)))
+    return fail(HFX_ERR_INVALID_ARG, "mass, force, V and v1 must be non-NULL 8-byte aligned device arrays");
+  HFX_ACE_TRY(sinr::update_v(a, n_dof, dt, mass, force, force_extra, V, v1, (cudaStream_t)cuda_stream));
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_sinr_update_x(const hfx_sinr_params* p, int64_t n_dof, double dt, const double* V, double* X,
+                                        double* v2, const double* R, void* cuda_stream) {
+  g_last_error.clear();
+  sinr::SinrArgs a;
+  if (hfx_status s = sinr_check(p, n_dof, true, &a)) return s;
+  if (bad_ptr(V, n_dof) || bad_ptr(X, n_dof) || bad_ptr(v2, n_dof) || bad_ptr(R, n_dof))
+    return fail(HFX_ERR_INVALID_ARG, "V, X, v2 and R must be non-NULL 8-byte aligned device arrays");
+  HFX_ACE_TRY(sinr::update_x(a, n_dof, dt, V, X, v2, R, (cudaStream_t)cuda_stream));
   return HFX_OK;
 }

@@ -31,7 +31,8 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_profile_read",
             "hfx_last_error", "hfx_destroy",
             "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
-            "hfx_scdm_workspace_bytes", "hfx_scdm_localise")
+            "hfx_scdm_workspace_bytes", "hfx_scdm_localise",
+            "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
@@ -45,6 +46,11 @@ class HfxApplyArgs(ctypes.Structure):
     _fields_ = [("orbitals", ctypes.c_void_p), ("n_orb", ctypes.c_int32), ("pairs", ctypes.c_void_p),
                 ("n_pairs", ctypes.c_int64), ("flags", ctypes.c_uint32), ("ex_dev", ctypes.c_void_p),
                 ("vxphi", ctypes.c_void_p)]
+
+
+class HfxSinrParams(ctypes.Structure):
+    _fields_ = [("kT", ctypes.c_double), ("Q1", ctypes.c_double), ("Q2", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("L", ctypes.c_int32)]
 
 
 class HFXError(RuntimeError):
@@ -107,6 +113,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_scdm_workspace_bytes.restype = sz
     L.hfx_scdm_localise.argtypes = [vp, vp, i32, vp, vp, vp, vp, sz, vp]
     L.hfx_scdm_localise.restype = ctypes.c_int
+    sp = ctypes.POINTER(HfxSinrParams)
+    L.hfx_sinr_update_n.argtypes = [sp, i64, dbl, i32, i32, vp, vp, vp, vp, vp]
+    L.hfx_sinr_update_n.restype = ctypes.c_int
+    L.hfx_sinr_update_v.argtypes = [sp, i64, dbl, vp, vp, vp, vp, vp, vp]
+    L.hfx_sinr_update_v.restype = ctypes.c_int
+    L.hfx_sinr_update_x.argtypes = [sp, i64, dbl, vp, vp, vp, vp, vp]
+    L.hfx_sinr_update_x.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -213,6 +226,31 @@ def hfx_scdm_localise(ctx, orbitals: torch.Tensor, pivots: torch.Tensor, q: Opti
                       phi_loc: torch.Tensor, workspace: torch.Tensor, stream: Optional[torch.cuda.Stream] = None) -> None:
     _check(load_library().hfx_scdm_localise(ctx, _ptr(orbitals), int(orbitals.shape[0]), _ptr(pivots), _ptr(q),
                                             _ptr(phi_loc), _ptr(workspace), _nbytes(workspace), _stream_handle(stream)))
+
+
+def _sinr_params(p) -> HfxSinrParams:
+    return p if isinstance(p, HfxSinrParams) else HfxSinrParams(float(p["kT"]), float(p["Q1"]), float(p["Q2"]),
+                                                                float(p.get("gamma", 0.0)), int(p["L"]))
+
+
+def hfx_sinr_update_n(params, dt: float, mass: torch.Tensor, V: torch.Tensor, v1: torch.Tensor, v2: torch.Tensor,
+                      n_res: int = 1, n_sy: int = 1, stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_sinr_update_n(ctypes.byref(_sinr_params(params)), int(V.numel()), float(dt), int(n_res),
+                                            int(n_sy), _ptr(mass), _ptr(V), _ptr(v1), _ptr(v2), _stream_handle(stream)))
+
+
+def hfx_sinr_update_v(params, dt: float, mass: torch.Tensor, force: torch.Tensor, V: torch.Tensor,
+                      v1: torch.Tensor, force_extra: Optional[torch.Tensor] = None,
+                      stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_sinr_update_v(ctypes.byref(_sinr_params(params)), int(V.numel()), float(dt), _ptr(mass),
+                                            _ptr(force), _ptr(force_extra), _ptr(V), _ptr(v1),
+                                            _stream_handle(stream)))
+
+
+def hfx_sinr_update_x(params, dt: float, V: torch.Tensor, X: torch.Tensor, v2: torch.Tensor, R: torch.Tensor,
+                      stream: Optional[torch.cuda.Stream] = None) -> None:
+    _check(load_library().hfx_sinr_update_x(ctypes.byref(_sinr_params(params)), int(V.numel()), float(dt), _ptr(V),
+                                            _ptr(X), _ptr(v2), _ptr(R), _stream_handle(stream)))
 
 
 def hfx_ace_profile_read(ctx) -> dict:

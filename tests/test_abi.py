@@ -78,6 +78,15 @@ def test_host_side_argument_errors(lib):
     assert lib.hfx_screen_pairs(None, None, 16, 1e-6, None, None, None, None, 0, None) == -1
     assert lib.hfx_scdm_workspace_bytes(None, 16) == 0
     assert lib.hfx_scdm_localise(None, None, 16, None, None, None, None, 0, None) == -1
+    sp = hfx.HfxSinrParams(0.001, 1.0, 1.0, 0.01, 4)
+    assert lib.hfx_sinr_update_n(None, 10, 1.0, 1, 1, None, None, None, None, None) == -1
+    assert lib.hfx_sinr_update_n(ctypes.byref(sp), 10, 1.0, 1, 2, None, None, None, None, None) == -1  # n_sy
+    assert lib.hfx_sinr_update_n(ctypes.byref(sp), 10, 1.0, 1, 1, None, None, None, None, None) == -1  # NULL arrays
+    bad = hfx.HfxSinrParams(0.001, 1.0, 1.0, 0.01, 17)
+    assert lib.hfx_sinr_update_v(ctypes.byref(bad), 10, 1.0, None, None, None, None, None, None) == -1  # L
+    nog = hfx.HfxSinrParams(0.001, 1.0, 1.0, 0.0, 4)
+    assert lib.hfx_sinr_update_x(ctypes.byref(nog), 10, 1.0, None, None, None, None, None) == -1  # gamma
+    assert lib.hfx_sinr_update_x(ctypes.byref(sp), 0, 1.0, None, None, None, None, None) == 0  # nothing to do
     lib.hfx_destroy(None)
 
 

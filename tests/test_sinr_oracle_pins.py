@@ -141,5 +141,5 @@ def test_xi_respa_keeps_the_constraint():
             X, V, v1, v2 = S.xi_respa_inner(X, V, v1, v2, M, lambda x: -kf * x, KT, Q1, Q2, L, GAMMA, dt,
                                             rng.standard_normal((n, L)), n_res=2, n_sy=3,
                                             F_first=n_mts * F_slow if k == 0 else None,
-                                            F_last=n_mts * (-ks * X) if k == n_mts - 1 else None)
+                                            F_last=(lambda x: n_mts * (-ks * x)) if k == n_mts - 1 else None)
             assert np.allclose(S.constraint(M, V, v1, Q1, L), L * KT, rtol=1e-12, atol=0)
