@@ -219,6 +219,52 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
     return row, (M, Pm)
 
 
+def sinr_rows(hfx, n_dof=3 * 1048576, L=4, reps=20):
+    """SIN(R) integrator updates (appendix A, B, C) on a synthetic 1M-atom state: time per update
+    and the bytes each moves per degree of freedom against measured HBM (A and B carry a few dozen
+    FP64 transcendental operations per degree of freedom, which the narrow FP64 pipe of this part
+    bounds)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    kT = 0.0019
+    p = {"kT": kT, "Q1": kT * 1600.0, "Q2": kT * 1600.0, "gamma": 0.01, "L": L}
+    M = torch.rand(n_dof, device="cuda", dtype=torch.float64, generator=g) * 29000.0 + 1000.0
+    V = torch.randn(n_dof, device="cuda", dtype=torch.float64, generator=g) * 1e-3
+    v1 = torch.randn(n_dof, L, device="cuda", dtype=torch.float64, generator=g) * (kT / p["Q1"]) ** 0.5
+    lam = M * V * V + (L / (L + 1.0)) * p["Q1"] * torch.sum(v1 * v1, dim=1)
+    f = torch.sqrt(L * kT / lam)
+    V *= f
+    v1 *= f[:, None]
+    v2 = torch.randn(n_dof, L, device="cuda", dtype=torch.float64, generator=g) * (kT / p["Q2"]) ** 0.5
+    X = torch.randn(n_dof, device="cuda", dtype=torch.float64, generator=g)
+    F = torch.randn(n_dof, device="cuda", dtype=torch.float64, generator=g) * 0.01
+    R = torch.randn(n_dof, L, device="cuda", dtype=torch.float64, generator=g)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    t_a = timed(lambda: hfx.hfx_sinr_update_n(p, 20.0, M, V, v1, v2, 1, 3))
+    t_b = timed(lambda: hfx.hfx_sinr_update_v(p, 20.0, M, F, V, v1))
+    t_c = timed(lambda: hfx.hfx_sinr_update_x(p, 20.0, V, X, v2, R))
+    hbm = measured_peak_hbm()[0]
+    per_dof = {"A": 8 * (2 + 2 * L) + 8 * (1 + 2 * L), "B": 8 * (3 + L) + 8 * (1 + L),
+               "C": 8 * (2 + 2 * L) + 8 * (1 + L)}
+    ms = {"A": t_a, "B": t_b, "C": t_c}
+    lam2 = M * V * V + (L / (L + 1.0)) * p["Q1"] * torch.sum(v1 * v1, dim=1)
+    return {"n_dof": n_dof, "L": L, "n_sy": 3, "ms": ms,
+            "hbm_frac": {k: per_dof[k] * n_dof / (ms[k] / 1e3) / 1e9 / hbm for k in ms},
+            "bytes_per_dof": per_dof,
+            "constraint_max_rel_dev": float(torch.max(torch.abs(lam2 / (L * kT) - 1.0)))}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -437,6 +483,7 @@ def main():
     if rank == 0 and not args.no_ace:
         line["ace"], ace_out = ace_rows(ex, phi, V, E_val, w, args.precision, hfx)
         line["ace"]["apply_vs_exchange_call"] = ms_step / line["ace"]["ms"]["apply"]
+        line["sinr"] = sinr_rows(hfx)
 
     if rank == 0 and args.precision == "fp32" and not args.no_fp64_compare:
         ex64 = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision="fp64")
