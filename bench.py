@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ace", action="store_true", help="skip the ACE / screen rows")
+    ap.add_argument("--rows-only", action="store_true",
+                    help="one exchange call, then the ACE / screen / SCDM / SIN(R) rows with 2 repetitions each; "
+                         "prints their JSON (a short run to profile those kernels)")
     return ap.parse_args()
 
 
@@ -329,6 +332,15 @@ def main():
     P = len(pairs_np)
     phi = torch.from_numpy(phi_np).to(dev)
     pairs = torch.from_numpy(pairs_np).to(dev)
+    if args.rows_only:
+        ex = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision=args.precision)
+        E, V = ex.apply(phi, pairs)
+        ex.sync_status()
+        rows, _ = ace_rows(ex, phi, V, float(E.item()), w, args.precision, hfx, reps=2)
+        if rank == 0:
+            print(json.dumps({"workload": args.workload, "ace": rows, "sinr": sinr_rows(hfx, reps=2)}), flush=True)
+        ex.close()
+        return
 
     ex = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision=args.precision)
     # schedule autotuner (block size, transform batch, two-stream pipelining), on these inputs

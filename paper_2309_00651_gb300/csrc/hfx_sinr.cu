@@ -46,15 +46,19 @@ __global__ void __launch_bounds__(kThreads) k_update_n(SinrArgs a, long long n_d
   for (int r = 0; r < n_res; ++r) {
     for (int k = 0; k < n_sy; ++k) {
       const double delta = w.w[k] * dt / n_res;
+      // e_j = exp(-v2_j Delta/2) serves both the rescaling of v1 and, squared, the denominator of H
+      // (one exponential per chain element and sub-step: the FP64 pipe of this part is narrow)
+      double e[kMaxChain];
       double den = M * vel * vel;
       for (int j = 0; j < L; ++j) {
         x2[j] += 0.25 * delta * (a.Q1 * x1[j] * x1[j] - a.kT) / a.Q2;
-        den += cfac * a.Q1 * x1[j] * x1[j] * exp(-x2[j] * delta);
+        e[j] = exp(-0.5 * x2[j] * delta);
+        den += cfac * a.Q1 * x1[j] * x1[j] * (e[j] * e[j]);
       }
       const double H = sqrt(lam / den);
       vel *= H;
       for (int j = 0; j < L; ++j) {
-        x1[j] *= H * exp(-0.5 * x2[j] * delta);
+        x1[j] *= H * e[j];
         x2[j] += 0.25 * delta * (a.Q1 * x1[j] * x1[j] - a.kT) / a.Q2;
       }
     }
