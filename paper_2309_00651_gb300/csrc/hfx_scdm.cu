@@ -27,7 +27,7 @@ namespace ace {
 namespace {
 
 constexpr int kUpdThreads = 256;
-constexpr int kUpdPoints = 2;  // grid points per thread per sweep (independent dot products)
+constexpr int kUpdPoints = 4;  // grid points per thread per sweep (independent dot products)
 
 template <typename T>
 __device__ __forceinline__ T round_to(double v);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(1024) k_scdm_pick(const double* __restrict__ p
 // step j: c_p = q_j . Psi^T[:, p], nu_p -= c_p^2 (picked points stay at -1), per-block maxima;
 // each thread takes kUpdPoints grid points, rows unrolled for loads in flight
 template <typename T>
-__global__ void __launch_bounds__(kUpdThreads) k_scdm_update(const T* __restrict__ A, long long N, int n,
+__global__ void __launch_bounds__(kUpdThreads, 3) k_scdm_update(const T* __restrict__ A, long long N, int n,
                                                              const T* __restrict__ qt, long long ldt, int j,
                                                              const long long* __restrict__ piv,
                                                              double* __restrict__ nu, double* __restrict__ bmax,
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_scdm_update(const T* __restrict
       c[u] = T(0);
       in[u] = p0 + u * kUpdThreads < N;
     }
-#pragma unroll 16
+#pragma unroll 8
     for (int i = 0; i < n; ++i) {
       const T qi = q[i];
       const T* row = A + (long long)i * N + p0;
@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_scdm_update(const T* __restrict
   if (threadIdx.x == 0) { bmax[blockIdx.x] = best; bidx[blockIdx.x] = bi; }
 }
 
-// blocks of the init / update launches: enough to cover the grid once with kUpdPoints per thread,
-// at most 8 per SM
+// blocks of the init / update launches: enough to cover the grid once with kUpdPoints per thread
+// (one wave at 3 blocks per SM for the 128 x 72^3 case), at most 8 per SM
 static int scdm_blocks(long long N, int sm_count) {
   const long long cover = (N + (long long)kUpdThreads * kUpdPoints - 1) / ((long long)kUpdThreads * kUpdPoints);
   return (int)std::max(1LL, std::min<long long>(cover, (long long)sm_count * 8));
