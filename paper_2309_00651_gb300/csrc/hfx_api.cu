@@ -94,8 +94,8 @@ struct Schedule {
   std::vector<int> slot_couple_base;    // [nslots + 1], prefix of slot_cap
   std::vector<int> batch_slot_begin;    // [nbatches + 1]
   // per batch: slots taken by the dense accumulation kernel and by the generic one
-  std::vector<int> dense_slots, generic_slots;             // concatenated over batches
-  std::vector<int> dense_begin, generic_begin;             // [nbatches + 1] offsets into the lists
+  std::vector<int> dense_slots, generic_slots, diag_slots;  // concatenated over batches
+  std::vector<int> dense_begin, generic_begin, diag_begin;  // [nbatches + 1] offsets into the lists
   long long max_batch_couples = 0, max_total_couples = 0;
   // device copies
   int2* d_slot_blocks = nullptr;
@@ -103,6 +103,7 @@ struct Schedule {
   int* d_slot_couple_base = nullptr;
   int* d_dense_slots = nullptr;
   int* d_generic_slots = nullptr;
+  int* d_diag_slots = nullptr;
 };
 
 static int block_size_of(int bi, int b, int n_orb) { return std::min(b, n_orb - bi * b); }
@@ -115,7 +116,7 @@ static int slot_capacity(int si, int sj, bool diag) {
 }
 
 static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budget, size_t bytes_per_couple,
-                           bool dense_ok) {
+                           bool dense_ok, bool diag_ok) {
   S.n_orb = n_orb;
   S.b = b;
   S.nb = (n_orb + b - 1) / b;
@@ -178,17 +179,21 @@ static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budge
   for (int k = 0; k < S.nslots; ++k) S.slot_couple_base[k + 1] = S.slot_couple_base[k] + S.slot_cap[k];
   S.dense_slots.clear();
   S.generic_slots.clear();
+  S.diag_slots.clear();
   S.dense_begin.assign(1, 0);
   S.generic_begin.assign(1, 0);
+  S.diag_begin.assign(1, 0);
   for (int bt = 0; bt < S.nbatches; ++bt) {
     for (int k = S.batch_slot_begin[bt]; k < S.batch_slot_begin[bt + 1]; ++k) {
       const int2 bp = S.slot_blocks[k];
       const bool full = block_size_of(bp.x, b, n_orb) == b && block_size_of(bp.y, b, n_orb) == b;
       if (dense_ok && bp.x != bp.y && full) S.dense_slots.push_back(k);
+      else if (diag_ok && bp.x == bp.y && full) S.diag_slots.push_back(k);
       else S.generic_slots.push_back(k);
     }
     S.dense_begin.push_back((int)S.dense_slots.size());
     S.generic_begin.push_back((int)S.generic_slots.size());
+    S.diag_begin.push_back((int)S.diag_slots.size());
   }
 }
 
@@ -307,6 +312,10 @@ static size_t smem_dense_ct(int n, int b) {
   const int zc = 8, ln = kDenseRowsCt * (b / 2) * zc, pts = n * zc;
   return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
 }
+static size_t smem_diag_ct(int n, int b) {
+  const int zc = 8, ln = kDiagCouplesPerItCt * zc, pts = n * zc;
+  return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)b * pts * sizeof(float);
+}
 
 // per-stage twiddle tables of one edge: stage s with m > 1 holds w_L^{j1 k}, j1 < m, k < r, L = r m
 static std::vector<double> stage_twiddles(int n) {
@@ -337,6 +346,11 @@ static int eparts(const hfx_ctx* c) { return c->pencil ? c->grid[1] * (c->grid[2
 static bool dense_available(const hfx_ctx* c) {
   return c->prec == HFX_PREC_FP64 ? Passes<double>::has_dense(c->bsize) : Passes<float>::has_dense(c->bsize);
 }
+// the register-accumulating pass for full diagonal block pairs exists for the compile-time FP32
+// geometry with blocks of 8
+static bool diag_available(const hfx_ctx* c) {
+  return c->ct != nullptr && c->prec == HFX_PREC_FP32 && c->bsize == 8;
+}
 
 static void free_ctx_tables(hfx_ctx* c) {
   for (cudaEvent_t* e : {&c->ev_fork, &c->ev_p2, &c->ev_p3[0], &c->ev_p3[1]}) {
@@ -359,7 +373,7 @@ static void free_ctx_tables(hfx_ctx* c) {
   for (auto& kv : c->sched) {
     Schedule& S = *kv.second;
     for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
-                    (void*)S.d_dense_slots, (void*)S.d_generic_slots})
+                    (void*)S.d_dense_slots, (void*)S.d_generic_slots, (void*)S.d_diag_slots})
       if (p) cudaFree(p);
   }
   c->sched.clear();
@@ -525,7 +539,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (prec == HFX_PREC_FP32 && !c->pencil && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
     const CtFns* f = ct_fns(grid[0]);
     const int n = grid[0];
-    if (f && std::max(smem_plane_ct(n), smem_dense_ct(n, 8)) + 512 <= (size_t)c->max_smem) {
+    if (f && std::max({smem_plane_ct(n), smem_dense_ct(n, 8), smem_diag_ct(n, 8)}) + 512 <= (size_t)c->max_smem) {
       e = f->prepare(c->max_smem - 512, smem_plane_ct(n), &c->blocks_fwd_ct, &c->blocks_x_ct);
       if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
       auto tw = to_real_vec<float>(stage_twiddles(n));
@@ -569,7 +583,8 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static Schedule make_host_schedule(const hfx_ctx* c, int n_orb) {
   Schedule S;
-  build_schedule(S, n_orb, c->bsize, c->transform_budget, (size_t)c->N * cplx_size(c), dense_available(c));
+  build_schedule(S, n_orb, c->bsize, c->transform_budget, (size_t)c->N * cplx_size(c), dense_available(c),
+                 diag_available(c));
   return S;
 }
 
@@ -613,9 +628,10 @@ static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
   if (st == HFX_OK) st = up((void**)&S->d_dense_slots, S->dense_slots.data(), S->dense_slots.size() * sizeof(int));
   if (st == HFX_OK)
     st = up((void**)&S->d_generic_slots, S->generic_slots.data(), S->generic_slots.size() * sizeof(int));
+  if (st == HFX_OK) st = up((void**)&S->d_diag_slots, S->diag_slots.data(), S->diag_slots.size() * sizeof(int));
   if (st != HFX_OK) {
     for (void* p : {(void*)S->d_slot_blocks, (void*)S->d_slot_of_bp, (void*)S->d_slot_couple_base,
-                    (void*)S->d_dense_slots, (void*)S->d_generic_slots})
+                    (void*)S->d_dense_slots, (void*)S->d_generic_slots, (void*)S->d_diag_slots})
       if (p) cudaFree(p);
     return st;
   }
@@ -780,6 +796,13 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
                                S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
                                (const C*)c->d_tw[1], vxphi, vscale);
       if (nd > 0) prof_close(c, kProfAcc, e0, st);
+      const int ndg = S.diag_begin[b + 1] - S.diag_begin[b];
+      e0 = prof_mark(c, st);
+      if (ndg > 0)  // [full diagonal block pairs]; the generic pass takes whatever is left
+        ct->y_acc_diag(dim3(nzc, g.n1, ndg), smem_diag_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
+                       S.d_diag_slots + S.diag_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
+                       (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
+      if (ndg > 0) prof_close(c, kProfAccGeneric, e0, st);
       e0 = prof_mark(c, st);
       if (ng > 0)
         Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
@@ -918,7 +941,8 @@ extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_
     launches = 1 /* placement */ + 1 /* energy */ + (long long)S.nbatches * 2;
     if (!eo)
       for (int b = 0; b < S.nbatches; ++b)
-        launches += (S.dense_begin[b + 1] > S.dense_begin[b]) + (S.generic_begin[b + 1] > S.generic_begin[b]);
+        launches += (S.dense_begin[b + 1] > S.dense_begin[b]) + (S.generic_begin[b + 1] > S.generic_begin[b]) +
+                    (S.diag_begin[b + 1] > S.diag_begin[b]);
     if (c->prec == HFX_PREC_FP32 && !(flags & HFX_ORBITALS_F32)) launches += 1; /* FP64 -> FP32 orbitals */
   } else if (!(flags & HFX_ACCUMULATE)) {
     launches = 1;
@@ -1070,6 +1094,7 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   const size_t o_base = take(S.slot_couple_base.size() * sizeof(int));
   const size_t o_dense = take(S.dense_slots.size() * sizeof(int));
   const size_t o_gen = take(S.generic_slots.size() * sizeof(int));
+  const size_t o_diag = take(S.diag_slots.size() * sizeof(int));
   const Layout L = layout_of(c, S, n_orb, n_pairs);
   if (off + L.total > kNoallocScratchBytes)
     return fail(HFX_ERR_OOM,
@@ -1088,11 +1113,13 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   HFX_CUDA_TRY(put(o_base, S.slot_couple_base.data(), S.slot_couple_base.size() * sizeof(int)));
   HFX_CUDA_TRY(put(o_dense, S.dense_slots.data(), S.dense_slots.size() * sizeof(int)));
   HFX_CUDA_TRY(put(o_gen, S.generic_slots.data(), S.generic_slots.size() * sizeof(int)));
+  HFX_CUDA_TRY(put(o_diag, S.diag_slots.data(), S.diag_slots.size() * sizeof(int)));
   S.d_slot_blocks = (int2*)(base + o_blocks);
   S.d_slot_of_bp = (int*)(base + o_of_bp);
   S.d_slot_couple_base = (int*)(base + o_base);
   S.d_dense_slots = (int*)(base + o_dense);
   S.d_generic_slots = (int*)(base + o_gen);
+  S.d_diag_slots = (int*)(base + o_diag);
 
   c->ws = base + off;
   c->ws_bytes = kNoallocScratchBytes - off;
@@ -1155,7 +1182,7 @@ extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_byt
     for (auto& kv : c->sched) {
       Schedule& S = *kv.second;
       for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
-                      (void*)S.d_dense_slots, (void*)S.d_generic_slots})
+                      (void*)S.d_dense_slots, (void*)S.d_generic_slots, (void*)S.d_diag_slots})
         if (p) cudaFree(p);
     }
     c->sched.clear();

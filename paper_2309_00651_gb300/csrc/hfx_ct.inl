@@ -1,6 +1,7 @@
 // Launchers of the compile-time-geometry FP32 passes for edge HFX_CT_N (one translation unit per
 // edge, so the sizes compile in parallel).
 #include "hfx_ct.cuh"
+#include "hfx_ct_diag.cuh"
 #include "hfx_internal.h"
 
 namespace hfx {
@@ -11,7 +12,7 @@ constexpr int kB = 8;
 
 cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x) {
   const void* ks[] = {(const void*)ct::k_fwd_yz_ct<float, kN>, (const void*)ct::k_x_coulomb_ct<float, kN>,
-                      (const void*)ct::k_y_acc_dense_ct<float, kN, kB>};
+                      (const void*)ct::k_y_acc_dense_ct<float, kN, kB>, (const void*)ct::k_y_acc_diag_ct<float, kN, kB>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
     if (e != cudaSuccess) return e;
@@ -42,7 +43,14 @@ void y_acc_dense(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }
 
-const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense};
+void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
+                const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* W,
+                const float2* tw, double* V, double vscale) {
+  ct::k_y_acc_diag_ct<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
+      orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
+}
+
+const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense, &y_acc_diag};
 
 }  // namespace
 

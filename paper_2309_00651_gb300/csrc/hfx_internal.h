@@ -43,6 +43,10 @@ struct Passes {
 
 namespace hfx {
 
+// couple tiles per ring slot of the diagonal-block accumulate pass (hfx_ct_diag.cuh): the 18
+// couples of a full B = 8 diagonal block pair in 3 slots
+constexpr int kDiagCouplesPerItCt = 6;
+
 // Compile-time-geometry FP32 passes for cubic grids of edge N (hfx_ct.cuh), one translation unit
 // per N; ct_fns(N) returns NULL for an edge without one.
 struct CtFns {
@@ -56,6 +60,10 @@ struct CtFns {
   void (*y_acc_dense)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                       const int4* couples, const int* slot_list, const int* slot_couple_base,
                       const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
+  // full diagonal block pairs (B = 8), same arguments and threads as the dense pass
+  void (*y_acc_diag)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
+                     const int4* couples, const int* slot_list, const int* slot_couple_base,
+                     const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
 };
 
 #define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128)
