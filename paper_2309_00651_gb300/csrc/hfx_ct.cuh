@@ -166,6 +166,36 @@ __device__ __forceinline__ void ld2(const double2* src, double2& a, double2& b) 
   b = __ldg(src + 1);
 }
 
+// FP32 -> FP64, exact for normal numbers and +-0, with integer operations only (sign, exponent
+// rebias 127 -> 1023, fraction widened); FP32 subnormals flush to zero.  The flushes below use it
+// so that their only FP64 instruction is the final add (the FP64 pipe of this part is narrow).
+__device__ __forceinline__ double widen_exact(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned mag = u & 0x7fffffffu, sign = u & 0x80000000u;
+  const bool tiny = mag < 0x00800000u;
+  const unsigned hi = tiny ? sign : (((mag >> 3) + 0x38000000u) | sign);
+  const unsigned lo = tiny ? 0u : (mag << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+// block-wide sum in FP32 (warp shuffles, then warp 0 over the warp partials); valid in thread 0
+__device__ __forceinline__ float block_sum_f32(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    r = (l < nw) ? red[l] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+  }
+  return r;
+}
+
 constexpr int kUnroll = 4;
 
 // ----------------------------------------------------------------------------------
@@ -243,7 +273,7 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
-  __shared__ double red[32];
+  __shared__ float red[32];
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
 
   const int items = (c1 - c0) * N;
@@ -257,7 +287,9 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
     stage_fwd_g2s<P.r[0], P.m[0], N, PLANE, 1, S, N, NT>(wc, buf, tw + P.twoff[0]);
     stages<N, false, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // remaining x stages but the last
     // last forward x stage (no twiddles) + Coulomb + energy + first inverse x stage
-    double e_acc = 0.0;
+    // the plane's energy partial in FP32 (a few terms per thread, then a tree over the block),
+    // widened once; the partials of all planes and couples are summed in FP64
+    T e_acc = T(0);
     {
       constexpr int TOTAL = N * (N / RL);
       const T* vy = vtab + (long long)y * N;
@@ -279,7 +311,7 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
           v[k].x *= vg[k];
           v[k].y *= vg[k];
         }
-        e_acc += double(e);
+        e_acc += e;
         if (!energy_only) {
           Dft<RL, 1, C>::run(v);
 #pragma unroll
@@ -287,8 +319,9 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
         }
       }
     }
-    const double es = block_sum(e_acc, red);
-    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = es;
+    static_assert(sizeof(T) == 4, "compile-time passes are FP32");
+    const float es = block_sum_f32(e_acc, red);
+    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = widen_exact(es);
     if (energy_only) continue;
     __syncthreads();
     // inverse transforms along different axes commute: z first (rows), then the remaining x
@@ -445,7 +478,9 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     __syncthreads();
   }
   // flush, FP64 read-modify-write of V_J (registers) and V_I (shared memory): every load is issued
-  // before any store (a store could alias a later load, which would serialise the round trips)
+  // before any store (a store could alias a later load, which would serialise the round trips);
+  // the contribution is scaled in FP32 and widened exactly, so one FP64 add per element remains
+  const float vs = (float)vscale;
   double old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
@@ -455,7 +490,7 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + vscale * double(accJ[k][j]);
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * accJ[k][j]);
   }
 #pragma unroll
   for (int k = 0; k < NP; ++k)
@@ -467,7 +502,7 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     const int p = threadIdx.x + k * NT;
 #pragma unroll
     for (int j = 0; j < B; ++j)
-      V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vscale * double(accI[j * PTS + p]);
+      V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * accI[j * PTS + p]);
   }
 }
 

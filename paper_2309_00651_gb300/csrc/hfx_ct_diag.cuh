@@ -172,7 +172,9 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
     __syncthreads();
   });
 
-  // FP64 read-modify-write of the block's V rows: every load before any store
+  // FP64 read-modify-write of the block's V rows: every load before any store; the contribution is
+  // scaled in FP32 and widened exactly (one FP64 add per element)
+  const float vs = (float)vscale;
   double old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
@@ -182,7 +184,7 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vscale * double(acc[k][j]);
+    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * acc[k][j]);
   }
 }
 
