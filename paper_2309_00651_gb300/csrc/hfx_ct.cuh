@@ -338,7 +338,9 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
 template <typename T, int N> struct DenseGeo {
   static constexpr int ZC = ZChunk<T>::value;
   static constexpr int PTS = N * ZC;
-  static constexpr int NP = (PTS + 319) / 320;                      // points per thread
+  // points per thread: one up to 640 points (more warps hide the pass's load latency), else as
+  // few as keep the block within 320 threads
+  static constexpr int NP = PTS <= 640 ? 1 : (PTS + 319) / 320;
   static constexpr int NT = ((PTS + NP - 1) / NP + 31) / 32 * 32;   // threads
 };
 
