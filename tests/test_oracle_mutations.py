@@ -75,17 +75,16 @@ def test_dropped_half_in_energy(monkeypatch):
 
 
 def test_off_diagonal_weight_one(monkeypatch):
-    # count every pair once: rescale the energy terms of i != j pairs by 1/2 through the pair
-    # transform (|F|^2 halves when F is scaled by 1/sqrt 2), leaving the potentials alone
-    good_t, good_p = O.pair_transform, O.pair_potential
+    # count every i != j pair once: its energy term halves when its transform is scaled by 1/sqrt 2
+    # (its potential is scaled too, a second symptom of the same mistake)
+    good_t = O.pair_transform
 
     def bad_t(phi_i, phi_j, direct=None):
         F = good_t(phi_i, phi_j, direct)
-        return F if phi_i is phi_j else F / math.sqrt(2.0)
+        same = phi_i.__array_interface__["data"][0] == phi_j.__array_interface__["data"][0]
+        return F if same else F / math.sqrt(2.0)
 
     monkeypatch.setattr(O, "pair_transform", bad_t)
-    monkeypatch.setattr(O, "pair_potential",
-                        lambda F, v, direct=None: good_p(F, v, direct))
     assert not real_closed_form_holds()
 
 
