@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ace", action="store_true", help="skip the ACE / screen rows")
     ap.add_argument("--rows-only", action="store_true",
