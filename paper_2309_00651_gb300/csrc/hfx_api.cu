@@ -576,7 +576,7 @@ extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes)
 // workspace layout
 // ------------------------------------------------------------------------------------
 struct Layout {
-  size_t orb32, W, W2, epart, couples, total;
+  size_t orb32, W, W2, epart, eblk, couples, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -599,6 +599,7 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   // a second transform buffer when batches are pipelined on two streams
   L.W2 = take(S.nbatches > 1 && c->side && c->pipeline ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
   L.epart = take((size_t)S.max_total_couples * eparts(c) * sizeof(double));
+  L.eblk = take((size_t)64 * sizeof(double));  // per-block energy sums (kEnergyBlocks)
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
   L.total = off;
   return L;
@@ -684,13 +685,18 @@ __global__ void k_plan_place(const int2* __restrict__ pairs, long long P, int n_
   }
 }
 
-// one block: E_x = scale * sum_g w_g sum_y epart[g][y] (fixed order), stored or accumulated
-__global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__ epart, const int4* __restrict__ couples,
-                                                      int total, int n2, double scale, int accumulate,
-                                                      double* __restrict__ ex) {
+// E_x = scale * sum_g w_g sum_y epart[g][y], in two deterministic launches: block b of
+// k_energy_blocks sums couples [b*chunk, (b+1)*chunk) in a fixed order, k_energy_final sums the
+// kEnergyBlocks block results in order and stores or accumulates E_x
+constexpr int kEnergyBlocks = 64;
+
+__global__ void __launch_bounds__(256) k_energy_blocks(const double* __restrict__ epart, const int4* __restrict__ couples,
+                                                       int total, int n2, double* __restrict__ eblk) {
   __shared__ double red[32];
+  const int chunk = (total + gridDim.x - 1) / gridDim.x;
+  const int g0 = blockIdx.x * chunk, g1 = min(total, g0 + chunk);
   double s = 0.0;
-  for (int g = threadIdx.x; g < total; g += blockDim.x) {
+  for (int g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
     const int4 cp = couples[g];
     if (couple_empty(cp)) continue;
     // both halves of a couple share a weight class: diagonal pairs count once, others twice
@@ -700,7 +706,20 @@ __global__ void __launch_bounds__(256) k_energy_final(const double* __restrict__
     s += (diag ? 1.0 : 2.0) * t;
   }
   const double tot = block_sum(s, red);
-  if (threadIdx.x == 0) ex[0] = (accumulate ? ex[0] : 0.0) + scale * tot;
+  if (threadIdx.x == 0) eblk[blockIdx.x] = tot;
+}
+
+__global__ void k_energy_final(const double* __restrict__ eblk, int nb, double scale, int accumulate,
+                               double* __restrict__ ex) {
+  double t = 0.0;
+  for (int b = 0; b < nb; ++b) t += eblk[b];
+  ex[0] = (accumulate ? ex[0] : 0.0) + scale * t;
+}
+
+static void launch_energy(const double* epart, const int4* couples, int total, int n2, double* eblk, double scale,
+                          bool accumulate, double* ex, cudaStream_t st) {
+  k_energy_blocks<<<kEnergyBlocks, 256, 0, st>>>(epart, couples, total, n2, eblk);
+  k_energy_final<<<1, 1, 0, st>>>(eblk, kEnergyBlocks, scale, accumulate ? 1 : 0, ex);
 }
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
@@ -883,8 +902,8 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
   cudaEvent_t e_en = prof_mark(c, st);
-  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S->max_total_couples, eparts(c),
-                                    scale, accumulate ? 1 : 0, ex_dev);
+  launch_energy((const double*)(ws + L.epart), couples, (int)S->max_total_couples, eparts(c), (double*)(ws + L.eblk),
+                scale, accumulate, ex_dev, st);
   prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
@@ -938,7 +957,7 @@ extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_
   const bool eo = (flags & HFX_ENERGY_ONLY) != 0;
   long long launches = 0;
   if (n_pairs > 0) {
-    launches = 1 /* placement */ + 1 /* energy */ + (long long)S.nbatches * 2;
+    launches = 1 /* placement */ + 2 /* energy */ + (long long)S.nbatches * 2;
     if (!eo)
       for (int b = 0; b < S.nbatches; ++b)
         launches += (S.dense_begin[b + 1] > S.dense_begin[b]) + (S.generic_begin[b + 1] > S.generic_begin[b]) +
@@ -1154,8 +1173,8 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   }
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
-  k_energy_final<<<1, 256, 0, st>>>((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), scale,
-                                    accumulate ? 1 : 0, ex_dev);
+  launch_energy((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), (double*)(ws + L.eblk),
+                scale, accumulate, ex_dev, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
 }
