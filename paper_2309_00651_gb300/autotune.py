@@ -18,7 +18,7 @@ from .hfx import Exchange
 
 DEFAULT_CANDIDATES = tuple(
     {"block": b, "batch_bytes": mb << 20, "pipeline": p}
-    for b in (8, 4) for mb in (1024, 2048, 512) for p in (True, False))
+    for b in (8, 4) for mb in (1024, 2048, 512, 256) for p in (True, False))
 
 
 def cache_path() -> str:
