@@ -320,3 +320,17 @@ def test_sphere_kernel_matches_oracle():
     E, V = run_gpu(phi, pairs, lat, "fp64", kernel="coulomb_sphere", ecut=ecut)
     assert abs(E - E_ref) <= 1e-8 * abs(E_ref)
     assert rel(V, V_ref) <= 1e-8
+
+
+def test_compile_time_passes_with_sparse_pair_list():
+    """FP32 on a compile-time grid (32^3) with a random third of the pairs: the dense and the
+    diagonal-block accumulate passes see couples with one or both halves missing."""
+    w = I.WORKLOADS["pw16_n32"]
+    phi, allp, _ = I.make_workload(w)
+    rng = np.random.default_rng(17)
+    sub = allp[np.sort(rng.permutation(len(allp))[: len(allp) // 3])]
+    assert any(i == j for i, j in sub) and any(i != j for i, j in sub)
+    E_ref, V_ref = O.exchange(phi, sub, w.lattice)
+    E, V = run_gpu(phi, sub, w.lattice, "fp32")
+    assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert rel(V, V_ref) <= TOL["fp32"]
