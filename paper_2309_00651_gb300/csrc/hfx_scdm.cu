@@ -112,33 +112,38 @@ __global__ void __launch_bounds__(kUpdThreads) k_scdm_init(const double* __restr
   if (threadIdx.x == 0) { bmax[blockIdx.x] = best; bidx[blockIdx.x] = bi; }
 }
 
-// step j: pick p_j and form q_j (one block of 1024 threads; dynamic shared memory holds a[n], h[n]
-// and the per-warp partial sums hp[32][n], all in T)
+// step j: pick p_j and form q_j (one block of kPickThreads threads; dynamic shared memory holds
+// a[n], h[n] and the per-warp partial sums hp[32][n], all in T).  The kernel is a chain of short
+// phases, so each phase issues all of its global loads before it uses any of them: the argmax
+// reads at most two per-block maxima per thread, and the Gram-Schmidt products read up to
+// kPickChunks x kPickRows entries of Q per lane at once.
+constexpr int kPickThreads = 1024;
+constexpr int kPickChunks = 4;  // 32-column chunks of Q a lane holds in flight (128 columns)
+constexpr int kPickRows = 4;    // rows of Q a warp takes at once in a -= Q h
 template <typename T>
-__global__ void __launch_bounds__(1024) k_scdm_pick(const double* __restrict__ psi, long long N, int n, int j,
-                                                    const double* __restrict__ bmax, const long long* __restrict__ bidx,
-                                                    int nb, long long* __restrict__ piv, T* __restrict__ qt,
-                                                    double* __restrict__ q64, long long ldt, double* __restrict__ rdiag,
-                                                    int* err) {
+__global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __restrict__ psi, long long N, int n, int j,
+                                                            const double* __restrict__ bmax,
+                                                            const long long* __restrict__ bidx, int nb,
+                                                            long long* __restrict__ piv, T* __restrict__ qt,
+                                                            double* __restrict__ q64, long long ldt,
+                                                            double* __restrict__ rdiag, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   T* a = reinterpret_cast<T*>(smem);  // [n]
   T* h = a + n;                       // [n]
   T* hp = h + n;                      // [32][n]
   __shared__ double red[33];
   __shared__ double scal[2];
+  __shared__ double sv[32];
+  __shared__ long long si[32];
   __shared__ long long pick;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (w == 0) {  // argmax over the per-block maxima, in one warp
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int nw = kPickThreads / 32;
+  {  // argmax over the per-block maxima (lowest index on a tie), the whole block
     double best = -2.0;
     long long bi = (long long)1 << 62;
-    for (int b = lane; b < nb; b += 32) take_max(best, bi, bmax[b], bidx[b]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
-      const long long i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-      take_max(best, bi, v2, i2);
-    }
-    if (lane == 0) {
+    for (int b = threadIdx.x; b < nb; b += kPickThreads) take_max(best, bi, bmax[b], bidx[b]);
+    block_argmax(best, bi, sv, si);
+    if (threadIdx.x == 0) {
       const bool ok = best > 0.0 && bi < N;
       if (!ok) atomicOr(err, kErrRankDeficient);
       pick = ok ? bi : 0;
@@ -153,30 +158,69 @@ __global__ void __launch_bounds__(1024) k_scdm_pick(const double* __restrict__ p
     sa = (double)a[threadIdx.x] * (double)a[threadIdx.x];
   }
   const double an2 = sum_first_n(sa, n, red);
-  // two passes of classical Gram-Schmidt against q_0..q_{j-1} (qt[i][k] = q_k[i]):
-  //   h = Q^T a  (warp w takes rows i = w, w + 32, ...; lanes take k: coalesced row reads)
-  //   a -= Q h   (warp w takes rows i = w, w + 32, ...; lanes take k, then a warp sum)
+  // two passes of classical Gram-Schmidt against q_0..q_{j-1} (qt[i][k] = q_k[i])
   for (int pass = 0; pass < 2; ++pass) {
-    for (int k0 = 0; k0 < j; k0 += 32) {
-      const int k = k0 + lane;
+    // h = Q^T a: warp w takes rows i = w, w + 32, ...; lane takes columns k = K0 + lane + 32 c
+    for (int K0 = 0; K0 < j; K0 += 32 * kPickChunks) {
+      T s[kPickChunks];
+#pragma unroll
+      for (int c = 0; c < kPickChunks; ++c) s[c] = T(0);
+#pragma unroll 4
+      for (int i = w; i < n; i += nw) {
+        const T ai = a[i];
+        const T* row = qt + (long long)i * ldt;
+#pragma unroll
+        for (int c = 0; c < kPickChunks; ++c) {
+          const int k = K0 + lane + 32 * c;
+          if (k < j) s[c] = fma(row[k], ai, s[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kPickChunks; ++c) {
+        const int k = K0 + lane + 32 * c;
+        if (k < j) hp[w * n + k] = s[c];
+      }
+    }
+    __syncthreads();
+    // h[k] = sum over the 32 warp partials, eight threads per column
+    for (int base = 0; base < j; base += kPickThreads / 8) {
+      const int k = base + (threadIdx.x >> 3), part = threadIdx.x & 7;
       T s = T(0);
       if (k < j)
-        for (int i = w; i < n; i += nw) s = fma(qt[(long long)i * ldt + k], a[i], s);
-      if (k < j) hp[w * n + k] = s;
+        for (int q = part; q < nw; q += 8) s += hp[q * n + k];
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      if (k < j && part == 0) h[k] = s;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < j; k += blockDim.x) {
-      T s = T(0);
-      for (int q = 0; q < nw; ++q) s += hp[q * n + k];
-      h[k] = s;
-    }
-    __syncthreads();
-    for (int i = w; i < n; i += nw) {
-      T s = T(0);
-      for (int k = lane; k < j; k += 32) s = fma(qt[(long long)i * ldt + k], h[k], s);
+    // a -= Q h: warp w takes kPickRows rows at once (i = i0 + r * 32); lanes take columns
+    for (int i0 = w; i0 < n; i0 += kPickRows * nw) {
+      T s[kPickRows];
 #pragma unroll
-      for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) a[i] -= s;
+      for (int r = 0; r < kPickRows; ++r) s[r] = T(0);
+      for (int K0 = 0; K0 < j; K0 += 32 * kPickChunks) {
+#pragma unroll
+        for (int c = 0; c < kPickChunks; ++c) {
+          const int k = K0 + lane + 32 * c;
+          if (k < j) {
+            const T hk = h[k];
+#pragma unroll
+            for (int r = 0; r < kPickRows; ++r) {
+              const int i = i0 + r * nw;
+              if (i < n) s[r] = fma(qt[(long long)i * ldt + k], hk, s[r]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kPickRows; ++r) {
+        T t = s[r];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        const int i = i0 + r * nw;
+        if (lane == 0 && i < n) a[i] -= t;
+      }
     }
     __syncthreads();
   }
@@ -271,7 +315,7 @@ static cudaError_t scdm_run(const double* psi, long long N, int n, T* a32, doubl
   }
   const size_t upd_smem = (size_t)n * sizeof(T);
   for (int j = 0; j < n; ++j) {
-    k_scdm_pick<T><<<1, 1024, pick_smem, st>>>(psi, N, n, j, bmax, bidx, nb, piv, qt, q64, ldt, rdiag, err);
+    k_scdm_pick<T><<<1, kPickThreads, pick_smem, st>>>(psi, N, n, j, bmax, bidx, nb, piv, qt, q64, ldt, rdiag, err);
     if (j + 1 < n) k_scdm_update<T><<<nb, kUpdThreads, upd_smem, st>>>(A, N, n, qt, ldt, j, piv, nu, bmax, bidx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
