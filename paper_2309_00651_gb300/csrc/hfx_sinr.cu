@@ -1,8 +1,9 @@
 // SIN(R) isokinetic-thermostat updates of the multiple-time-step integrator (the paper's
 // appendix, updates A, B and C, applied in its XI-RESPA factorisation; equations of motion
 // eq. eom, constraint eq. kecons).  One thread per physical degree of freedom I, its L thermostat
-// velocities v1_{I,j}, v2_{I,j} in registers; FP64 throughout (the updates are a few dozen
-// operations per degree of freedom and bound by memory traffic).
+// velocities v1_{I,j}, v2_{I,j} in registers; FP64 throughout.  The FP64 pipe of this part is
+// narrow, so the quotients that do not depend on the degree of freedom are taken once on the host
+// (Delta/(4 Q2), -Delta/2, sqrt(Lambda), L Q1/(L+1)) and H comes from one reciprocal square root.
 //
 //   A  exp(iL_N Delta/2), n_res x n_sy factors with Delta = w_k dt / n_res:
 //        v2 += (Delta/4) (Q1 v1^2 - kT)/Q2
@@ -28,8 +29,13 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__global__ void __launch_bounds__(kThreads) k_update_n(SinrArgs a, long long n_dof, double dt, int n_res, int n_sy,
-                                                       SyWeights w, const double* __restrict__ mass,
+// per Suzuki-Yoshida factor k: c = Delta_k / (4 Q2) and hd = -Delta_k / 2
+struct SubSteps {
+  double c[5], hd[5];
+};
+
+__global__ void __launch_bounds__(kThreads) k_update_n(SinrArgs a, long long n_dof, int n_res, int n_sy, SubSteps ss,
+                                                       double sqrt_lam, double cq, const double* __restrict__ mass,
                                                        double* __restrict__ V, double* __restrict__ v1,
                                                        double* __restrict__ v2) {
   const long long I = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -42,24 +48,22 @@ __global__ void __launch_bounds__(kThreads) k_update_n(SinrArgs a, long long n_d
   }
   const double M = mass[I];
   double vel = V[I];
-  const double lam = L * a.kT, cfac = (double)L / (L + 1.0);
   for (int r = 0; r < n_res; ++r) {
     for (int k = 0; k < n_sy; ++k) {
-      const double delta = w.w[k] * dt / n_res;
+      const double c = ss.c[k], hd = ss.hd[k];
       // e_j = exp(-v2_j Delta/2) serves both the rescaling of v1 and, squared, the denominator of H
-      // (one exponential per chain element and sub-step: the FP64 pipe of this part is narrow)
       double e[kMaxChain];
       double den = M * vel * vel;
       for (int j = 0; j < L; ++j) {
-        x2[j] += 0.25 * delta * (a.Q1 * x1[j] * x1[j] - a.kT) / a.Q2;
-        e[j] = exp(-0.5 * x2[j] * delta);
-        den += cfac * a.Q1 * x1[j] * x1[j] * (e[j] * e[j]);
+        x2[j] += c * fma(a.Q1 * x1[j], x1[j], -a.kT);
+        e[j] = exp(hd * x2[j]);
+        den += cq * (x1[j] * x1[j]) * (e[j] * e[j]);
       }
-      const double H = sqrt(lam / den);
+      const double H = sqrt_lam * rsqrt(den);
       vel *= H;
       for (int j = 0; j < L; ++j) {
         x1[j] *= H * e[j];
-        x2[j] += 0.25 * delta * (a.Q1 * x1[j] * x1[j] - a.kT) / a.Q2;
+        x2[j] += c * fma(a.Q1 * x1[j], x1[j], -a.kT);
       }
     }
   }
@@ -70,30 +74,34 @@ __global__ void __launch_bounds__(kThreads) k_update_n(SinrArgs a, long long n_d
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_update_v(SinrArgs a, long long n_dof, double dt,
+__global__ void __launch_bounds__(kThreads) k_update_v(SinrArgs a, long long n_dof, double dt, double inv_lam,
                                                        const double* __restrict__ mass, const double* __restrict__ force,
                                                        const double* __restrict__ force_extra, double* __restrict__ V,
                                                        double* __restrict__ v1) {
   const long long I = (long long)blockIdx.x * kThreads + threadIdx.x;
   if (I >= n_dof) return;
   const int L = a.L;
-  const double lam = L * a.kT;
-  const double M = mass[I];
+  const double M = mass[I], inv_m = 1.0 / M;
   const double F = force[I] + (force_extra ? force_extra[I] : 0.0);
   const double vel = V[I];
-  const double ca = F * vel / lam, cb = F * F / (M * lam);
+  const double ca = F * vel * inv_lam, cb = F * F * inv_m * inv_lam;
   const double rb = sqrt(cb), h = 0.5 * dt, x = rb * h;
   double s, sd;
   if (x < 1e-4) {
     s = h * (1.0 + cb * h * h / 6.0 + cb * cb * h * h * h * h / 120.0) + ca * h * h * (0.5 + cb * h * h / 24.0);
     sd = 1.0 + cb * h * h / 2.0 + cb * cb * h * h * h * h / 24.0 + ca * h * (1.0 + cb * h * h / 6.0);
   } else {
-    const double sh = sinh(x), shh = sinh(0.5 * x);
-    s = sh / rb + (ca / cb) * (2.0 * shh * shh);
-    sd = cosh(x) + (ca / rb) * sh;
+    // one hyperbolic function: sinh x = 2 sinh(x/2) cosh(x/2), cosh x - 1 = 2 sinh(x/2)^2,
+    // cosh(x/2) = sqrt(1 + sinh(x/2)^2); a/b = V M / F (F != 0 on this branch)
+    const double shh = sinh(0.5 * x);
+    const double chh = sqrt(fma(shh, shh, 1.0));
+    const double sh = 2.0 * shh * chh, chm1 = 2.0 * shh * shh;
+    const double inv_rb = 1.0 / rb;
+    s = sh * inv_rb + (vel * M / F) * chm1;
+    sd = 1.0 + chm1 + ca * inv_rb * sh;
   }
   const double inv = 1.0 / sd;
-  V[I] = (vel + s * F / M) * inv;
+  V[I] = (vel + s * F * inv_m) * inv;
   for (int j = 0; j < L; ++j) v1[I * L + j] *= inv;
 }
 
@@ -115,14 +123,21 @@ int blocks(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 cudaError_t update_n(const SinrArgs& a, long long n_dof, double dt, int n_res, const SyWeights& w, int n_sy,
                      const double* mass, double* V, double* v1, double* v2, cudaStream_t st) {
   if (n_dof == 0) return cudaSuccess;
-  k_update_n<<<blocks(n_dof), kThreads, 0, st>>>(a, n_dof, dt, n_res, n_sy, w, mass, V, v1, v2);
+  SubSteps ss{};
+  for (int k = 0; k < n_sy; ++k) {
+    const double delta = w.w[k] * dt / n_res;
+    ss.c[k] = 0.25 * delta / a.Q2;
+    ss.hd[k] = -0.5 * delta;
+  }
+  const double sqrt_lam = sqrt(a.L * a.kT), cq = (double)a.L / (a.L + 1.0) * a.Q1;
+  k_update_n<<<blocks(n_dof), kThreads, 0, st>>>(a, n_dof, n_res, n_sy, ss, sqrt_lam, cq, mass, V, v1, v2);
   return cudaGetLastError();
 }
 
 cudaError_t update_v(const SinrArgs& a, long long n_dof, double dt, const double* mass, const double* force,
                      const double* force_extra, double* V, double* v1, cudaStream_t st) {
   if (n_dof == 0) return cudaSuccess;
-  k_update_v<<<blocks(n_dof), kThreads, 0, st>>>(a, n_dof, dt, mass, force, force_extra, V, v1);
+  k_update_v<<<blocks(n_dof), kThreads, 0, st>>>(a, n_dof, dt, 1.0 / (a.L * a.kT), mass, force, force_extra, V, v1);
   return cudaGetLastError();
 }
 
