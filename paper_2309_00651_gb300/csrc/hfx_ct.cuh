@@ -178,24 +178,6 @@ __device__ __forceinline__ double widen_exact(float v) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
-// block-wide sum in FP32 (warp shuffles, then warp 0 over the warp partials); valid in thread 0
-__device__ __forceinline__ float block_sum_f32(float v, float* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  float r = 0.f;
-  if (w == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    r = (l < nw) ? red[l] : 0.f;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-  }
-  return r;
-}
-
 constexpr int kUnroll = 4;
 
 // ----------------------------------------------------------------------------------
@@ -273,9 +255,10 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
-  __shared__ float red[32];
+  __shared__ float red[2][32];  // warp partials of the plane energy, double-buffered by item parity
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
 
+  int par = 0;
   const int items = (c1 - c0) * N;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     const int cl = it / N;
@@ -320,10 +303,25 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
       }
     }
     static_assert(sizeof(T) == 4, "compile-time passes are FP32");
-    const float es = block_sum_f32(e_acc, red);
-    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = widen_exact(es);
-    if (energy_only) continue;
+    // block sum without barriers of its own: a shuffle tree per warp, the warp partials to
+    // red[par] now, and warp 0 adds them (a second tree) after the barrier that the inverse
+    // stages need anyway
+    {
+      float v = e_acc;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) red[par][threadIdx.x >> 5] = v;
+    }
     __syncthreads();
+    if (threadIdx.x < 32) {
+      constexpr int NW = (NT + 31) / 32;
+      float r = threadIdx.x < NW ? red[par][threadIdx.x] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+      if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = widen_exact(r);
+    }
+    par ^= 1;
+    if (energy_only) continue;
     // inverse transforms along different axes commute: z first (rows), then the remaining x
     // stages, the last of which writes W directly
     stages<N, true, 0, P.ns, N, S, 1, NT>(buf, tw);      // z inverse: N rows
