@@ -15,6 +15,7 @@
 //
 // The Cholesky factorisation of -(M + M^T)/2 and the triangular inverse are small FP64
 // kernels; the screen's pair compaction is a count / scan / write sequence over rows.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -525,6 +526,85 @@ __global__ void __launch_bounds__(1024) k_cholesky_smem(const double* __restrict
   if (tid == 0 && bad) atomicOr(err, kErrNotPosDef);
 }
 
+// The same factorisation spread over a cluster of kCholCluster CTAs, one per SM, so that the
+// trailing updates use the FP64 pipes of eight SMs.  CTA r keeps rows i = r + kCholCluster q of
+// the lower triangle in shared memory.  Step k reads column k of the updated A and the pivot's
+// reciprocal square root from a double-buffered column buffer that every CTA holds; whoever
+// updates A[i][k+1] during step k writes it straight into every CTA's next buffer (distributed
+// shared memory), the thread that updates the diagonal element A[k+1][k+1] adds 1/sqrt(d) and
+// 1/d, and one cluster barrier per step orders those writes before their use.
+constexpr int kCholCluster = 8;
+constexpr int kCholThreads = 512;
+constexpr int kCholMaxN = 256;
+constexpr size_t kCholSmemOneCta = 120 * 1024;  // more than half an SM: one CTA of the cluster per SM
+
+__global__ void __cluster_dims__(kCholCluster, 1, 1) __launch_bounds__(kCholThreads, 1)
+    k_cholesky_cluster(const double* __restrict__ m, long long ldm, int n, double* __restrict__ l, int* err) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int C = kCholCluster;
+  const int rank = (int)cluster.block_rank();
+  const int rows_max = (n + C - 1) / C;
+  const int rows = (n - rank + C - 1) / C;  // local rows q: global row i = rank + C q
+  extern __shared__ __align__(16) double sc[];
+  double* A = sc;                                    // [rows_max][n], row q holds columns 0..i
+  double* colbuf = sc + (size_t)rows_max * n;        // [2][n + 2]: column entries, 1/sqrt(d), 1/d
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int NW = kCholThreads / 32;
+
+  // write value v as entry e of column buffer b in every CTA of the cluster
+  auto bcast = [&](int b, int e, double v) {
+#pragma unroll
+    for (int r = 0; r < C; ++r) cluster.map_shared_rank(colbuf, r)[(size_t)b * (n + 2) + e] = v;
+  };
+  auto pivot = [&](int b, double d) {
+    if (!(d > 0.0)) atomicOr(err, kErrNotPosDef);
+    const double r = rsqrt(d);
+    bcast(b, n, r);
+    bcast(b, n + 1, r * r);
+  };
+
+  for (int idx = threadIdx.x; idx < rows * n; idx += kCholThreads) {
+    const int q = idx / n, j = idx % n, i = rank + C * q;
+    if (j <= i) A[(size_t)q * n + j] = -0.5 * (m[(long long)i * ldm + j] + m[(long long)j * ldm + i]);
+    else l[(long long)i * n + j] = 0.0;
+  }
+  __syncthreads();
+  // column 0 and the first pivot
+  for (int q = w; q < rows; q += NW) {
+    if (lane != 0) continue;
+    const int i = rank + C * q;
+    const double v = A[(size_t)q * n];
+    bcast(0, i, v);
+    if (i == 0) pivot(0, v);
+  }
+  cluster.sync();
+
+  for (int k = 0; k < n; ++k) {
+    const double* cb = colbuf + (size_t)(k & 1) * (n + 2);
+    const int nb = (k + 1) & 1;
+    const double inv_sd = cb[n], inv_d = cb[n + 1];
+    for (int q = w; q < rows; q += NW) {
+      const int i = rank + C * q;
+      if (i < k) continue;
+      double* row = A + (size_t)q * n;
+      const double aik = row[k];
+      if (lane == 0) l[(long long)i * n + k] = aik * inv_sd;
+      if (i == k) continue;
+      const double s = aik * inv_d;
+      for (int j = k + 1 + lane; j <= i; j += 32) {
+        const double v = row[j] - s * cb[j];
+        row[j] = v;
+        if (j == k + 1) {  // column k+1 of the updated A, and the next pivot
+          bcast(nb, i, v);
+          if (i == k + 1) pivot(nb, v);
+        }
+      }
+    }
+    cluster.sync();
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // L^-1 by forward substitution, one block per column j; L's rows j..n-1 are staged in shared
 // memory when they fit.  Column j of L^-1 is row j of the transposed output linvt (compute
@@ -723,6 +803,17 @@ cudaError_t lmul(bool fp32, const void* tt, long long ldt, int m, int k, bool lo
 
 cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, double* work, int* err, int max_smem,
                              cudaStream_t st) {
+  if (n <= kCholMaxN) {
+    const size_t need = ((size_t)((n + kCholCluster - 1) / kCholCluster) * n + 2 * (n + 2)) * sizeof(double);
+    const size_t smem = std::max(need, kCholSmemOneCta);
+    if (smem + 1024 <= (size_t)max_smem) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_cholesky_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_cholesky_cluster<<<kCholCluster, kCholThreads, smem, st>>>(m, ldm, n, l, err);
+      return cudaGetLastError();
+    }
+  }
   const size_t padded = (size_t)n * (n + 1) * sizeof(double);
   if (padded + 64 <= (size_t)max_smem) {
     const cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)padded);
