@@ -8,6 +8,7 @@
   entry point itself;
 * accumulate, a non-positive-definite -M reported through the device error word, a short
   workspace rejected on the host;
+* the Cholesky factorisation on both sides of the cluster kernel's size limit (200, 256, 257);
 * the screen: s against the oracle, the kept-pair list identical (FP64) or identical away from
   the cut (FP32).
 
@@ -111,6 +112,27 @@ def test_build_and_apply_parity(precision, n_orb, n, seed):
     ex.ace_apply(P, dev(psi), out=out, accumulate=True)
     assert rel(out.cpu().numpy(), base + A.ace_apply(P0, psi, lat)) < 10 * tol
     ex.sync_status()
+    ex.close()
+
+
+@pytest.mark.parametrize("n_orb", [200, 256, 257])
+def test_cholesky_paths(n_orb):
+    # 200 and 256 orbitals: the cluster factorisation with one and two local rows per warp (256 is
+    # its largest size); 257: the single-block factorisation with A in global scratch
+    n, L = 12, 6.0
+    lat = np.diag([L, L, L])
+    N = n ** 3
+    q, _ = np.linalg.qr(np.random.default_rng(n_orb).standard_normal((N, n_orb)))
+    phi = (q.T * math.sqrt(N / L ** 3)).reshape(n_orb, n, n, n)
+    W = synthetic_action(phi, n_orb + 1)
+    M0, L0, P0 = A.ace_build(phi, W, lat)
+    ex = make_exchange(L, n, "fp64")
+    M, Lf, P = ex.ace_build(dev(phi), dev(W))
+    ex.sync_status()
+    assert rel(M.cpu().numpy(), M0) < TOL["fp64"]
+    assert rel(Lf.cpu().numpy(), L0) < 10 * TOL["fp64"]
+    assert np.all(np.triu(Lf.cpu().numpy(), 1) == 0)
+    assert rel(P.cpu().numpy(), P0) < 10 * TOL["fp64"]
     ex.close()
 
 
