@@ -85,6 +85,12 @@ __device__ __forceinline__ double sum_first_n(double v, int n, double* red) {
   return red[32];
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 }  // namespace
 
 // residual norms nu_p = |Psi^T[:, p]|^2 (in the compute type, widened), the FP32 copy of the
@@ -113,15 +119,19 @@ __global__ void __launch_bounds__(kUpdThreads) k_scdm_init(const double* __restr
 }
 
 // step j: pick p_j and form q_j (one block of kPickThreads threads; dynamic shared memory holds
-// a[n], h[n] and the per-warp partial sums hp[32][n], all in T).  The kernel is a chain of short
-// phases, so each phase issues all of its global loads before it uses any of them: the argmax
-// reads at most two per-block maxima per thread, and the Gram-Schmidt products read up to
-// kPickChunks x kPickRows entries of Q per lane at once.
+// a[n], h[n] and the per-warp partial sums hp[32][n], all in T, and with QS a copy of
+// q_0..q_{j-1} at the row stride of qt).  The kernel is a chain of short phases, so each phase
+// issues all of its global loads before it uses any of them: the argmax reads at most two
+// per-block maxima per thread, and the Gram-Schmidt products read up to kPickChunks x kPickRows
+// entries of Q per lane at once -- from shared memory when QS, where the copy of Q is started
+// before the argmax (Q does not depend on the pick) and lands while the argmax and the column
+// load wait on memory.
 constexpr int kPickThreads = 1024;
 constexpr int kPickChunks = 4;  // 32-column chunks of Q a lane holds in flight (128 columns)
 constexpr int kPickRows = 4;    // rows of Q a warp takes at once in a -= Q h
-template <typename T>
-__global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __restrict__ psi, long long N, int n, int j,
+constexpr size_t kPickSmemBudget = 200 * 1024;  // shared memory for the QS variant
+template <typename T, bool QS>
+__global__ void __launch_bounds__(kPickThreads, 1) k_scdm_pick(const double* __restrict__ psi, long long N, int n, int j,
                                                             const double* __restrict__ bmax,
                                                             const long long* __restrict__ bidx, int nb,
                                                             long long* __restrict__ piv, T* __restrict__ qt,
@@ -138,6 +148,18 @@ __global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __rest
   __shared__ long long pick;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   constexpr int nw = kPickThreads / 32;
+  // Q's rows (16-byte aligned: ldt is a multiple of 16 bytes), columns 0 .. j-1 rounded up to
+  // whole 16-byte pieces, which stay inside the row
+  T* qs = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(hp + 32 * n) + 15) & ~uintptr_t(15));
+  const T* Q = QS ? qs : qt;
+  if (QS && j > 0) {
+    constexpr int EPC = 16 / (int)sizeof(T);
+    const int cpr = (j + EPC - 1) / EPC;
+    for (int c = threadIdx.x; c < n * cpr; c += kPickThreads) {
+      const int i = c / cpr, kc = c - i * cpr;
+      cp_async16(qs + (long long)i * ldt + kc * EPC, qt + (long long)i * ldt + kc * EPC);
+    }
+  }
   {  // argmax over the per-block maxima (lowest index on a tie), the whole block
     double best = -2.0;
     long long bi = (long long)1 << 62;
@@ -157,8 +179,9 @@ __global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __rest
     a[threadIdx.x] = round_to<T>(psi[(long long)threadIdx.x * N + p]);
     sa = (double)a[threadIdx.x] * (double)a[threadIdx.x];
   }
+  if (QS) cp_async_wait_all();  // this thread's pieces of Q; the barriers below publish them
   const double an2 = sum_first_n(sa, n, red);
-  // two passes of classical Gram-Schmidt against q_0..q_{j-1} (qt[i][k] = q_k[i])
+  // two passes of classical Gram-Schmidt against q_0..q_{j-1} (Q[i][k] = q_k[i])
   for (int pass = 0; pass < 2; ++pass) {
     // h = Q^T a: warp w takes rows i = w, w + 32, ...; lane takes columns k = K0 + lane + 32 c
     for (int K0 = 0; K0 < j; K0 += 32 * kPickChunks) {
@@ -168,7 +191,7 @@ __global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __rest
 #pragma unroll 4
       for (int i = w; i < n; i += nw) {
         const T ai = a[i];
-        const T* row = qt + (long long)i * ldt;
+        const T* row = Q + (long long)i * ldt;
 #pragma unroll
         for (int c = 0; c < kPickChunks; ++c) {
           const int k = K0 + lane + 32 * c;
@@ -208,7 +231,7 @@ __global__ void __launch_bounds__(kPickThreads) k_scdm_pick(const double* __rest
 #pragma unroll
             for (int r = 0; r < kPickRows; ++r) {
               const int i = i0 + r * nw;
-              if (i < n) s[r] = fma(qt[(long long)i * ldt + k], hk, s[r]);
+              if (i < n) s[r] = fma(Q[(long long)i * ldt + k], hk, s[r]);
             }
           }
         }
@@ -308,14 +331,21 @@ static cudaError_t scdm_run(const double* psi, long long N, int n, T* a32, doubl
   k_scdm_init<T><<<nb, kUpdThreads, 0, st>>>(psi, N, n, a32, nu, bmax, bidx);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t pick_smem = 34 * (size_t)n * sizeof(T);
+  const size_t base_smem = 34 * (size_t)n * sizeof(T);
+  const size_t qs_smem = base_smem + 16 + (size_t)n * ldt * sizeof(T);
+  const bool qs = qs_smem <= kPickSmemBudget;
+  const size_t pick_smem = qs ? qs_smem : base_smem;
   if (pick_smem > 48 * 1024) {
-    e = cudaFuncSetAttribute(k_scdm_pick<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pick_smem);
+    e = qs ? cudaFuncSetAttribute(k_scdm_pick<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pick_smem)
+           : cudaFuncSetAttribute(k_scdm_pick<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pick_smem);
     if (e != cudaSuccess) return e;
   }
   const size_t upd_smem = (size_t)n * sizeof(T);
   for (int j = 0; j < n; ++j) {
-    k_scdm_pick<T><<<1, kPickThreads, pick_smem, st>>>(psi, N, n, j, bmax, bidx, nb, piv, qt, q64, ldt, rdiag, err);
+    if (qs)
+      k_scdm_pick<T, true><<<1, kPickThreads, pick_smem, st>>>(psi, N, n, j, bmax, bidx, nb, piv, qt, q64, ldt, rdiag, err);
+    else
+      k_scdm_pick<T, false><<<1, kPickThreads, pick_smem, st>>>(psi, N, n, j, bmax, bidx, nb, piv, qt, q64, ldt, rdiag, err);
     if (j + 1 < n) k_scdm_update<T><<<nb, kUpdThreads, upd_smem, st>>>(A, N, n, qt, ldt, j, piv, nu, bmax, bidx);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
