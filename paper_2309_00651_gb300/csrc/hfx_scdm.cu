@@ -28,6 +28,7 @@ namespace {
 
 constexpr int kUpdThreads = 256;
 constexpr int kUpdPoints = 4;  // grid points per thread per sweep (independent dot products)
+constexpr int kUpdBlocksPerSm = 3;  // resident update blocks per SM at its launch bounds
 
 template <typename T>
 __device__ __forceinline__ T round_to(double v);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kPickThreads, 1) k_scdm_pick(const double* __r
 // step j: c_p = q_j . Psi^T[:, p], nu_p -= c_p^2 (picked points stay at -1), per-block maxima;
 // each thread takes kUpdPoints grid points, rows unrolled for loads in flight
 template <typename T>
-__global__ void __launch_bounds__(kUpdThreads, 3) k_scdm_update(const T* __restrict__ A, long long N, int n,
+__global__ void __launch_bounds__(kUpdThreads, kUpdBlocksPerSm) k_scdm_update(const T* __restrict__ A, long long N, int n,
                                                              const T* __restrict__ qt, long long ldt, int j,
                                                              const long long* __restrict__ piv,
                                                              double* __restrict__ nu, double* __restrict__ bmax,
@@ -283,14 +284,18 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_scdm_update(const T* __restr
   const long long picked = piv[j];
   double best = -2.0;
   long long bi = (long long)1 << 62;
-  const long long stride = (long long)gridDim.x * kUpdThreads * kUpdPoints;
-  for (long long p0 = (long long)blockIdx.x * kUpdThreads * kUpdPoints + threadIdx.x; p0 < N; p0 += stride) {
+  // block b takes the contiguous run [b chunk, (b+1) chunk) of grid points (chunk a multiple of
+  // 32), in sweeps of kUpdThreads x kUpdPoints points: every block gets the same share
+  const long long chunk = ((N + gridDim.x - 1) / gridDim.x + 31) / 32 * 32;
+  const long long b0 = (long long)blockIdx.x * chunk;
+  const long long b1 = min(N, b0 + chunk);
+  for (long long p0 = b0 + threadIdx.x; p0 < b1; p0 += (long long)kUpdThreads * kUpdPoints) {
     T c[kUpdPoints];
     bool in[kUpdPoints];
 #pragma unroll
     for (int u = 0; u < kUpdPoints; ++u) {
       c[u] = T(0);
-      in[u] = p0 + u * kUpdThreads < N;
+      in[u] = p0 + u * kUpdThreads < b1;
     }
 #pragma unroll 8
     for (int i = 0; i < n; ++i) {
@@ -315,11 +320,12 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_scdm_update(const T* __restr
   if (threadIdx.x == 0) { bmax[blockIdx.x] = best; bidx[blockIdx.x] = bi; }
 }
 
-// blocks of the init / update launches: enough to cover the grid once with kUpdPoints per thread
-// (one wave at 3 blocks per SM for the 128 x 72^3 case), at most 8 per SM
+// blocks of the init / update launches: one wave of kUpdBlocksPerSm blocks on every SM (equal
+// shares of the grid, so no SM runs a block more than the others), fewer for small grids (at
+// least kUpdThreads points per block)
 static int scdm_blocks(long long N, int sm_count) {
-  const long long cover = (N + (long long)kUpdThreads * kUpdPoints - 1) / ((long long)kUpdThreads * kUpdPoints);
-  return (int)std::max(1LL, std::min<long long>(cover, (long long)sm_count * 8));
+  const long long cover = (N + kUpdThreads - 1) / kUpdThreads;
+  return (int)std::max(1LL, std::min<long long>(cover, (long long)sm_count * kUpdBlocksPerSm));
 }
 
 template <typename T>
