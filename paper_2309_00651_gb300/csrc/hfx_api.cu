@@ -309,7 +309,7 @@ static size_t smem_dense(const hfx_ctx* c) {
 }
 static size_t smem_plane_ct(int n) { return (size_t)(n * (n + 1) + stage_plan(n).twtotal) * sizeof(float2); }
 static size_t smem_dense_ct(int n, int b) {
-  const int zc = 8, ln = kDenseRowsCt * (b / 2) * zc, pts = n * zc;
+  const int zc = 8, ln = dense_rows_ct(n) * (b / 2) * zc, pts = n * zc;
   return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
 }
 static size_t smem_diag_ct(int n, int b) {

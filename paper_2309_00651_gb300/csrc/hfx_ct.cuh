@@ -337,13 +337,17 @@ template <typename T, int N> struct DenseGeo {
   static constexpr int ZC = ZChunk<T>::value;
   static constexpr int PTS = N * ZC;
   // points per thread: one up to 640 points (more warps hide the pass's load latency), else as
-  // few as keep the block within 320 threads
-  static constexpr int NP = PTS <= 640 ? 1 : (PTS + 319) / 320;
+  // few as keep the block within 512 threads
+  static constexpr int NP = PTS <= 640 ? 1 : (PTS + 511) / 512;
   static constexpr int NT = ((PTS + NP - 1) / NP + 31) / 32 * 32;   // threads
+  // orbital rows per iteration of the off-diagonal pass: two up to N = 72; one beyond, which
+  // halves the ring of couple tiles so that two blocks fit an SM at N = 96
+  static constexpr int RPI = dense_rows_ct(N);
+  static constexpr int MINB = N <= 96 ? 2 : 1;  // resident blocks per SM the passes are built for
 };
 
 template <typename T, int N, int B>
-__global__ void __launch_bounds__(DenseGeo<T, N>::NT, 2)
+__global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
                  const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                  const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
@@ -352,7 +356,7 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   using G = DenseGeo<T, N>;
   constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
   constexpr int HB = B / 2;
-  constexpr int RPI = kDenseRowsCt;  // orbital rows per iteration
+  constexpr int RPI = G::RPI;  // orbital rows per iteration
   constexpr int RING = kDenseRingCt;
   constexpr int LN = RPI * HB * ZC;  // lines of the interleaved tile [y][u][t][zz]
   constexpr int ITERS = B / RPI;

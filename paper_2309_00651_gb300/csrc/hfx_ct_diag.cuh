@@ -38,7 +38,7 @@ template <int B> struct DiagLayout {
 };
 
 template <typename T, int N, int B>
-__global__ void __launch_bounds__(DenseGeo<T, N>::NT, 2)
+__global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
                 const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                 const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,

@@ -548,9 +548,9 @@ __device__ __forceinline__ void cp_async_wait() {
 // ----------------------------------------------------------------------------------
 constexpr int kDenseMaxThreads = 512;
 constexpr int kDenseRing = 3;  // orbital rows of couple tiles in flight
-// compile-time dense pass: orbital rows transformed together per iteration, and its ring depth
-constexpr int kDenseRowsCt = 2;
+// compile-time dense pass: ring depth (its orbital rows per iteration are DenseGeo::RPI)
 constexpr int kDenseRingCt = 2;
+__host__ __device__ constexpr int dense_rows_ct(int n) { return n <= 72 ? 2 : 1; }
 template <int NP> struct DenseBounds;
 template <> struct DenseBounds<2> { static constexpr int threads = 320, blocks = 2; };
 template <> struct DenseBounds<4> { static constexpr int threads = 512, blocks = 1; };
