@@ -482,50 +482,6 @@ __global__ void __launch_bounds__(1024) k_cholesky(const double* __restrict__ m,
   if (tid == 0 && bad) atomicOr(err, kErrNotPosDef);
 }
 
-// The same factorisation with A in shared memory at row stride n + 1 (odd, so reading column k
-// across lanes hits distinct banks and needs no copy) and one barrier per step: the element
-// (k+1, k+1) is updated by thread 0, which then takes the next pivot's square root and
-// reciprocal into a double-buffered pair while the other threads finish the step.
-__global__ void __launch_bounds__(1024) k_cholesky_smem(const double* __restrict__ m, long long ldm, int n,
-                                                        double* __restrict__ l, int* err) {
-  extern __shared__ __align__(16) double sa[];  // [n][n + 1], lower triangle of A
-  __shared__ double piv[2][2];
-  __shared__ int bad;
-  const int ld = n + 1;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  const int nthr = blockDim.x * blockDim.y;
-  for (long long idx = tid; idx < (long long)n * n; idx += nthr) {
-    const int i = (int)(idx / n), j = (int)(idx % n);
-    if (j <= i) sa[(long long)i * ld + j] = -0.5 * (m[(long long)i * ldm + j] + m[(long long)j * ldm + i]);
-    else l[idx] = 0.0;
-  }
-  __syncthreads();
-  auto take_pivot = [&](int k) {  // thread 0 only
-    const double d = sa[(long long)k * ld + k];
-    if (!(d > 0.0)) bad = 1;
-    const double r = rsqrt(d);
-    piv[k & 1][0] = r;      // column scale 1/sqrt(d)
-    piv[k & 1][1] = r * r;  // update scale 1/d
-  };
-  if (tid == 0) {
-    bad = 0;
-    take_pivot(0);
-  }
-  __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const double inv_sd = piv[k & 1][0], inv_d = piv[k & 1][1];
-    for (int i = k + tid; i < n; i += nthr) l[(long long)i * n + k] = sa[(long long)i * ld + k] * inv_sd;
-    for (int i = k + 1 + threadIdx.y; i < n; i += blockDim.y) {
-      const double aik = sa[(long long)i * ld + k] * inv_d;
-      for (int j = k + 1 + threadIdx.x; j <= i; j += 32) sa[(long long)i * ld + j] -= aik * sa[(long long)j * ld + k];
-    }
-    // thread 0 (row k+1, column k+1 of the update) owns the next pivot
-    if (tid == 0 && k + 1 < n) take_pivot(k + 1);
-    __syncthreads();
-  }
-  if (tid == 0 && bad) atomicOr(err, kErrNotPosDef);
-}
-
 // The same factorisation spread over a cluster of kCholCluster CTAs, one per SM, so that the
 // trailing updates use the FP64 pipes of eight SMs.  CTA r keeps rows i = r + kCholCluster q of
 // the lower triangle in shared memory.  Step k reads column k of the updated A and the pivot's
@@ -813,13 +769,6 @@ cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, d
       k_cholesky_cluster<<<kCholCluster, kCholThreads, smem, st>>>(m, ldm, n, l, err);
       return cudaGetLastError();
     }
-  }
-  const size_t padded = (size_t)n * (n + 1) * sizeof(double);
-  if (padded + 64 <= (size_t)max_smem) {
-    const cudaError_t e = cudaFuncSetAttribute(k_cholesky_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)padded);
-    if (e != cudaSuccess) return e;
-    k_cholesky_smem<<<1, dim3(32, 32), padded, st>>>(m, ldm, n, l, err);
-    return cudaGetLastError();
   }
   const size_t need = ((size_t)n * n + n) * sizeof(double);
   const bool use_smem = need + 64 <= (size_t)max_smem;
