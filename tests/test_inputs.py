@@ -1,8 +1,5 @@
 """The synthetic input generator: orthonormality, pair-list shapes and the workload rules."""
-import math
-
 import numpy as np
-import pytest
 
 from paper_2309_00651_gb300 import inputs as I
 

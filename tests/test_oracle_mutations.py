@@ -10,7 +10,6 @@ without the isokinetic division by sdot.
 import math
 
 import numpy as np
-import pytest
 
 from oracle import ace_oracle as A
 from oracle import hfx_oracle as O
