@@ -153,13 +153,18 @@ hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, i
  * HFX_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that loads the library
  * holds until the process exits.  It allocates nothing (no cudaMalloc, cudaFree or allocating
  * library call) and never touches the context's own workspace.
- *   - Problems whose scratch would exceed HFX_NOALLOC_SCRATCH_BYTES are rejected with
- *     HFX_ERR_OOM before anything is enqueued (e.g. 16 orbitals on a 32^3 grid fit in both
- *     precisions; use hfx_apply with a workspace beyond that).
+ *   - The batches of one call run one after another on cuda_stream (no second stream), each sized
+ *     to the scratch left after the tables: problems whose default batches would not fit run in
+ *     more, smaller batches.  Problems in which one orbital-block pair's transforms, plus the
+ *     per-call tables, exceed HFX_NOALLOC_SCRATCH_BYTES are rejected with HFX_ERR_OOM before
+ *     anything is enqueued (e.g. 32 orbitals on a 32^3 grid fit in both precisions, 32 orbitals
+ *     on 72^3 do not; use hfx_apply with a workspace beyond that).
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
  *     with that device current; make that first call before any stream capture.
- *   - The schedule tables are copied from pageable host memory with cudaMemcpyAsync on
- *     cuda_stream.
+ *   - The schedule tables reach the array as the arguments of small kernels launched on
+ *     cuda_stream (no host-to-device copy, so no host buffer has to outlive the call).
+ *   - The context itself is only read: its workspace, streams and profiling settings are neither
+ *     used nor changed, so the caller's workspace keeps its contents.
  *   - Every call shares the one array, which keeps the previous call's contents (each call
  *     re-initialises what it needs).  Calls that overlap on the GPU -- on any stream, any
  *     context -- race on the array: serialise them. */

@@ -588,8 +588,10 @@ static Schedule make_host_schedule(const hfx_ctx* c, int n_orb) {
   return S;
 }
 
-static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long long n_pairs) {
-  (void)n_pairs;
+// two transform buffers when the batches of a call are pipelined on the context's two streams
+static bool two_buffers(const hfx_ctx* c, const Schedule& S) { return S.nbatches > 1 && c->side && c->pipeline; }
+
+static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, bool second_buffer) {
   Layout L;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
@@ -597,7 +599,7 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
   L.orb32 = take(orb32_bytes);
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   // a second transform buffer when batches are pipelined on two streams
-  L.W2 = take(S.nbatches > 1 && c->side && c->pipeline ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
+  L.W2 = take(second_buffer ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
   L.epart = take((size_t)S.max_total_couples * eparts(c) * sizeof(double));
   L.eblk = take((size_t)64 * sizeof(double));  // per-block energy sums (kEnergyBlocks)
   L.couples = take((size_t)S.max_total_couples * sizeof(int4));
@@ -608,7 +610,8 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, long lon
 extern "C" size_t hfx_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs) {
   if (!c || n_orb <= 0 || n_pairs < 0) return 0;
   Schedule S = make_host_schedule(c, n_orb);
-  return layout_of(c, S, n_orb, n_pairs).total;
+  (void)n_pairs;
+  return layout_of(c, S, n_orb, two_buffers(c, S)).total;
 }
 
 static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
@@ -727,12 +730,23 @@ __global__ void k_set_scalar(double* p, double v) { *p = v; }
 // ------------------------------------------------------------------------------------
 // apply
 // ------------------------------------------------------------------------------------
+// where one call's scratch lives and how its batches run: the workspace base, the second stream
+// for pipelined batches (NULL: every batch on the caller's stream) and whether per-pass events
+// are recorded
+struct CallEnv {
+  char* ws;
+  cudaStream_t side;
+  bool prof;
+};
+
 template <typename T>
-static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* orb, int n_orb, uint32_t flags,
-                             double* vxphi, cudaStream_t st) {
-  char* ws = (char*)c->ws;
+static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const CallEnv& env, const T* orb, int n_orb,
+                             uint32_t flags, double* vxphi, cudaStream_t st) {
+  char* ws = env.ws;
   using C = cx<T>;
-  const bool pipe = S.nbatches > 1 && c->side != nullptr && c->pipeline;
+  const bool pipe = S.nbatches > 1 && env.side != nullptr && c->pipeline;
+  auto mark = [&](cudaStream_t s) { return env.prof ? prof_mark(c, s) : nullptr; };
+  auto close = [&](int slot, cudaEvent_t e, cudaStream_t s) { if (env.prof) prof_close(c, slot, e, s); };
   C* Wbuf[2] = {(C*)(ws + L.W), (C*)(ws + (pipe ? L.W2 : L.W))};
   int4* couples = (int4*)(ws + L.couples);
   double* epart = (double*)(ws + L.epart);
@@ -746,7 +760,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
   const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
                                      (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
   // forward and x passes on `fs`, accumulate passes on the caller's stream `st`
-  cudaStream_t fs = pipe ? c->side : st;
+  cudaStream_t fs = pipe ? env.side : st;
   if (pipe) {
     HFX_CUDA_TRY(cudaEventRecord(c->ev_fork, st));
     HFX_CUDA_TRY(cudaStreamWaitEvent(fs, c->ev_fork, 0));
@@ -761,7 +775,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
     const CtFns* ct = std::is_same<T, float>::value ? c->ct : nullptr;
-    cudaEvent_t e0 = prof_mark(c, fs);
+    cudaEvent_t e0 = mark(fs);
     if (c->pencil) {
       const int nzc3 = g.n3 / zc, nrb = (g.n2 + c->rb - 1) / c->rb;
       const long long cap = (long long)c->sm_count * 16;
@@ -770,40 +784,40 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
       const int gx = (int)std::max<long long>(1, std::min<long long>((long long)(c1 - c0) * g.n2 * nzc3, cap));
       Passes<T>::fwd_z_rows(g, gr, smem_rows(c, c->rb), fs, orb, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
       Passes<T>::fwd_y_cols(g, gy, smem_cols(c, g.n2), fs, couples, c0, c1, W, (const C*)c->d_tw[1]);
-      prof_close(c, kProfFwd, e0, fs);
-      e0 = prof_mark(c, fs);
+      close(kProfFwd, e0, fs);
+      e0 = mark(fs);
       Passes<T>::x_cols(g, gx, smem_cols(c, g.n1), fs, couples, c0, c1, W, (const T*)c->d_vtab,
                         (const C*)c->d_tw[0], epart, energy_only ? 1 : 0);
       if (!energy_only)
         Passes<T>::inv_z_rows(g, gr, smem_rows(c, c->rb), fs, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
-      prof_close(c, kProfX, e0, fs);
+      close(kProfX, e0, fs);
     } else {
-    if (ct) {
-      const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
-      ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
-                 (const float2*)c->d_twct);
-    } else {
-      Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), fs, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
-                        (const C*)c->d_tw[2]);
-    }
-    prof_close(c, kProfFwd, e0, fs);
-    e0 = prof_mark(c, fs);
-    if (ct) {
-      const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
-      ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
-                    (const float2*)c->d_twct, epart, energy_only ? 1 : 0);
-    } else {
-      Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), fs, couples, c0, c1, W, (const T*)c->d_vtab,
-                           (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
-    }
-    prof_close(c, kProfX, e0, fs);
+      if (ct) {
+        const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
+        ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
+                   (const float2*)c->d_twct);
+      } else {
+        Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), fs, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
+                          (const C*)c->d_tw[2]);
+      }
+      close(kProfFwd, e0, fs);
+      e0 = mark(fs);
+      if (ct) {
+        const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
+        ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
+                      (const float2*)c->d_twct, epart, energy_only ? 1 : 0);
+      } else {
+        Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), fs, couples, c0, c1, W, (const T*)c->d_vtab,
+                             (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);
+      }
+      close(kProfX, e0, fs);
     }
     if (pipe) {
       HFX_CUDA_TRY(cudaEventRecord(c->ev_p2, fs));
       HFX_CUDA_TRY(cudaStreamWaitEvent(st, c->ev_p2, 0));
     }
     if (!energy_only) {
-      e0 = prof_mark(c, st);
+      e0 = mark(st);
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
       if (nd > 0 && ct && S.b == 8)  // [dense block pairs]
@@ -814,77 +828,84 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const T* 
         Passes<T>::y_acc_dense(g, dim3(nzc, g.n1, nd), dense_threads, smem_dense(c), st, S.b, orb, couples,
                                S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
                                (const C*)c->d_tw[1], vxphi, vscale);
-      if (nd > 0) prof_close(c, kProfAcc, e0, st);
+      if (nd > 0) close(kProfAcc, e0, st);
       const int ndg = S.diag_begin[b + 1] - S.diag_begin[b];
-      e0 = prof_mark(c, st);
+      e0 = mark(st);
       if (ndg > 0)  // [full diagonal block pairs]; the generic pass takes whatever is left
         ct->y_acc_diag(dim3(nzc, g.n1, ndg), smem_diag_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                        S.d_diag_slots + S.diag_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
                        (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
-      if (ndg > 0) prof_close(c, kProfAccGeneric, e0, st);
-      e0 = prof_mark(c, st);
+      if (ndg > 0) close(kProfAccGeneric, e0, st);
+      e0 = mark(st);
       if (ng > 0)
         Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
                                  S.d_generic_slots + S.generic_begin[b], S.d_slot_couple_base, S.d_slot_blocks, S.b,
                                  n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale, c->gen_grp, c->gen_phi,
                                  gen_cap_max(c));
-      if (ng > 0) prof_close(c, kProfAccGeneric, e0, st);
+      if (ng > 0) close(kProfAccGeneric, e0, st);
     }
     if (pipe) HFX_CUDA_TRY(cudaEventRecord(c->ev_p3[b & 1], st));
   }
   return HFX_OK;
 }
 
-static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
-                             uint32_t flags, double* ex_dev, double* vxphi, cudaStream_t st) {
+// argument checks shared by every exchange entry point (host-visible errors, nothing enqueued)
+static hfx_status check_apply_args(const hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
+                                   int64_t n_pairs, uint32_t flags, const double* ex_dev, const double* vxphi) {
   if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
   if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32)) return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
   if (n_orb <= 0) return fail(HFX_ERR_INVALID_ARG, "n_orb must be > 0");
   if (n_pairs < 0 || n_pairs > (int64_t)1 << 31) return fail(HFX_ERR_INVALID_ARG, "n_pairs out of range");
   if (!orbitals || !ex_dev) return fail(HFX_ERR_INVALID_ARG, "orbitals or ex_dev is NULL");
   if (n_pairs > 0 && !pairs) return fail(HFX_ERR_INVALID_ARG, "pairs is NULL");
-  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
-  if (!energy_only && !vxphi) return fail(HFX_ERR_INVALID_ARG, "vxphi is NULL without HFX_ENERGY_ONLY");
+  if (!(flags & HFX_ENERGY_ONLY) && !vxphi) return fail(HFX_ERR_INVALID_ARG, "vxphi is NULL without HFX_ENERGY_ONLY");
   if ((flags & HFX_ORBITALS_F32) && c->prec != HFX_PREC_FP32)
     return fail(HFX_ERR_INVALID_ARG, "HFX_ORBITALS_F32 needs HFX_PREC_FP32");
   if (((uintptr_t)orbitals | (uintptr_t)pairs | (uintptr_t)vxphi) % 16 || ((uintptr_t)ex_dev % 8))
     return fail(HFX_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
-  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
-  const size_t vbytes = (size_t)n_orb * c->N * sizeof(double);
-  if (n_pairs == 0) {
-    if (!accumulate) {
-      k_set_scalar<<<1, 1, 0, st>>>(ex_dev, 0.0);
-      if (!energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
-    }
-    HFX_CUDA_TRY(cudaGetLastError());
-    return HFX_OK;
+  return HFX_OK;
+}
+
+// an empty pair list: E_x = 0 and V_x phi = 0, or both left alone with HFX_ACCUMULATE
+static hfx_status apply_empty(const hfx_ctx* c, int32_t n_orb, uint32_t flags, double* ex_dev, double* vxphi,
+                              cudaStream_t st) {
+  if (!(flags & HFX_ACCUMULATE)) {
+    k_set_scalar<<<1, 1, 0, st>>>(ex_dev, 0.0);
+    if (!(flags & HFX_ENERGY_ONLY))
+      HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, (size_t)n_orb * c->N * sizeof(double), st));
   }
-  Schedule* S = nullptr;
-  hfx_status s = get_schedule(c, n_orb, &S);
-  if (s != HFX_OK) return s;
-  const Layout L = layout_of(c, *S, n_orb, n_pairs);
-  if (!c->ws || c->ws_bytes < L.total)
-    return fail(HFX_ERR_OOM, "workspace too small: have %zu bytes, need %zu (hfx_workspace_bytes)", c->ws_bytes, L.total);
-  char* ws = (char*)c->ws;
-  if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
+  HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
+}
+
+// one evaluation with its schedule tables on the device and its scratch at env.ws: stage a1
+// (V cleared, pairs placed, FP32 orbital copy), the passes of every batch, then the energy sum
+static hfx_status apply_with(hfx_ctx* c, Schedule& S, const Layout& L, const CallEnv& env, const void* orbitals,
+                             int32_t n_orb, const int32_t* pairs, int64_t n_pairs, uint32_t flags, double* ex_dev,
+                             double* vxphi, cudaStream_t st) {
+  char* ws = env.ws;
+  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
+  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
+  if (!accumulate && !energy_only)
+    HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, (size_t)n_orb * c->N * sizeof(double), st));
 
   // stage a1: pair list -> couples in the canonical layout
-  cudaEvent_t e_stage = prof_mark(c, st);
+  cudaEvent_t e_stage = env.prof ? prof_mark(c, st) : nullptr;
   int4* couples = (int4*)(ws + L.couples);
-  HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S->max_total_couples * sizeof(int4), st));
+  HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S.max_total_couples * sizeof(int4), st));
   {
     const int threads = 256;
     const int blocks = (int)std::max<long long>(1, std::min<long long>((n_pairs + threads - 1) / threads,
                                                                         (long long)c->sm_count * 8));
-    k_plan_place<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S->b, S->nb, S->d_slot_of_bp,
-                                             S->d_slot_couple_base, couples, c->d_err);
+    k_plan_place<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S.b, S.nb, S.d_slot_of_bp,
+                                             S.d_slot_couple_base, couples, c->d_err);
   }
   HFX_CUDA_TRY(cudaGetLastError());
 
   hfx_status rs;
   if (c->prec == HFX_PREC_FP64) {
-    prof_close(c, kProfStage, e_stage, st);
-    rs = run_passes<double>(c, *S, L, (const double*)orbitals, n_orb, flags, vxphi, st);
+    if (env.prof) prof_close(c, kProfStage, e_stage, st);
+    rs = run_passes<double>(c, S, L, env, (const double*)orbitals, n_orb, flags, vxphi, st);
   } else {
     const float* orb32;
     if (flags & HFX_ORBITALS_F32) {
@@ -896,17 +917,32 @@ static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
       k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
       orb32 = dst;
     }
-    prof_close(c, kProfStage, e_stage, st);
-    rs = run_passes<float>(c, *S, L, orb32, n_orb, flags, vxphi, st);
+    if (env.prof) prof_close(c, kProfStage, e_stage, st);
+    rs = run_passes<float>(c, S, L, env, orb32, n_orb, flags, vxphi, st);
   }
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
-  cudaEvent_t e_en = prof_mark(c, st);
-  launch_energy((const double*)(ws + L.epart), couples, (int)S->max_total_couples, eparts(c), (double*)(ws + L.eblk),
+  cudaEvent_t e_en = env.prof ? prof_mark(c, st) : nullptr;
+  launch_energy((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), (double*)(ws + L.eblk),
                 scale, accumulate, ex_dev, st);
-  prof_close(c, kProfEnergy, e_en, st);
+  if (env.prof) prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
+}
+
+static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
+                             uint32_t flags, double* ex_dev, double* vxphi, cudaStream_t st) {
+  hfx_status s = check_apply_args(c, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi);
+  if (s != HFX_OK) return s;
+  if (n_pairs == 0) return apply_empty(c, n_orb, flags, ex_dev, vxphi, st);
+  Schedule* S = nullptr;
+  s = get_schedule(c, n_orb, &S);
+  if (s != HFX_OK) return s;
+  const Layout L = layout_of(c, *S, n_orb, two_buffers(c, *S));
+  if (!c->ws || c->ws_bytes < L.total)
+    return fail(HFX_ERR_OOM, "workspace too small: have %zu bytes, need %zu (hfx_workspace_bytes)", c->ws_bytes, L.total);
+  const CallEnv env{(char*)c->ws, c->side, c->prof_on};
+  return apply_with(c, *S, L, env, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi, st);
 }
 
 extern "C" hfx_status hfx_apply(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
@@ -1062,49 +1098,43 @@ static hfx_status noalloc_scratch(void** out) {
   return HFX_OK;
 }
 
+// The schedule tables reach the scratch array as kernel arguments (8 KiB per launch): no host
+// buffer has to outlive the call and no pageable-memory copy is involved.
+constexpr int kTableWords = 2048;
+struct TableChunk { uint32_t w[kTableWords]; };
+__global__ void k_put_words(uint32_t* __restrict__ dst, TableChunk chunk, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = chunk.w[i];
+}
+static hfx_status put_table(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const uint32_t* s = (const uint32_t*)src;
+  size_t words = bytes / 4;
+  uint32_t* d = (uint32_t*)dst;
+  while (words > 0) {
+    const int n = (int)std::min<size_t>(words, kTableWords);
+    TableChunk ch;
+    std::memcpy(ch.w, s, (size_t)n * 4);
+    k_put_words<<<1, 256, 0, st>>>(d, ch, n);
+    HFX_CUDA_TRY(cudaGetLastError());
+    s += n;
+    d += n;
+    words -= (size_t)n;
+  }
+  return HFX_OK;
+}
+
 extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
                                         int64_t n_pairs, uint32_t flags, double* ex_dev, double* vxphi,
                                         void* cuda_stream) {
   g_last_error.clear();
-  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
-  if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32)) return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
-  if (n_orb <= 0) return fail(HFX_ERR_INVALID_ARG, "n_orb must be > 0");
-  if (n_pairs < 0 || n_pairs > (int64_t)1 << 31) return fail(HFX_ERR_INVALID_ARG, "n_pairs out of range");
-  if (!orbitals || !ex_dev) return fail(HFX_ERR_INVALID_ARG, "orbitals or ex_dev is NULL");
-  if (n_pairs > 0 && !pairs) return fail(HFX_ERR_INVALID_ARG, "pairs is NULL");
-  const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
-  if (!energy_only && !vxphi) return fail(HFX_ERR_INVALID_ARG, "vxphi is NULL without HFX_ENERGY_ONLY");
-  if ((flags & HFX_ORBITALS_F32) && c->prec != HFX_PREC_FP32)
-    return fail(HFX_ERR_INVALID_ARG, "HFX_ORBITALS_F32 needs HFX_PREC_FP32");
-  if (((uintptr_t)orbitals | (uintptr_t)pairs | (uintptr_t)vxphi) % 16 || ((uintptr_t)ex_dev % 8))
-    return fail(HFX_ERR_INVALID_ARG, "device pointers must be 16-byte aligned");
+  hfx_status s = check_apply_args(c, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi);
+  if (s != HFX_OK) return s;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
-  const size_t vbytes = (size_t)n_orb * c->N * sizeof(double);
-  if (n_pairs == 0) {
-    if (!accumulate) {
-      k_set_scalar<<<1, 1, 0, st>>>(ex_dev, 0.0);
-      if (!energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
-    }
-    HFX_CUDA_TRY(cudaGetLastError());
-    return HFX_OK;
-  }
+  if (n_pairs == 0) return apply_empty(c, n_orb, flags, ex_dev, vxphi, st);
 
-  // the passes read the context's workspace and side stream: for this call the workspace is the
-  // scratch array and the batches run on the caller's stream alone (one transform buffer), with
-  // event timing off (it would create events); calls on one context never overlap
-  struct Restore {
-    hfx_ctx* c;
-    void* ws;
-    size_t bytes;
-    bool prof;
-    cudaStream_t side;
-    ~Restore() { c->ws = ws; c->ws_bytes = bytes; c->prof_on = prof; c->side = side; }
-  } restore{c, c->ws, c->ws_bytes, c->prof_on, c->side};
-  c->side = nullptr;
-  c->prof_on = false;
-
-  // host schedule; its device tables go to the head of the scratch array, the workspace after them
+  // host schedule; its device tables go to the head of the scratch array, the workspace after
+  // them.  The batches run on the caller's stream alone (one transform buffer), sized to the
+  // space left: the schedule is rebuilt with that transform budget when the default one does
+  // not fit, and the call is refused only when a single block pair's transforms do not.
   Schedule S = make_host_schedule(c, n_orb);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align256(std::max<size_t>(bytes, 16)); return o; };
@@ -1114,69 +1144,47 @@ extern "C" hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_
   const size_t o_dense = take(S.dense_slots.size() * sizeof(int));
   const size_t o_gen = take(S.generic_slots.size() * sizeof(int));
   const size_t o_diag = take(S.diag_slots.size() * sizeof(int));
-  const Layout L = layout_of(c, S, n_orb, n_pairs);
+  const size_t couple_bytes = (size_t)c->N * cplx_size(c);
+  Layout L = layout_of(c, S, n_orb, false);
+  if (off + L.total > kNoallocScratchBytes) {
+    const size_t w_now = align256((size_t)S.max_batch_couples * couple_bytes);
+    const size_t fixed = off + L.total - w_now;  // everything but the transform buffer
+    int cap_max = 1;
+    for (int k : S.slot_cap) cap_max = std::max(cap_max, k);
+    const size_t room = fixed < kNoallocScratchBytes ? kNoallocScratchBytes - fixed : 0;
+    if (room >= (size_t)cap_max * couple_bytes + 256) {
+      build_schedule(S, n_orb, c->bsize, room - 256, couple_bytes, dense_available(c), diag_available(c));
+      L = layout_of(c, S, n_orb, false);
+    }
+  }
   if (off + L.total > kNoallocScratchBytes)
     return fail(HFX_ERR_OOM,
                 "problem needs %zu bytes of scratch; the allocation-free entry point holds %zu (use hfx_apply with a "
                 "caller-owned workspace)",
                 off + L.total, kNoallocScratchBytes);
   void* scratch = nullptr;
-  hfx_status s0 = noalloc_scratch(&scratch);
-  if (s0 != HFX_OK) return s0;
+  s = noalloc_scratch(&scratch);
+  if (s != HFX_OK) return s;
   char* base = (char*)scratch;
-  auto put = [&](size_t o, const void* src, size_t bytes) -> cudaError_t {
-    return bytes ? cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
-  };
-  HFX_CUDA_TRY(put(o_blocks, S.slot_blocks.data(), S.slot_blocks.size() * sizeof(int2)));
-  HFX_CUDA_TRY(put(o_of_bp, S.slot_of_bp.data(), S.slot_of_bp.size() * sizeof(int)));
-  HFX_CUDA_TRY(put(o_base, S.slot_couple_base.data(), S.slot_couple_base.size() * sizeof(int)));
-  HFX_CUDA_TRY(put(o_dense, S.dense_slots.data(), S.dense_slots.size() * sizeof(int)));
-  HFX_CUDA_TRY(put(o_gen, S.generic_slots.data(), S.generic_slots.size() * sizeof(int)));
-  HFX_CUDA_TRY(put(o_diag, S.diag_slots.data(), S.diag_slots.size() * sizeof(int)));
+  const struct { size_t off; const void* src; size_t bytes; } tables[] = {
+      {o_blocks, S.slot_blocks.data(), S.slot_blocks.size() * sizeof(int2)},
+      {o_of_bp, S.slot_of_bp.data(), S.slot_of_bp.size() * sizeof(int)},
+      {o_base, S.slot_couple_base.data(), S.slot_couple_base.size() * sizeof(int)},
+      {o_dense, S.dense_slots.data(), S.dense_slots.size() * sizeof(int)},
+      {o_gen, S.generic_slots.data(), S.generic_slots.size() * sizeof(int)},
+      {o_diag, S.diag_slots.data(), S.diag_slots.size() * sizeof(int)}};
+  for (const auto& t : tables) {
+    s = put_table(base + t.off, t.src, t.bytes, st);
+    if (s != HFX_OK) return s;
+  }
   S.d_slot_blocks = (int2*)(base + o_blocks);
   S.d_slot_of_bp = (int*)(base + o_of_bp);
   S.d_slot_couple_base = (int*)(base + o_base);
   S.d_dense_slots = (int*)(base + o_dense);
   S.d_generic_slots = (int*)(base + o_gen);
   S.d_diag_slots = (int*)(base + o_diag);
-
-  c->ws = base + off;
-  c->ws_bytes = kNoallocScratchBytes - off;
-  char* ws = (char*)c->ws;
-
-  if (!accumulate && !energy_only) HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, vbytes, st));
-  int4* couples = (int4*)(ws + L.couples);
-  HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S.max_total_couples * sizeof(int4), st));
-  {
-    const int threads = 256;
-    const int blocks = (int)std::max<long long>(1, std::min<long long>((n_pairs + threads - 1) / threads,
-                                                                        (long long)c->sm_count * 8));
-    k_plan_place<<<blocks, threads, 0, st>>>((const int2*)pairs, n_pairs, n_orb, S.b, S.nb, S.d_slot_of_bp,
-                                             S.d_slot_couple_base, couples, c->d_err);
-  }
-  HFX_CUDA_TRY(cudaGetLastError());
-  hfx_status rs;
-  if (c->prec == HFX_PREC_FP64) {
-    rs = run_passes<double>(c, S, L, (const double*)orbitals, n_orb, flags, vxphi, st);
-  } else {
-    const float* orb32;
-    if (flags & HFX_ORBITALS_F32) {
-      orb32 = (const float*)orbitals;
-    } else {
-      float* dst = (float*)(ws + L.orb32);
-      const long long n = (long long)n_orb * c->N;
-      const int blocks = (int)std::min<long long>((n / 2 + 255) / 256 + 1, (long long)c->sm_count * 16);
-      k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
-      orb32 = dst;
-    }
-    rs = run_passes<float>(c, S, L, orb32, n_orb, flags, vxphi, st);
-  }
-  if (rs != HFX_OK) return rs;
-  const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
-  launch_energy((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), (double*)(ws + L.eblk),
-                scale, accumulate, ex_dev, st);
-  HFX_CUDA_TRY(cudaGetLastError());
-  return HFX_OK;
+  const CallEnv env{base + off, nullptr, false};
+  return apply_with(c, S, L, env, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi, st);
 }
 
 extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_bytes, int32_t pipeline) {

@@ -4,7 +4,10 @@ update entry points (include/hfx_sinr.h); forces come from caller-supplied calla
 One outer step of length n_MTS dt applies n_MTS inner factors, each
     A(dt/2)  B(dt/2; F_fast)  C(dt)  B(dt/2; F_fast at the new X)  A(dt/2),
 with the slow kick n_MTS F_slow added to the first B of the first inner factor and to the last B
-of the last one.  Every arithmetic step runs in the CUDA library; this module only orders calls.
+of the last one.  The updates A, B and C run in the CUDA library; this module orders the calls.
+Two things here are plain torch work on the caller's tensors rather than library kernels: the
+slow kick's scaling n_MTS F_slow (one multiply per element, passed to update B as its extra
+force) and constraint(), the diagnostic sum M V^2 + L/(L+1) Q1 sum v1^2 of eq. kecons.
 """
 from __future__ import annotations
 
@@ -21,6 +24,7 @@ class SinR:
         self.n_res, self.n_sy = int(n_res), int(n_sy)
 
     def constraint(self, mass: torch.Tensor, V: torch.Tensor, v1: torch.Tensor) -> torch.Tensor:
+        """Isokinetic constraint value per degree of freedom (eq. kecons), a diagnostic in torch."""
         L = self.params.L
         return mass * V * V + (L / (L + 1.0)) * self.params.Q1 * torch.sum(v1 * v1, dim=-1)
 

@@ -31,6 +31,17 @@ def rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
 
 
+def maxrel(a, b):
+    """max |a - b| / max |b|: a localised error (one plane, one ragged chunk) is not diluted by the
+    grid size the way it is in a Frobenius norm."""
+    return float(np.max(np.abs(np.ravel(a - b))) / max(np.max(np.abs(np.ravel(b))), 1e-300))
+
+
+def assert_v_close(V, V_ref, tol):
+    assert rel(V, V_ref) <= tol
+    assert maxrel(V, V_ref) <= tol
+
+
 def run_gpu(phi, pairs, lattice, prec, **kw):
     from paper_2309_00651_gb300 import hfx
     ex = hfx.Exchange(lattice, phi.shape[1:], alpha=kw.pop("alpha", 0.25), precision=prec,
@@ -61,6 +72,7 @@ def test_real_plane_wave_closed_form(prec):
     assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
     for b in range(len(phi)):
         assert rel(V[b], eps[b // 2] * phi[b]) <= 10 * TOL[prec]
+        assert maxrel(V[b], eps[b // 2] * phi[b]) <= 10 * TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -74,7 +86,7 @@ def test_small_grids_all_pairs(prec, n, n_orb):
     E_ref, V_ref = O.exchange(phi, pairs, lat)
     E, V = run_gpu(phi, pairs, lat, prec)
     assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-    assert rel(V, V_ref) <= TOL[prec]
+    assert_v_close(V, V_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -89,7 +101,7 @@ def test_orthorhombic_non_cubic_grid(prec):
     E_ref, V_ref = O.exchange(phi, pairs, lat)
     E, V = run_gpu(phi, pairs, lat, prec)
     assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-    assert rel(V, V_ref) <= TOL[prec]
+    assert_v_close(V, V_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -100,7 +112,7 @@ def test_pw16_n32_full(prec):
     E_ref, V_ref = O.exchange(phi, pairs, w.lattice)
     E, V = run_gpu(phi, pairs, w.lattice, prec)
     assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-    assert rel(V, V_ref) <= TOL[prec]
+    assert_v_close(V, V_ref, TOL[prec])
     # per-orbital norm-wise error as well
     worst = max(rel(V[i], V_ref[i]) for i in range(len(V)))
     assert worst <= 10 * TOL[prec]
@@ -117,7 +129,7 @@ def test_shuffled_subset_with_diagonals_and_accumulate(prec):
     E_ref, V_ref = O.exchange(phi, sub, lat)
     E, V = run_gpu(phi, sub, lat, prec)
     assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-    assert rel(V, V_ref) <= TOL[prec]
+    assert_v_close(V, V_ref, TOL[prec])
     # linearity: two halves with HFX_ACCUMULATE equal the whole list
     from paper_2309_00651_gb300 import hfx
     ex = hfx.Exchange(lat, (n, n, n), precision=prec)
@@ -127,7 +139,7 @@ def test_shuffled_subset_with_diagonals_and_accumulate(prec):
     E1, V1 = ex.apply(phi_d, h1)
     E2, V2 = ex.apply(phi_d, h2, accumulate=True, ex=E1, vxphi=V1)
     assert abs(E2.item() - E_ref) <= TOL[prec] * abs(E_ref)
-    assert rel(V2.cpu().numpy(), V_ref) <= TOL[prec]
+    assert_v_close(V2.cpu().numpy(), V_ref, TOL[prec])
     # energy only
     Ee, Ve = ex.apply(phi_d, torch.from_numpy(sub).cuda(), energy_only=True)
     assert Ve is None and abs(Ee.item() - E_ref) <= TOL[prec] * abs(E_ref)
@@ -181,7 +193,7 @@ def test_duplicate_pairs_are_reported_and_counted_once():
         ex.sync_status()
     assert ei.value.status == -5
     assert abs(E.item() - E_ref) <= 1e-8 * abs(E_ref)
-    assert rel(V.cpu().numpy(), V_ref) <= 1e-8
+    assert_v_close(V.cpu().numpy(), V_ref, 1e-8)
     ex.close()
 
 
@@ -197,7 +209,7 @@ def test_orbital_block_sizes(block, monkeypatch):
     for prec in ("fp64", "fp32"):
         E, V = run_gpu(phi, pairs, lat, prec)
         assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-        assert rel(V, V_ref) <= TOL[prec]
+        assert_v_close(V, V_ref, TOL[prec])
 
 
 def test_large_tile_sparse_block_pair():
@@ -213,7 +225,7 @@ def test_large_tile_sparse_block_pair():
     for prec in ("fp64", "fp32"):
         E, V = run_gpu(phi, pairs, lat, prec)
         assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-        assert rel(V, V_ref) <= TOL[prec]
+        assert_v_close(V, V_ref, TOL[prec])
 
 
 @pytest.mark.parametrize("n", [48, 64])
@@ -229,7 +241,7 @@ def test_compile_time_and_runtime_kernels(n, no_ct, monkeypatch):
     E_ref, V_ref = O.exchange(phi, pairs, lat)
     E, V = run_gpu(phi, pairs, lat, "fp32")
     assert abs(E - E_ref) <= 1e-6 * abs(E_ref)
-    assert rel(V, V_ref) <= 1e-6
+    assert_v_close(V, V_ref, 1e-6)
 
 
 def test_cuda_graph_capture_and_replay():
@@ -275,7 +287,7 @@ def test_pencil_form(prec, monkeypatch):
         E_ref, V_ref = O.exchange(phi, pairs, lat)
         E, V = run_gpu(phi, pairs, lat, prec)
         assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
-        assert rel(V, V_ref) <= TOL[prec]
+        assert_v_close(V, V_ref, TOL[prec])
         Ee, _ = run_gpu(phi, pairs, lat, prec, energy_only=True)
         assert abs(Ee - E_ref) <= TOL[prec] * abs(E_ref)
 
@@ -289,7 +301,7 @@ def test_fp64_on_128_grid_uses_pencils_and_matches_oracle():
     E_ref, V_ref = O.exchange(phi, pairs, lat)
     E, V = run_gpu(phi, pairs, lat, "fp64")
     assert abs(E - E_ref) <= 1e-8 * abs(E_ref)
-    assert rel(V, V_ref) <= 1e-8
+    assert_v_close(V, V_ref, 1e-8)
 
 
 def test_bad_pairs_are_reported_and_skipped():
@@ -306,7 +318,7 @@ def test_bad_pairs_are_reported_and_skipped():
         ex.sync_status()
     assert ei.value.status == -5
     assert abs(E.item() - E_ref) <= 1e-8 * abs(E_ref)
-    assert rel(V.cpu().numpy(), V_ref) <= 1e-8
+    assert_v_close(V.cpu().numpy(), V_ref, 1e-8)
     ex.sync_status()  # cleared
     ex.close()
 
@@ -319,7 +331,7 @@ def test_sphere_kernel_matches_oracle():
     E_ref, V_ref = O.exchange(phi, pairs, lat, sphere_ecut=ecut)
     E, V = run_gpu(phi, pairs, lat, "fp64", kernel="coulomb_sphere", ecut=ecut)
     assert abs(E - E_ref) <= 1e-8 * abs(E_ref)
-    assert rel(V, V_ref) <= 1e-8
+    assert_v_close(V, V_ref, 1e-8)
 
 
 def test_compile_time_passes_with_sparse_pair_list():
@@ -333,4 +345,4 @@ def test_compile_time_passes_with_sparse_pair_list():
     E_ref, V_ref = O.exchange(phi, sub, w.lattice)
     E, V = run_gpu(phi, sub, w.lattice, "fp32")
     assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
-    assert rel(V, V_ref) <= TOL["fp32"]
+    assert_v_close(V, V_ref, TOL["fp32"])

@@ -317,3 +317,80 @@ def test_planted_mistakes_are_caught(monkeypatch):
         with monkeypatch.context() as m:
             plant(m)
             assert not pin_holds(), f"mutant {name!r} not caught"
+
+
+# ----------------------------------------------------------------------------- sampled rows
+
+def _rows_case():
+    """7 orbitals on a 10^3 grid with a partial pair list: orbital 6 appears in no pair, rows 1
+    and 4 appear as the first and as the second member of off-diagonal pairs and with their own
+    diagonal pair."""
+    L, n = 7.0, 10
+    lat = np.diag([L] * 3)
+    phi = small_orbitals(7, n, L, seed=21)
+    allp = I.all_pairs(7)
+    keep = np.random.default_rng(22).random(len(allp)) < 0.6
+    sub = allp[keep & (allp[:, 0] != 6) & (allp[:, 1] != 6)]
+    for must in ([1, 1], [4, 4], [0, 1], [1, 5], [2, 4], [4, 5]):
+        if not any((sub[:, 0] == must[0]) & (sub[:, 1] == must[1])):
+            sub = np.concatenate([sub, np.array([must], dtype=np.int32)])
+    return phi, sub, lat
+
+
+def test_exchange_rows_matches_full_exchange():
+    """exchange_rows (the checker of every full-size parity row) equals the rows of the full
+    V_x phi over the same partial list, including diagonal pairs, both pair positions and a row
+    that no pair contains (exactly zero)."""
+    phi, sub, lat = _rows_case()
+    _, V = O.exchange(phi, sub, lat)
+    rows = [1, 4, 6, 0, 5]
+    R = O.exchange_rows(phi, sub, rows, lat)
+    for r, k in enumerate(rows):
+        if k == 6:
+            assert np.all(R[r] == 0.0)
+        else:
+            assert rel(R[r], V[k]) < 1e-13
+    # reversing the pair list (order inside the sums only) changes nothing beyond rounding
+    R2 = O.exchange_rows(phi, sub[::-1].copy(), rows, lat)
+    assert rel(R2, R) < 1e-13
+
+
+def test_exchange_rows_closed_form_real():
+    """Rows of the real plane-wave closed form: every orbital of the k pair gets eps_k phi."""
+    L, n = 8.5, 12
+    lat = np.diag([L] * 3)
+    kset = np.array([[1, 0, 0], [0, 2, 1], [1, -1, 2]])
+    phi = I.real_plane_wave_orbitals(kset, L, n)
+    _, eps = O.closed_form_real(kset, lat)
+    rows = [0, 3, 5]
+    R = O.exchange_rows(phi, I.all_pairs(len(phi)), rows, lat)
+    for r, b in enumerate(rows):
+        assert rel(R[r], eps[b // 2] * phi[b]) < 1e-12
+
+
+def test_exchange_rows_planted_slips_are_caught():
+    """Plausible slips in a rows checker (the partner index taken as the row itself, diagonal
+    pairs skipped, off-diagonal pairs counted only where the row is the first member) written
+    out here as variants: each one disagrees with the full exchange that the real one matches."""
+    phi, sub, lat = _rows_case()
+    _, V = O.exchange(phi, sub, lat)
+    v = O.coulomb_kernel(lat, phi.shape[1:])
+
+    def variant(k, slip):
+        out = np.zeros(phi.shape[1:])
+        for i, j in sub:
+            if i != k and j != k:
+                continue
+            if slip == "first_only" and i != k:
+                continue
+            if slip == "no_diag" and i == j:
+                continue
+            other = k if slip == "self" else (j if i == k else i)
+            out -= 0.25 * O.pair_potential(O.pair_transform(phi[i], phi[j]), v) * phi[other]
+        return out
+
+    for k in (1, 4):
+        assert rel(variant(k, "none"), V[k]) < 1e-13
+        for slip in ("self", "no_diag", "first_only"):
+            assert rel(variant(k, slip), V[k]) > 1e-3, (k, slip)
+    assert rel(O.exchange_rows(phi, sub, [4], lat)[0], V[4]) < 1e-13
