@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-ace", action="store_true", help="skip the ACE / screen rows")
+    ap.add_argument("--no-extra", action="store_true", help="skip the 96^3 (256-orbital) sub-measurement")
+    ap.add_argument("--with-128", action="store_true",
+                    help="also measure the 512-orbital 128^3 screened workload (minutes of input generation)")
     ap.add_argument("--rows-only", action="store_true",
                     help="one exchange call, then the ACE / screen / SCDM / SIN(R) rows with 2 repetitions each; "
                          "prints their JSON (a short run to profile those kernels)")
@@ -143,6 +146,63 @@ def oracle_rate(phi, pairs, lattice, n_sample, seed=0):
     E, V = O.exchange(phi, sub, lattice, alpha=0.25)
     dt = time.perf_counter() - t0
     return len(sub) / dt, dt, sub, E, V
+
+
+def _oracle_chunk(task):
+    """Worker of the all-cores oracle leg: the oracle, as it stands, over one chunk of the pair
+    sample, on orbitals shared through a named shared-memory block."""
+    from multiprocessing import shared_memory
+
+    import numpy as np
+    from oracle import hfx_oracle as O
+    name, shape, lattice, chunk = task
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        phi = np.ndarray(shape, dtype=np.float64, buffer=shm.buf)
+        t0 = time.perf_counter()
+        E, V = O.exchange(phi, chunk, lattice, alpha=0.25)
+        dt = time.perf_counter() - t0
+        return E, dt
+    finally:
+        shm.close()
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core (started with spawn, so it is
+    safe after CUDA initialisation), the orbitals shared read-only through shared memory, each
+    process evaluating its own slice of a pair sample."""
+
+    def __init__(self, phi, lattice, procs=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        import numpy as np
+        self.procs = procs or len(os.sched_getaffinity(0))
+        self.shm = shared_memory.SharedMemory(create=True, size=phi.nbytes)
+        buf = np.ndarray(phi.shape, dtype=np.float64, buffer=self.shm.buf)
+        buf[...] = phi
+        self.shape = phi.shape
+        self.lattice = np.asarray(lattice, dtype=np.float64)
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        # first use in every process (imports, FFT plans) outside any timed region
+        self.pool.map(_oracle_chunk, [(self.shm.name, self.shape, self.lattice, np.zeros((1, 2), np.int32))] * self.procs)
+
+    def rate(self, pairs, n_sample, seed):
+        """pairs/s of the whole pool over a seeded sample (wall clock), and its E_x."""
+        import numpy as np
+        from paper_2309_00651_gb300 import inputs as I
+        sub = I.random_pairs_subset(pairs, n_sample, seed)
+        chunks = [c for c in np.array_split(sub, self.procs) if len(c)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_chunk, [(self.shm.name, self.shape, self.lattice, c) for c in chunks], chunksize=1)
+        dt = time.perf_counter() - t0
+        return len(sub) / dt, dt, sum(r[0] for r in res)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
 
 
 FP32_FFMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop x max SM clock
@@ -268,35 +328,145 @@ def sinr_rows(hfx, n_dof=3 * 1048576, L=4, reps=20):
 
 
 def run_reference(args):
+    """The oracle as it stands on every host core (one process per core), on bounded samples of
+    the same workload; the GPU path's metric, unit and config."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np
     from paper_2309_00651_gb300 import inputs as I
     w = I.WORKLOADS[args.workload]
     phi, pairs, info = I.make_workload(w)
-    # calibrate the per-pair cost, then size each step so the whole run stays within ~3 minutes
-    rate, dt, _, _, _ = oracle_rate(phi, pairs, w.lattice, 4, seed=123)
-    per_step = max(2, int(150.0 / max(1, args.steps + args.warmup) * rate))
-    per_step = min(per_step, len(pairs))
-    for k in range(args.warmup):
-        oracle_rate(phi, pairs, w.lattice, per_step, seed=1000 + k)
-    total_pairs, total_t = 0, 0.0
-    for k in range(args.steps):
-        _, dt, sub, _, _ = oracle_rate(phi, pairs, w.lattice, per_step, seed=k)
-        total_pairs += len(sub)
-        total_t += dt
+    pool = OraclePool(phi, w.lattice)
+    try:
+        # calibrate the per-pair cost, then size each step so the whole run stays within ~3 minutes
+        rate, _, _ = pool.rate(pairs, 2 * pool.procs, seed=123)
+        per_step = max(pool.procs, int(150.0 / max(1, args.steps + args.warmup) * rate))
+        per_step = min(per_step, len(pairs))
+        for k in range(args.warmup):
+            pool.rate(pairs, per_step, seed=1000 + k)
+        total_pairs, total_t = 0, 0.0
+        for k in range(args.steps):
+            r, dt, _ = pool.rate(pairs, per_step, seed=k)
+            total_pairs += per_step
+            total_t += dt
+    finally:
+        pool.close()
     value = total_pairs / total_t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_desc(w, len(pairs)),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{per_step} seeded random pairs of the {len(pairs)}-pair list per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+                         "sample": f"{per_step} seeded random pairs of the {len(pairs)}-pair list per step, split "
+                                   f"over {pool.procs} processes (numpy FP64, one per host core)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+PASS_KEYS = ("fwd_yz", "x_coulomb", "y_acc_dense", "y_acc_generic")
+
+
+def pass_rooflines(prof, steps, stats, N, csize, P, ms_step, peak):
+    """Per pass: algorithmic bytes per step (per couple: forward pass writes the packed transform,
+    8 N B in FP32; the x pass reads and writes it; the accumulate passes read it), device time per
+    step from the library's per-launch CUDA events, and the fraction of the measured HBM peak;
+    plus the whole call at 16 N B per pair (FP32; 32 N B in FP64)."""
+    per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_acc_dense": csize * N,
+                  "y_acc_generic": csize * N}
+    couples_of = {"fwd_yz": stats["couples"], "x_coulomb": stats["couples"],
+                  "y_acc_dense": stats["dense_couples"], "y_acc_generic": stats["couples"] - stats["dense_couples"]}
+    out = {}
+    for k in PASS_KEYS:
+        ms = prof[k]["ms"] / steps
+        if ms <= 0:
+            continue
+        b = per_couple[k] * couples_of[k]
+        out[k] = {"ms_per_step": ms, "alg_bytes_per_step": b, "achieved_gbs": b / (ms / 1e3) / 1e9,
+                  "frac": b / (ms / 1e3) / 1e9 / peak}
+    whole = 2 * csize * N * P
+    out["whole_call"] = {"ms_per_step": ms_step, "alg_bytes_per_step": whole,
+                         "achieved_gbs": whole / (ms_step / 1e3) / 1e9, "frac": whole / (ms_step / 1e3) / 1e9 / peak}
+    return out
+
+
+def graph_steps(step, stream, steps, barrier):
+    """Capture one step in a CUDA graph and time `steps` replays: CUDA events around the whole
+    region (the contract's timing) and around each replay (for the median)."""
+    import torch
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):  # captured on torch's own side stream, replayed on `stream`
+        step()
+    g.replay()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    barrier()
+    evs[0].record(stream)
+    for k in range(steps):
+        g.replay()
+        evs[k + 1].record(stream)
+    barrier()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+    return evs[0].elapsed_time(evs[-1]), per, g
+
+
+def measure_workload(name, precision, hfx, I, O, dev, reps=3, n_check=12):
+    """A further workload of the scope table at full size: ms per call (median of `reps` replays
+    of a captured call), pairs/s, per-pass rooflines, and E_x over a seeded pair sample against
+    the oracle (the sample run as the GPU's own pair list)."""
+    import numpy as np
+    import torch
+    w = I.WORKLOADS[name]
+    t0 = time.time()
+    phi_np, pairs_np, info = I.make_workload(w)
+    gen_s = time.time() - t0
+    P, N = len(pairs_np), w.n ** 3
+    phi = torch.from_numpy(phi_np).to(dev)
+    pairs = torch.from_numpy(pairs_np).to(dev)
+    ex = hfx.Exchange(w.lattice, w.grid, alpha=0.25, precision=precision)
+    ex.ensure_workspace(w.n_orb, P)
+    E = torch.zeros(1, dtype=torch.float64, device=dev)
+    V = torch.empty_like(phi)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ex.apply(phi, pairs, ex=E, vxphi=V)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    ex.sync_status()
+    total, per, g = graph_steps(step, stream, reps, torch.cuda.synchronize)
+    del g
+    med = statistics.median(per)
+    stats = hfx.hfx_plan_stats(ex.ctx, w.n_orb, P, 0)
+    ex.set_tuning(8, 1 << 30, False)
+    ex.ensure_workspace(w.n_orb, P)
+    step()
+    hfx.hfx_profile_enable(ex.ctx, True)
+    hfx.hfx_profile_read(ex.ctx)
+    step()
+    torch.cuda.synchronize()
+    hfx.hfx_profile_enable(ex.ctx, False)
+    prof = hfx.hfx_profile_read(ex.ctx)
+    csize = 8 if precision == "fp32" else 16
+    peak = measured_peak_hbm()[0]
+    E_val = float(E.item())
+    hom = 0.5 * (w.volume / N) * float(torch.sum(phi * V).item())
+    sub = I.random_pairs_subset(pairs_np, n_check, seed=5)
+    Es, _ = ex.apply(phi, torch.from_numpy(sub).to(dev), energy_only=True)
+    E_ref, _ = O.exchange(phi_np, sub, w.lattice, want_v=False)
+    ex.close()
+    del phi, V, pairs
+    torch.cuda.empty_cache()
+    return {"config": workload_desc(w, P), "precision": precision, "value": P / (med / 1e3), "unit": UNIT,
+            "ms_per_call_median": med, "ms_per_call_mean": total / reps, "replays": reps,
+            "roofline_passes": pass_rooflines(prof, 1, stats, N, csize, P, med, peak),
+            "checks": {"E_x": E_val, "homogeneity_rel_err": abs(hom - E_val) / abs(E_val),
+                       "E_rel_err_vs_oracle_on_sample": abs(Es.item() - E_ref) / abs(E_ref),
+                       "sample": f"{len(sub)} seeded pairs as the GPU's own list"},
+            "input_generation_s": gen_s}
 
 
 # ------------------------------------------------------------------------------------------------
@@ -367,16 +537,12 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    # timed region: K full steps
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # timed region: K full steps, each one replay of a captured call (the schedule and tables
+    # were uploaded by the warm-up calls); CUDA events around the region and around each replay
     with ClockSampler(dev.index) as clk:
-        barrier()
-        start.record(stream)
-        for _ in range(args.steps):
-            step()
-        stop.record(stream)
-        barrier()
-    ms_total = start.elapsed_time(stop)
+        ms_total, per_step_ms, graph = graph_steps(step, stream, args.steps, barrier)
+    del graph
+    median_ms = statistics.median(per_step_ms)
 
     # per-kernel durations for the roofline: a second timed region of K steps with the batches on
     # one stream (pipelined batches share the GPU, which would stretch every kernel's duration);
@@ -435,7 +601,8 @@ def main():
                 "traffic": traffic, "kernel": dom, "peak_kind": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "measured": "CUDA events around each launch, batches on one stream, K steps",
-                "pass_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof}}
+                "pass_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof},
+                "passes": pass_rooflines(prof, args.steps, stats, N, csize, P, ms_step, peak)}
 
     # end to end through the public API with host buffers: every step copies its orbitals and pair
     # list in from pinned host memory and its E_x and V_x phi back out.  Steps are pipelined the way
@@ -503,7 +670,11 @@ def main():
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": max(3, args.warmup), "ms_per_step": ms_step, "median_ms_per_step": median_ms,
+        "value_at_median": world * P / (median_ms / 1000.0),
+        "timing": "each step is one replay of a CUDA graph of the full call; value = K steps / CUDA-event time "
+                  "of the K-step region (max over ranks); median over the K per-replay event times beside it",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
         "data": "synthetic (seeded water-box-shaped orbitals; no dataset)",
         "config": dict(workload_desc(w, P), precision=args.precision,
@@ -534,7 +705,7 @@ def main():
         V64 = torch.empty_like(V)
         ex64.apply(phi, pairs, ex=E64, vxphi=V64)
         torch.cuda.synchronize()
-        k64 = 2
+        k64 = 10
         s3, t3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s3.record(stream)
         for _ in range(k64):
@@ -561,6 +732,17 @@ def main():
         Es, Vs = ex.apply(phi, sub_d)
         torch.cuda.synchronize()
         Vs_np = Vs.cpu().numpy()
+        # the same oracle on every host core (one process per core) over a larger sample
+        pool = OraclePool(phi_np, w.lattice)
+        try:
+            n_all = int(max(pool.procs, min(P, 15.0 * rate * pool.procs)))
+            rate_all, dt_all, _ = pool.rate(pairs_np, n_all, seed=8)
+        finally:
+            pool.close()
+        line["cpu_baseline_all_cores"] = {
+            "value": rate_all, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
+            "sample": f"{n_all} seeded random pairs of the {P}-pair list split over {pool.procs} processes "
+                      f"({dt_all:.1f} s wall, numpy FP64, one process per host core)"}
         line["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{len(sub)} seeded random pairs of the {P}-pair list ({dt:.1f} s, numpy FP64, "
@@ -585,9 +767,20 @@ def main():
                 "sample": f"full ACE construction, {n_orb} orbitals on {N} points",
                 "M_rel_gpu_vs_oracle": rel(M_g.cpu().numpy(), M0), "P_rel_gpu_vs_oracle": rel(P_g.cpu().numpy(), P0)}
 
+    if rank == 0 and not args.no_extra:
+        from oracle import hfx_oracle as O
+        ex.close()
+        del V, phi
+        torch.cuda.empty_cache()
+        extra = {"water64_n96": measure_workload("water64_n96", args.precision, hfx, I, O, dev)}
+        if args.with_128:
+            extra["water128_n128"] = measure_workload("water128_n128", args.precision, hfx, I, O, dev, reps=2, n_check=8)
+        line["other_workloads"] = extra
+    else:
+        ex.close()
+
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ex.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
