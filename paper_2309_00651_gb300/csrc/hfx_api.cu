@@ -234,11 +234,6 @@ struct hfx_ctx {
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
   int blocks_fwd_ct = 1, blocks_x_ct = 1;
-  // register-resident forward and x passes (one grid line per thread) for the edges that have
-  // them; their Coulomb table is in [kx natural][y position][kz natural] order
-  bool line = false;
-  void* d_vline = nullptr;
-  int blocks_fwd_line = 1, blocks_x_line = 1;
   std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
   // optional per-pass device timing (hfx_profile_enable)
   bool prof_on = false;
@@ -312,7 +307,6 @@ static size_t smem_dense(const hfx_ctx* c) {
   return (size_t)(kDenseRing * c->grid[1] * (c->bsize / 2) * zc + c->grid[1]) * cplx_size(c) +
          (size_t)2 * c->bsize * c->grid[1] * zc * real_size(c);
 }
-static size_t smem_plane_line(int n) { return (size_t)n * (n + 1) * sizeof(float2); }
 static size_t smem_plane_ct(int n) { return (size_t)(n * (n + 1) + stage_plan(n).twtotal) * sizeof(float2); }
 static size_t smem_dense_ct(int n, int b) {
   const int zc = 8, ln = dense_rows_ct(n) * (b / 2) * zc, pts = n * zc;
@@ -367,8 +361,6 @@ static void free_ctx_tables(hfx_ctx* c) {
   c->side = nullptr;
   if (c->d_twct) cudaFree(c->d_twct);
   c->d_twct = nullptr;
-  if (c->d_vline) cudaFree(c->d_vline);
-  c->d_vline = nullptr;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   c->ev_pending.clear();
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -402,43 +394,6 @@ static hfx_status upload(void** dst, const void* src, size_t bytes) {
   return HFX_OK;
 }
 
-static int signed_freq(int f, int n) { return (f <= n / 2) ? f : f - n; }
-
-// v(G) = 4 pi / |G|^2 (0 at G = 0; 0 beyond the pair-density sphere for the sphere kernel) at
-// the grid position (a, b, e) whose signed frequencies along the three axes are mf[0][a],
-// mf[1][b] and mf[2][e]; row-major [a][b][e]
-static std::vector<double> coulomb_table(const hfx_ctx* c, const double (*B)[3], const std::vector<int> (&mf)[3]) {
-  const int n1 = c->grid[0], n2 = c->grid[1], n3 = c->grid[2];
-  std::vector<double> v((size_t)c->N);
-  for (int a = 0; a < n1; ++a)
-    for (int b = 0; b < n2; ++b)
-      for (int e = 0; e < n3; ++e) {
-        double G[3];
-        for (int k = 0; k < 3; ++k) G[k] = mf[0][a] * B[0][k] + mf[1][b] * B[1][k] + mf[2][e] * B[2][k];
-        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-        double val = (g2 > 0.0) ? 4.0 * kPi / g2 : 0.0;
-        if (c->kernel == HFX_KERNEL_COULOMB_SPHERE && 0.5 * g2 >= 4.0 * c->ecut) val = 0.0;
-        v[((size_t)a * n2 + b) * n3 + e] = val;
-      }
-  return v;
-}
-
-// reciprocal rows b_k with a_i . b_k = 2 pi delta_ik
-static void reciprocal_rows(const hfx_ctx* c, double B[3][3]) {
-  const double (*A)[3] = c->lat;
-  const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
-                     A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-  // inverse transpose: b_k = 2 pi (a_{k+1} x a_{k+2}) / det
-  for (int k = 0; k < 3; ++k) {
-    const double* p = A[(k + 1) % 3];
-    const double* q = A[(k + 2) % 3];
-    B[k][0] = 2.0 * kPi * (p[1] * q[2] - p[2] * q[1]) / det;
-    B[k][1] = 2.0 * kPi * (p[2] * q[0] - p[0] * q[2]) / det;
-    B[k][2] = 2.0 * kPi * (p[0] * q[1] - p[1] * q[0]) / det;
-  }
-}
-
 static hfx_status build_tables(hfx_ctx* c) {
   // twiddles w_n^t = exp(-2 pi i t / n), t < n, from the rational angle t/n
   for (int d = 0; d < 3; ++d) {
@@ -455,15 +410,42 @@ static hfx_status build_tables(hfx_ctx* c) {
     if (st != HFX_OK) return st;
   }
   // Coulomb table in storage order: v[x_pos][y_pos][z_pos] = 4 pi / |G|^2 (0 at G = 0)
-  double B[3][3];
-  reciprocal_rows(c, B);
+  double B[3][3];  // reciprocal rows b_k with a_i . b_k = 2 pi delta_ik
+  {
+    const double (*A)[3] = c->lat;
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) -
+                       A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                       A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    // inverse transpose: b_k = 2 pi (a_{k+1} x a_{k+2}) / det
+    for (int k = 0; k < 3; ++k) {
+      const double* p = A[(k + 1) % 3];
+      const double* q = A[(k + 2) % 3];
+      B[k][0] = 2.0 * kPi * (p[1] * q[2] - p[2] * q[1]) / det;
+      B[k][1] = 2.0 * kPi * (p[2] * q[0] - p[0] * q[2]) / det;
+      B[k][2] = 2.0 * kPi * (p[0] * q[1] - p[1] * q[0]) / det;
+    }
+  }
+  const int n1 = c->grid[0], n2 = c->grid[1], n3 = c->grid[2];
   std::vector<int> mf[3];
   for (int d = 0; d < 3; ++d) {
     const int n = c->grid[d];
     mf[d].resize(n);
-    for (int pos = 0; pos < n; ++pos) mf[d][pos] = signed_freq(freq_of_pos(c->geo.d[d], pos), n);
+    for (int pos = 0; pos < n; ++pos) {
+      const int f = freq_of_pos(c->geo.d[d], pos);
+      mf[d][pos] = (f <= n / 2) ? f : f - n;
+    }
   }
-  std::vector<double> v = coulomb_table(c, B, mf);
+  std::vector<double> v((size_t)c->N);
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b)
+      for (int e = 0; e < n3; ++e) {
+        double G[3];
+        for (int k = 0; k < 3; ++k) G[k] = mf[0][a] * B[0][k] + mf[1][b] * B[1][k] + mf[2][e] * B[2][k];
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        double val = (g2 > 0.0) ? 4.0 * kPi / g2 : 0.0;
+        if (c->kernel == HFX_KERNEL_COULOMB_SPHERE && 0.5 * g2 >= 4.0 * c->ecut) val = 0.0;
+        v[((size_t)a * n2 + b) * n3 + e] = val;
+      }
   hfx_status st;
   if (c->prec == HFX_PREC_FP64) st = upload(&c->d_vtab, v.data(), v.size() * sizeof(double));
   else { auto f = to_real_vec<float>(v); st = upload(&c->d_vtab, f.data(), f.size() * sizeof(float)); }
@@ -567,28 +549,6 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
       c->blocks_x_ct = std::max(1, c->blocks_x_ct);
       c->ct = f;
     }
-  }
-  // register-resident forward and x passes for the edges that have them (HFX_NO_LINE=1: the
-  // stage-by-stage compile-time passes instead)
-  const char* no_line = std::getenv("HFX_NO_LINE");
-  if (c->ct && c->ct->fwd_line && smem_plane_line(grid[0]) + 512 <= (size_t)c->max_smem && !(no_line && atoi(no_line) != 0)) {
-    const int n = grid[0];
-    e = c->ct->prepare_line(c->max_smem - 512, smem_plane_line(n), &c->blocks_fwd_line, &c->blocks_x_line);
-    if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
-    // v(G) at [kx natural][y in the digit-reversed positions of the forward pass][kz natural]
-    double B[3][3];
-    reciprocal_rows(c.get(), B);
-    std::vector<int> mf[3];
-    for (int d = 0; d < 3; ++d) {
-      mf[d].resize(n);
-      for (int pos = 0; pos < n; ++pos) mf[d][pos] = signed_freq(d == 1 ? freq_of_pos(c->geo.d[1], pos) : pos, n);
-    }
-    auto vl = to_real_vec<float>(coulomb_table(c.get(), B, mf));
-    st = upload(&c->d_vline, vl.data(), vl.size() * sizeof(float));
-    if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
-    c->blocks_fwd_line = std::max(1, c->blocks_fwd_line);
-    c->blocks_x_line = std::max(1, c->blocks_x_line);
-    c->line = true;
   }
   *out = c.release();
   return HFX_OK;
@@ -832,10 +792,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
         Passes<T>::inv_z_rows(g, gr, smem_rows(c, c->rb), fs, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
       close(kProfX, e0, fs);
     } else {
-      if (ct && c->line) {
-        const int gl = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_line * 8);
-        ct->fwd_line(std::max(gl, 1), smem_plane_line(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W);
-      } else if (ct) {
+      if (ct) {
         const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
         ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
                    (const float2*)c->d_twct);
@@ -845,11 +802,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       }
       close(kProfFwd, e0, fs);
       e0 = mark(fs);
-      if (ct && c->line) {
-        const int gl = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_line * 8);
-        ct->x_line(std::max(gl, 1), smem_plane_line(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vline,
-                   epart, energy_only ? 1 : 0);
-      } else if (ct) {
+      if (ct) {
         const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
         ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
                       (const float2*)c->d_twct, epart, energy_only ? 1 : 0);

@@ -3,7 +3,6 @@
 #include "hfx_ct.cuh"
 #include "hfx_ct_diag.cuh"
 #include "hfx_internal.h"
-#include "hfx_line.cuh"
 
 namespace hfx {
 namespace {
@@ -51,41 +50,7 @@ void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long 
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }
 
-// register-resident passes where the edge has them
-template <int N, bool HAS = line::Has<N>::value> struct LineLaunch {
-  static constexpr int threads = 0;
-  static constexpr cudaError_t (*prepare)(int, size_t, int*, int*) = nullptr;
-  static constexpr void (*fwd)(int, size_t, cudaStream_t, const float*, long long, const int4*, int, int,
-                               float2*) = nullptr;
-  static constexpr void (*x)(int, size_t, cudaStream_t, const int4*, int, int, float2*, const float*, double*,
-                             int) = nullptr;
-};
-template <int N> struct LineLaunch<N, true> {
-  static constexpr int threads = line::Geo<N>::NT;
-  static cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x) {
-    const void* ks[] = {(const void*)line::k_fwd_line<N>, (const void*)line::k_x_line<N>};
-    for (const void* k : ks) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
-      if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_fwd, line::k_fwd_line<N>, threads, smem_plane);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_x, line::k_x_line<N>, threads, smem_plane);
-  }
-  static void fwd(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
-                  int c0, int c1, float2* W) {
-    line::k_fwd_line<N><<<grid, threads, smem, st>>>(orb, Ntot, couples, c0, c1, W);
-  }
-  static void x(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
-                const float* vline, double* epart, int energy_only) {
-    line::k_x_line<N><<<grid, threads, smem, st>>>(couples, c0, c1, W, vline, epart, energy_only);
-  }
-};
-
-const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense, &y_acc_diag,
-                    LineLaunch<kN>::threads, LineLaunch<kN>::prepare, LineLaunch<kN>::fwd, LineLaunch<kN>::x};
+const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense, &y_acc_diag};
 
 }  // namespace
 

@@ -64,15 +64,6 @@ struct CtFns {
   void (*y_acc_diag)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                      const int4* couples, const int* slot_list, const int* slot_couple_base,
                      const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
-  // register-resident forward and x passes (hfx_line.cuh; NULL for edges without them): one grid
-  // line per thread, `line_threads` threads per block, a plane of n x (n + 1) complex values in
-  // shared memory; the x pass reads v(G) in [kx natural][y position][kz natural] order
-  int line_threads;
-  cudaError_t (*prepare_line)(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x);
-  void (*fwd_line)(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
-                   int c0, int c1, float2* W);
-  void (*x_line)(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
-                 const float* vline, double* epart, int energy_only);
 };
 
 #define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128)

@@ -346,22 +346,3 @@ def test_compile_time_passes_with_sparse_pair_list():
     E, V = run_gpu(phi, sub, w.lattice, "fp32")
     assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
     assert_v_close(V, V_ref, TOL["fp32"])
-
-
-@pytest.mark.parametrize("n", [32, 48, 64, 72])
-@pytest.mark.parametrize("no_line", ["0", "1"])
-def test_register_line_and_stage_passes(n, no_line, monkeypatch):
-    """FP32 edges up to 72 run the register-resident forward and x passes (one grid line per
-    thread); HFX_NO_LINE=1 forces the stage-by-stage compile-time passes.  Both against the oracle
-    on 10 orbitals (two orbital blocks, one of them ragged), the full list and an energy-only call."""
-    monkeypatch.setenv("HFX_NO_LINE", no_line)
-    L, n_orb = 0.26 * n, 10
-    lat = np.diag([L] * 3)
-    phi = band_limited(n_orb, n, L, seed=3 * n + 1, frac=0.2)
-    pairs = I.all_pairs(n_orb)
-    E_ref, V_ref = O.exchange(phi, pairs, lat)
-    E, V = run_gpu(phi, pairs, lat, "fp32")
-    assert abs(E - E_ref) <= 1e-6 * abs(E_ref)
-    assert_v_close(V, V_ref, 1e-6)
-    Ee, _ = run_gpu(phi, pairs, lat, "fp32", energy_only=True)
-    assert abs(Ee - E_ref) <= 1e-6 * abs(E_ref)
