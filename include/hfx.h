@@ -135,12 +135,44 @@ typedef struct {
 } hfx_apply_args;
 
 /* hfx_apply_batched -- several independent problems (each with its own context, so its own
- * cell, grid and workspace) enqueued together on one stream: the uneven batch of
- * independent configurations (the CP-group idea of Sec. 2.2 applied to whole problems).
- * Same argument rules, per problem, as hfx_apply; stops at the first problem whose
- * arguments are rejected and returns that error. */
+ * cell, grid, orbital count and workspace), all their passes in ONE persistent launch: the
+ * uneven batch of independent configurations, distributed as independent work the way Sec. 2.2
+ * spreads independent work over processor groups.
+ *   Per problem the call first enqueues its staging (V_x phi cleared, pairs placed, the FP32
+ *   orbital copy), then one launch runs every pass of every problem from a device work queue:
+ *   items (planes, tiles) are taken in a fixed task order by all blocks; the tasks of one problem
+ *   run as a chain (forward, x/Coulomb and accumulate pass of each batch of couples, then the
+ *   energy sum) and the chains of different problems are interleaved, so the problems share the
+ *   GPU.  A block whose item depends on an unfinished task waits for it at most the context's
+ *   wait budget (hfx_set_wait_budget); a wait that runs out sets HFX_ERR_TIMEOUT in the error
+ *   word of that problem's context, every block then stops, and the call's results are undefined.
+ *   Results equal hfx_apply's up to rounding order (the batched passes are the runtime-geometry
+ *   forms for every grid).
+ *   Rules: same argument rules per problem as hfx_apply; one distinct context per problem; every
+ *   context needs the same precision and device and planes that fit in shared memory
+ *   (HFX_ERR_UNSUPPORTED_GRID otherwise); each context's workspace must hold hfx_workspace_bytes
+ *   for its problem; batched calls led by one context must not overlap on the GPU.  The queue tables live in a
+ *   device buffer owned by the first context (ctxs[0]); the first call that needs a larger one
+ *   allocates it (and synchronises the stream), so make that call before any stream capture --
+ *   during capture such a call is rejected with HFX_ERR_INVALID_ARG.  Stops at the first problem
+ *   whose arguments are rejected and returns that error. */
 hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
                              void* cuda_stream);
+
+/* flag for hfx_apply_args of hfx_apply_batched only -- a failure-detection test: the problem's
+ * first dependent wait expects one more finished item than its predecessor task has, so it can
+ * only end by running out of the wait budget (HFX_ERR_TIMEOUT); no GPU fault is involved. */
+#define HFX_TEST_STALL    0x100u
+
+/* hfx_apply_sequential -- the same problems as separate hfx_apply calls, one after another on
+ * the stream, each with the fastest passes its own context has (compile-time geometry where the
+ * edge has it).  Same argument rules; HFX_TEST_STALL is rejected. */
+hfx_status hfx_apply_sequential(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
+                                void* cuda_stream);
+
+/* hfx_set_wait_budget -- clock cycles one device-side wait of hfx_apply_batched may last when
+ * this context leads the batch (0: the default, 2^34 cycles, about 8 s at 2 GHz). */
+hfx_status hfx_set_wait_budget(hfx_ctx* c, int64_t cycles);
 
 /* hfx_apply_noalloc -- hfx_apply for callers that cannot allocate device memory.
  * The paper has no counterpart: this exists for callers that must not call cudaMalloc when

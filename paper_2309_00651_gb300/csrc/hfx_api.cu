@@ -235,6 +235,10 @@ struct hfx_ctx {
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
   int blocks_fwd_ct = 1, blocks_x_ct = 1;
   std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
+  // queue tables of hfx_apply_batched when this context comes first in a batch
+  void* d_batch = nullptr;
+  size_t batch_bytes = 0;
+  long long wait_budget = 1LL << 34;  // clock cycles a device-side wait may take (~8 s)
   // optional per-pass device timing (hfx_profile_enable)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -361,6 +365,9 @@ static void free_ctx_tables(hfx_ctx* c) {
   c->side = nullptr;
   if (c->d_twct) cudaFree(c->d_twct);
   c->d_twct = nullptr;
+  if (c->d_batch) cudaFree(c->d_batch);
+  c->d_batch = nullptr;
+  c->batch_bytes = 0;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   c->ev_pending.clear();
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -727,6 +734,31 @@ static void launch_energy(const double* epart, const int4* couples, int total, i
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// Small tables reach device memory as kernel arguments (8 KiB per launch): no host buffer has to
+// outlive the call (it may be captured in a graph) and no pageable-memory copy is involved.
+constexpr int kTableWords = 2048;
+struct TableChunk { uint32_t w[kTableWords]; };
+__global__ void k_put_words(uint32_t* __restrict__ dst, TableChunk chunk, int count) {
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = chunk.w[i];
+}
+static hfx_status put_table(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  const uint32_t* s = (const uint32_t*)src;
+  size_t words = bytes / 4;
+  uint32_t* d = (uint32_t*)dst;
+  while (words > 0) {
+    const int n = (int)std::min<size_t>(words, kTableWords);
+    TableChunk ch;
+    std::memcpy(ch.w, s, (size_t)n * 4);
+    k_put_words<<<1, 256, 0, st>>>(d, ch, n);
+    HFX_CUDA_TRY(cudaGetLastError());
+    s += n;
+    d += n;
+    words -= (size_t)n;
+  }
+  return HFX_OK;
+}
+
+
 // ------------------------------------------------------------------------------------
 // apply
 // ------------------------------------------------------------------------------------
@@ -878,19 +910,16 @@ static hfx_status apply_empty(const hfx_ctx* c, int32_t n_orb, uint32_t flags, d
   return HFX_OK;
 }
 
-// one evaluation with its schedule tables on the device and its scratch at env.ws: stage a1
-// (V cleared, pairs placed, FP32 orbital copy), the passes of every batch, then the energy sum
-static hfx_status apply_with(hfx_ctx* c, Schedule& S, const Layout& L, const CallEnv& env, const void* orbitals,
-                             int32_t n_orb, const int32_t* pairs, int64_t n_pairs, uint32_t flags, double* ex_dev,
-                             double* vxphi, cudaStream_t st) {
+// stage a1 of one evaluation: V cleared (unless accumulating or energy-only), the pair list placed
+// in the canonical couple layout, the FP32 orbital copy; *orb_pass = the orbitals the passes read
+static hfx_status stage_call(hfx_ctx* c, Schedule& S, const Layout& L, const CallEnv& env, const void* orbitals,
+                             int32_t n_orb, const int32_t* pairs, int64_t n_pairs, uint32_t flags, double* vxphi,
+                             cudaStream_t st, const void** orb_pass) {
   char* ws = env.ws;
   const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
   const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
   if (!accumulate && !energy_only)
     HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, (size_t)n_orb * c->N * sizeof(double), st));
-
-  // stage a1: pair list -> couples in the canonical layout
-  cudaEvent_t e_stage = env.prof ? prof_mark(c, st) : nullptr;
   int4* couples = (int4*)(ws + L.couples);
   HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S.max_total_couples * sizeof(int4), st));
   {
@@ -901,30 +930,37 @@ static hfx_status apply_with(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
                                              S.d_slot_couple_base, couples, c->d_err);
   }
   HFX_CUDA_TRY(cudaGetLastError());
-
-  hfx_status rs;
-  if (c->prec == HFX_PREC_FP64) {
-    if (env.prof) prof_close(c, kProfStage, e_stage, st);
-    rs = run_passes<double>(c, S, L, env, (const double*)orbitals, n_orb, flags, vxphi, st);
-  } else {
-    const float* orb32;
-    if (flags & HFX_ORBITALS_F32) {
-      orb32 = (const float*)orbitals;
-    } else {
-      float* dst = (float*)(ws + L.orb32);
-      const long long n = (long long)n_orb * c->N;
-      const int blocks = (int)std::min<long long>((n / 2 + 255) / 256 + 1, (long long)c->sm_count * 16);
-      k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
-      orb32 = dst;
-    }
-    if (env.prof) prof_close(c, kProfStage, e_stage, st);
-    rs = run_passes<float>(c, S, L, env, orb32, n_orb, flags, vxphi, st);
+  *orb_pass = orbitals;
+  if (c->prec == HFX_PREC_FP32 && !(flags & HFX_ORBITALS_F32)) {
+    float* dst = (float*)(ws + L.orb32);
+    const long long n = (long long)n_orb * c->N;
+    const int blocks = (int)std::min<long long>((n / 2 + 255) / 256 + 1, (long long)c->sm_count * 16);
+    k_cast_f32<<<blocks, 256, 0, st>>>((const double*)orbitals, dst, n);
+    HFX_CUDA_TRY(cudaGetLastError());
+    *orb_pass = dst;
   }
+  return HFX_OK;
+}
+
+// one evaluation with its schedule tables on the device and its scratch at env.ws: stage a1, the
+// passes of every batch, then the energy sum
+static hfx_status apply_with(hfx_ctx* c, Schedule& S, const Layout& L, const CallEnv& env, const void* orbitals,
+                             int32_t n_orb, const int32_t* pairs, int64_t n_pairs, uint32_t flags, double* ex_dev,
+                             double* vxphi, cudaStream_t st) {
+  char* ws = env.ws;
+  const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
+  cudaEvent_t e_stage = env.prof ? prof_mark(c, st) : nullptr;
+  const void* orb = nullptr;
+  hfx_status rs = stage_call(c, S, L, env, orbitals, n_orb, pairs, n_pairs, flags, vxphi, st, &orb);
+  if (rs != HFX_OK) return rs;
+  if (env.prof) prof_close(c, kProfStage, e_stage, st);
+  if (c->prec == HFX_PREC_FP64) rs = run_passes<double>(c, S, L, env, (const double*)orb, n_orb, flags, vxphi, st);
+  else rs = run_passes<float>(c, S, L, env, (const float*)orb, n_orb, flags, vxphi, st);
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
   cudaEvent_t e_en = env.prof ? prof_mark(c, st) : nullptr;
-  launch_energy((const double*)(ws + L.epart), couples, (int)S.max_total_couples, eparts(c), (double*)(ws + L.eblk),
-                scale, accumulate, ex_dev, st);
+  launch_energy((const double*)(ws + L.epart), (const int4*)(ws + L.couples), (int)S.max_total_couples, eparts(c),
+                (double*)(ws + L.eblk), scale, accumulate, ex_dev, st);
   if (env.prof) prof_close(c, kProfEnergy, e_en, st);
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
@@ -951,11 +987,13 @@ extern "C" hfx_status hfx_apply(hfx_ctx* c, const void* orbitals, int32_t n_orb,
   return apply_impl(c, orbitals, n_orb, pairs, n_pairs, flags, ex_dev, vxphi, (cudaStream_t)cuda_stream);
 }
 
-extern "C" hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n, void* cuda_stream) {
+extern "C" hfx_status hfx_apply_sequential(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
+                                           void* cuda_stream) {
   g_last_error.clear();
   if (n < 0 || (n > 0 && (!ctxs || !args))) return fail(HFX_ERR_INVALID_ARG, "bad batch arguments");
   for (int32_t k = 0; k < n; ++k) {
     const hfx_apply_args& a = args[k];
+    if (a.flags & HFX_TEST_STALL) return fail(HFX_ERR_INVALID_ARG, "problem %d: HFX_TEST_STALL is for hfx_apply_batched", (int)k);
     hfx_status s = apply_impl(ctxs[k], a.orbitals, a.n_orb, a.pairs, a.n_pairs, a.flags, a.ex_dev, a.vxphi,
                               (cudaStream_t)cuda_stream);
     if (s != HFX_OK) {
@@ -963,6 +1001,175 @@ extern "C" hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_ar
       return fail(s, "problem %d: %s", (int)k, m.c_str());
     }
   }
+  return HFX_OK;
+}
+
+// The batch as one persistent launch (hfx_batch.cuh): per problem the staging launches (V cleared,
+// pairs placed, FP32 copy), then one launch of k_batch_persistent over the tasks of all problems.
+template <typename T>
+static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n, cudaStream_t st) {
+  hfx_ctx* lead = ctxs[0];
+  std::vector<BatchProblem<T>> probs;
+  std::vector<std::vector<BatchTask>> chains;
+  std::vector<int> stall;
+  size_t smem = 0;
+  for (int32_t k = 0; k < n; ++k) {
+    hfx_ctx* c = ctxs[k];
+    const hfx_apply_args& a = args[k];
+    if (c->pencil)
+      return fail(HFX_ERR_UNSUPPORTED_GRID, "problem %d: planes exceed shared memory (use hfx_apply_sequential)", (int)k);
+    if (a.n_pairs == 0) {
+      hfx_status s = apply_empty(c, a.n_orb, a.flags, a.ex_dev, a.vxphi, st);
+      if (s != HFX_OK) return s;
+      continue;
+    }
+    Schedule* S = nullptr;
+    hfx_status s = get_schedule(c, a.n_orb, &S);
+    if (s != HFX_OK) return s;
+    const Layout L = layout_of(c, *S, a.n_orb, false);
+    if (!c->ws || c->ws_bytes < L.total)
+      return fail(HFX_ERR_OOM, "problem %d: workspace too small: have %zu bytes, need %zu", (int)k, c->ws_bytes, L.total);
+    const CallEnv env{(char*)c->ws, nullptr, false};
+    const void* orb = nullptr;
+    s = stage_call(c, *S, L, env, a.orbitals, a.n_orb, a.pairs, a.n_pairs, a.flags, a.vxphi, st, &orb);
+    if (s != HFX_OK) return s;
+    const bool eo = (a.flags & HFX_ENERGY_ONLY) != 0;
+    BatchProblem<T> P;
+    std::memset(&P, 0, sizeof(P));
+    P.g = c->geo;
+    P.orb = (const T*)orb;
+    P.couples = (const int4*)(env.ws + L.couples);
+    P.W = (cx<T>*)(env.ws + L.W);
+    P.epart = (double*)(env.ws + L.epart);
+    P.V = a.vxphi;
+    P.ex = a.ex_dev;
+    P.vtab = (const T*)c->d_vtab;
+    P.tw1 = (const cx<T>*)c->d_tw[0];
+    P.tw2 = (const cx<T>*)c->d_tw[1];
+    P.tw3 = (const cx<T>*)c->d_tw[2];
+    P.slot_couple_base = S->d_slot_couple_base;
+    P.slot_blocks = S->d_slot_blocks;
+    P.err = c->d_err;
+    P.vscale = -c->alpha / (double)c->N;
+    P.escale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
+    P.n_orb = a.n_orb;
+    P.bsize = S->b;
+    P.grp = c->gen_grp;
+    P.phi_smem = c->gen_phi;
+    P.cap_max = gen_cap_max(c);
+    P.total_couples = (int)S->max_total_couples;
+    P.accumulate = (a.flags & HFX_ACCUMULATE) ? 1 : 0;
+    P.energy_only = eo ? 1 : 0;
+    const int prob = (int)probs.size();
+    probs.push_back(P);
+    stall.push_back((a.flags & HFX_TEST_STALL) ? 1 : 0);
+    std::vector<BatchTask> ch;
+    auto add = [&](int kind, long long items, int a0, int a1, int cbase) {
+      BatchTask t;
+      std::memset(&t, 0, sizeof(t));
+      t.items = (int)items;
+      t.prob = prob;
+      t.kind = kind;
+      t.a0 = a0;
+      t.a1 = a1;
+      t.cbase = cbase;
+      ch.push_back(t);
+    };
+    const int zc = zchunk(c), nzc = (c->grid[2] + zc - 1) / zc;
+    for (int b = 0; b < S->nbatches; ++b) {
+      const int s0 = S->batch_slot_begin[b], s1 = S->batch_slot_begin[b + 1];
+      const int c0 = S->slot_couple_base[s0], c1 = S->slot_couple_base[s1];
+      add(kTaskFwd, (long long)(c1 - c0) * c->grid[0], c0, c1, c0);
+      add(kTaskX, (long long)(c1 - c0) * c->grid[1], c0, c1, c0);
+      if (!eo) add(kTaskAcc, (long long)nzc * c->grid[0] * (s1 - s0), s0, s1, c0);
+    }
+    add(kTaskEnergy, 1, 0, 0, 0);
+    chains.push_back(ch);
+    smem = std::max({smem, smem_fwd(c), smem_x(c), eo ? (size_t)0 : smem_acc(c)});
+  }
+  if (probs.empty()) return HFX_OK;
+  if (smem + 512 > (size_t)lead->max_smem)
+    return fail(HFX_ERR_UNSUPPORTED_GRID, "a batch tile needs %zu bytes of shared memory (limit %d)", smem, lead->max_smem);
+  // interleave the chains level by level; each task waits for its predecessor in its own chain
+  std::vector<BatchTask> tasks;
+  std::vector<std::vector<int>> gidx(chains.size());
+  size_t maxlen = 0;
+  for (auto& ch : chains) maxlen = std::max(maxlen, ch.size());
+  for (size_t lvl = 0; lvl < maxlen; ++lvl)
+    for (size_t p = 0; p < chains.size(); ++p) {
+      if (lvl >= chains[p].size()) continue;
+      BatchTask t = chains[p][lvl];
+      t.dep = lvl == 0 ? -1 : gidx[p][lvl - 1];
+      t.extra = (lvl == 1 && stall[p]) ? 1 : 0;
+      gidx[p].push_back((int)tasks.size());
+      tasks.push_back(t);
+    }
+  long long total = 0;
+  for (auto& t : tasks) { t.first = total; total += t.items; }
+  const int ntasks = (int)tasks.size();
+  // device tables: queue header and done counters, tasks, problems
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  const size_t o_queue = take(sizeof(BatchQueue) + (size_t)ntasks * sizeof(int));
+  const size_t o_tasks = take((size_t)ntasks * sizeof(BatchTask));
+  const size_t o_probs = take(probs.size() * sizeof(BatchProblem<T>));
+  if (lead->batch_bytes < off) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HFX_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(HFX_ERR_INVALID_ARG, "the first batched call of this size on its lead context must come before stream capture");
+    if (lead->d_batch) { HFX_CUDA_TRY(cudaStreamSynchronize(st)); cudaFree(lead->d_batch); }
+    lead->d_batch = nullptr;
+    lead->batch_bytes = 0;
+    cudaError_t e = cudaMalloc(&lead->d_batch, off);
+    if (e != cudaSuccess) return fail(HFX_ERR_OOM, "cudaMalloc(%zu) for the batch tables failed: %s", off, cudaGetErrorString(e));
+    lead->batch_bytes = off;
+  }
+  char* base = (char*)lead->d_batch;
+  hfx_status s = put_table(base + o_tasks, tasks.data(), tasks.size() * sizeof(BatchTask), st);
+  if (s == HFX_OK) s = put_table(base + o_probs, probs.data(), probs.size() * sizeof(BatchProblem<T>), st);
+  if (s != HFX_OK) return s;
+  HFX_CUDA_TRY(cudaMemsetAsync(base + o_queue, 0, sizeof(BatchQueue) + (size_t)ntasks * sizeof(int), st));
+  int per_sm = 0;
+  HFX_CUDA_TRY(Passes<T>::batch_occupancy(smem, &per_sm));
+  const int grid = std::max(1, per_sm) * lead->sm_count;
+  Passes<T>::batch(grid, smem, st, (const BatchProblem<T>*)(base + o_probs), (const BatchTask*)(base + o_tasks), ntasks,
+                   total, (BatchQueue*)(base + o_queue), lead->wait_budget);
+  HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
+}
+
+extern "C" hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n, void* cuda_stream) {
+  g_last_error.clear();
+  if (n < 0 || (n > 0 && (!ctxs || !args))) return fail(HFX_ERR_INVALID_ARG, "bad batch arguments");
+  if (n == 0) return HFX_OK;
+  for (int32_t k = 0; k < n; ++k) {
+    const hfx_apply_args& a = args[k];
+    hfx_status s = check_apply_args(ctxs[k], a.orbitals, a.n_orb, a.pairs, a.n_pairs, a.flags & ~HFX_TEST_STALL,
+                                    a.ex_dev, a.vxphi);
+    if (s != HFX_OK) {
+      std::string m = g_last_error;
+      return fail(s, "problem %d: %s", (int)k, m.c_str());
+    }
+    if (ctxs[k]->prec != ctxs[0]->prec || ctxs[k]->device != ctxs[0]->device)
+      return fail(HFX_ERR_INVALID_ARG, "problem %d: every context of a batch needs the same precision and device", (int)k);
+  }
+  {  // one context per problem: problems of one batch run concurrently in their own workspaces
+    std::vector<const hfx_ctx*> seen(ctxs, ctxs + n);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+      return fail(HFX_ERR_INVALID_ARG, "a context appears twice in the batch (each problem needs its own)");
+  }
+  hfx_status s = ctxs[0]->prec == HFX_PREC_FP64 ? batched_persistent<double>(ctxs, args, n, (cudaStream_t)cuda_stream)
+                                                : batched_persistent<float>(ctxs, args, n, (cudaStream_t)cuda_stream);
+  return s;
+}
+
+extern "C" hfx_status hfx_set_wait_budget(hfx_ctx* c, int64_t cycles) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+  if (cycles < 0) return fail(HFX_ERR_INVALID_ARG, "cycles must be >= 0");
+  c->wait_budget = cycles == 0 ? (1LL << 34) : cycles;
   return HFX_OK;
 }
 
@@ -1095,30 +1302,6 @@ static hfx_status noalloc_scratch(void** out) {
     g_noalloc_addr[dev] = p;
   }
   *out = g_noalloc_addr[dev];
-  return HFX_OK;
-}
-
-// The schedule tables reach the scratch array as kernel arguments (8 KiB per launch): no host
-// buffer has to outlive the call and no pageable-memory copy is involved.
-constexpr int kTableWords = 2048;
-struct TableChunk { uint32_t w[kTableWords]; };
-__global__ void k_put_words(uint32_t* __restrict__ dst, TableChunk chunk, int count) {
-  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = chunk.w[i];
-}
-static hfx_status put_table(void* dst, const void* src, size_t bytes, cudaStream_t st) {
-  const uint32_t* s = (const uint32_t*)src;
-  size_t words = bytes / 4;
-  uint32_t* d = (uint32_t*)dst;
-  while (words > 0) {
-    const int n = (int)std::min<size_t>(words, kTableWords);
-    TableChunk ch;
-    std::memcpy(ch.w, s, (size_t)n * 4);
-    k_put_words<<<1, 256, 0, st>>>(d, ch, n);
-    HFX_CUDA_TRY(cudaGetLastError());
-    s += n;
-    d += n;
-    words -= (size_t)n;
-  }
   return HFX_OK;
 }
 

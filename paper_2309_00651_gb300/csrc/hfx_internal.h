@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "hfx_batch.cuh"
 #include "hfx_kernels.cuh"
 
 namespace hfx {
@@ -33,6 +34,10 @@ struct Passes {
   static void y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b, const T* orb,
                           const int4* couples, const int* slot_list, const int* slot_couple_base,
                           const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
+  // one persistent launch over the task list of a batch of problems (hfx_batch.cuh)
+  static void batch(int grid, size_t smem, cudaStream_t st, const BatchProblem<T>* probs, const BatchTask* tasks,
+                    int ntasks, long long total_items, BatchQueue* queue, long long budget);
+  static cudaError_t batch_occupancy(size_t smem, int* blocks);
   static void y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples,
                             const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int bsize,
                             int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale, int grp,

@@ -169,7 +169,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // plane copies, one complex value per thread step (consecutive threads on consecutive z: 8- or
-// 16-byte coalesced global accesses and conflict-free shared accesses into the padded rows)
+// 16-byte coalesced global accesses and conflict-free shared accesses into the padded rows); the
+// loads go through L2 only (the plane is read once, and in a persistent launch another block of
+// the same launch may have written it)
 constexpr int kLoadUnroll = 4;  // loads each thread keeps in flight per copy step
 
 template <typename C>
@@ -183,7 +185,7 @@ __device__ __forceinline__ void plane_g2s(C* __restrict__ buf, int S, const C* _
       const int p = p0 + u * blockDim.x;
       if (p < total) {
         const int r = n3div.div(p), z = p - r * n3;
-        v[u] = __ldg(src + r * gstride + z);
+        v[u] = __ldcg(src + r * gstride + z);
       }
     }
 #pragma unroll
@@ -209,6 +211,54 @@ __device__ __forceinline__ void plane_s2g(C* __restrict__ dst, long long gstride
 // ----------------------------------------------------------------------------------
 // pass 1: pair product + forward FFT along z and y of one x-plane
 // ----------------------------------------------------------------------------------
+// one item (couple cl = it / n1, x-plane x = it mod n1); buf holds the padded plane, tw2/tw3 the
+// twiddles in shared memory (loaded by the caller before its first barrier)
+template <typename T>
+__device__ __forceinline__ void fwd_yz_item(const Geo& g, const T* __restrict__ orb, const int4* __restrict__ couples,
+                                            int c0, cx<T>* __restrict__ W, const cx<T>* tw2, const cx<T>* tw3,
+                                            cx<T>* buf, long long it) {
+  using C = cx<T>;
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
+  const int plane = n2 * n3;
+  const int cl = int(it / n1);
+  const int x = int(it - (long long)cl * n1);
+  const int4 cp = couples[c0 + cl];
+  if (couple_empty(cp)) return;
+  const long long off = (long long)x * plane;
+  const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+  const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * g.N + off;
+  const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * g.N + off;
+  const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * g.N + off;
+  const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
+  __syncthreads();  // previous item's store has finished reading buf (and tables are loaded)
+  const FastDiv n3div = g.d[2].ndiv;
+  for (int p0 = threadIdx.x; p0 < plane; p0 += kLoadUnroll * blockDim.x) {
+    T a1[kLoadUnroll], a2[kLoadUnroll], b1[kLoadUnroll], b2[kLoadUnroll];
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int p = p0 + u * blockDim.x;
+      const bool in = p < plane;
+      a1[u] = (in && hasa) ? __ldg(pa1 + p) : T(0);
+      a2[u] = (in && hasa) ? __ldg(pa2 + p) : T(0);
+      b1[u] = (in && hasb) ? __ldg(pb1 + p) : T(0);
+      b2[u] = (in && hasb) ? __ldg(pb2 + p) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kLoadUnroll; ++u) {
+      const int p = p0 + u * blockDim.x;
+      if (p < plane) {
+        const int y = n3div.div(p), z = p - y * n3;
+        buf[y * S + z] = mk<C>(a1[u] * a2[u], b1[u] * b2[u]);
+      }
+    }
+  }
+  __syncthreads();
+  // z: n2 rows (stride S) of length n3; y: n3 columns (stride 1) of length n2 (element stride S)
+  fft_forward(g.d[2], 0, g.d[2].ns, buf, tw3, n2, g.d[1].ndiv, S, 1);
+  fft_forward(g.d[1], 0, g.d[1].ns, buf, tw2, n3, g.d[2].ndiv, 1, S);
+  plane_s2g(W + ((long long)cl * n1 + x) * plane, n3, buf, S, n2, n3, g.d[2].ndiv);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsPlane, 3)
 k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W,
@@ -216,53 +266,13 @@ k_fwd_yz(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* _
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
-  const int plane = n2 * n3;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw2 = buf + n2 * S;
   C* tw3 = tw2 + n2;
   for (int i = threadIdx.x; i < n2; i += blockDim.x) tw2[i] = tw2g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
-
   const long long items = (long long)(c1 - c0) * n1;
-  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const int cl = int(it / n1);
-    const int x = int(it - (long long)cl * n1);
-    const int4 cp = couples[c0 + cl];
-    if (couple_empty(cp)) continue;
-    const long long off = (long long)x * plane;
-    const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
-    const T* pa1 = orb + (long long)(hasa ? cp.x : 0) * g.N + off;
-    const T* pa2 = orb + (long long)(hasa ? cp.y : 0) * g.N + off;
-    const T* pb1 = orb + (long long)(hasb ? cp.z : 0) * g.N + off;
-    const T* pb2 = orb + (long long)(hasb ? cp.w : 0) * g.N + off;
-    __syncthreads();  // previous item's store has finished reading buf (and tables are loaded)
-    const FastDiv n3div = g.d[2].ndiv;
-    for (int p0 = threadIdx.x; p0 < plane; p0 += kLoadUnroll * blockDim.x) {
-      T a1[kLoadUnroll], a2[kLoadUnroll], b1[kLoadUnroll], b2[kLoadUnroll];
-#pragma unroll
-      for (int u = 0; u < kLoadUnroll; ++u) {
-        const int p = p0 + u * blockDim.x;
-        const bool in = p < plane;
-        a1[u] = (in && hasa) ? __ldg(pa1 + p) : T(0);
-        a2[u] = (in && hasa) ? __ldg(pa2 + p) : T(0);
-        b1[u] = (in && hasb) ? __ldg(pb1 + p) : T(0);
-        b2[u] = (in && hasb) ? __ldg(pb2 + p) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < kLoadUnroll; ++u) {
-        const int p = p0 + u * blockDim.x;
-        if (p < plane) {
-          const int y = n3div.div(p), z = p - y * n3;
-          buf[y * S + z] = mk<C>(a1[u] * a2[u], b1[u] * b2[u]);
-        }
-      }
-    }
-    __syncthreads();
-    // z: n2 rows (stride S) of length n3; y: n3 columns (stride 1) of length n2 (element stride S)
-    fft_forward(g.d[2], 0, g.d[2].ns, buf, tw3, n2, g.d[1].ndiv, S, 1);
-    fft_forward(g.d[1], 0, g.d[1].ns, buf, tw2, n3, g.d[2].ndiv, 1, S);
-    plane_s2g(W + ((long long)cl * n1 + x) * plane, n3, buf, S, n2, n3, g.d[2].ndiv);
-  }
+  for (long long it = blockIdx.x; it < items; it += gridDim.x) fwd_yz_item(g, orb, couples, c0, W, tw2, tw3, buf, it);
 }
 
 // ----------------------------------------------------------------------------------
@@ -318,6 +328,35 @@ __device__ __forceinline__ double x_last_coulomb_rt(int R, C* buf, int S, int n1
   }
 }
 
+// one item (couple cl = it / n2, y-plane y = it mod n2); red: 32 doubles of shared memory
+template <typename T>
+__device__ __forceinline__ void x_coulomb_item(const Geo& g, const int4* __restrict__ couples, int c0,
+                                               cx<T>* __restrict__ W, const T* __restrict__ vtab, const cx<T>* tw1,
+                                               const cx<T>* tw3, double* __restrict__ epart, bool energy_only,
+                                               cx<T>* buf, double* red, long long it) {
+  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
+  const long long plane = (long long)n2 * n3;
+  const int cl = int(it / n2);
+  const int y = int(it - (long long)cl * n2);
+  if (couple_empty(couples[c0 + cl])) return;
+  cx<T>* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
+  __syncthreads();
+  plane_g2s(buf, S, wc, plane, n1, n3, g.d[2].ndiv);  // rows x: W[cl][x][y][:]
+  __syncthreads();
+  const DimPlan& dx = g.d[0];
+  // x: n3 columns of length n1 (element stride S)
+  fft_forward(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
+  const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vtab + (long long)y * n3, plane,
+                                     energy_only);
+  const double es = block_sum(e, red);
+  if (threadIdx.x == 0) epart[(long long)(c0 + cl) * n2 + y] = es;
+  if (energy_only) return;
+  __syncthreads();
+  fft_inverse(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
+  fft_inverse(g.d[2], 0, g.d[2].ns, buf, tw3, n1, g.d[0].ndiv, S, 1);  // z: n1 rows
+  plane_s2g(wc, plane, buf, S, n1, n3, g.d[2].ndiv);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreadsPlane, 3)
 k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
@@ -325,37 +364,16 @@ k_x_coulomb(const __grid_constant__ Geo g, const int4* __restrict__ couples, int
             int energy_only) {
   using C = cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int n1 = g.n1, n2 = g.n2, n3 = g.n3, S = g.S;
+  const int n1 = g.n1, n3 = g.n3, S = g.S;
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw1 = buf + n1 * S;
   C* tw3 = tw1 + n1;
   __shared__ double red[32];
   for (int i = threadIdx.x; i < n1; i += blockDim.x) tw1[i] = tw1g[i];
   for (int i = threadIdx.x; i < n3; i += blockDim.x) tw3[i] = tw3g[i];
-
-  const long long items = (long long)(c1 - c0) * n2;
-  const long long plane = (long long)n2 * n3;
-  for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-    const int cl = int(it / n2);
-    const int y = int(it - (long long)cl * n2);
-    if (couple_empty(couples[c0 + cl])) continue;
-    C* wc = W + (long long)cl * n1 * plane + (long long)y * n3;
-    __syncthreads();
-    plane_g2s(buf, S, wc, plane, n1, n3, g.d[2].ndiv);  // rows x: W[cl][x][y][:]
-    __syncthreads();
-    const DimPlan& dx = g.d[0];
-    // x: n3 columns of length n1 (element stride S)
-    fft_forward(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
-    const double e = x_last_coulomb_rt(dx.r[dx.ns - 1], buf, S, n1, n3, g.d[2].ndiv, vtab + (long long)y * n3,
-                                       plane, energy_only != 0);
-    const double es = block_sum(e, red);
-    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * n2 + y] = es;
-    if (energy_only) continue;
-    __syncthreads();
-    fft_inverse(dx, 0, dx.ns - 1, buf, tw1, n3, g.d[2].ndiv, 1, S);
-    fft_inverse(g.d[2], 0, g.d[2].ns, buf, tw3, n1, g.d[0].ndiv, S, 1);  // z: n1 rows
-    plane_s2g(wc, plane, buf, S, n1, n3, g.d[2].ndiv);
-  }
+  const long long items = (long long)(c1 - c0) * g.n2;
+  for (long long it = blockIdx.x; it < items; it += gridDim.x)
+    x_coulomb_item(g, couples, c0, W, vtab, tw1, tw3, epart, energy_only != 0, buf, red, it);
 }
 
 // ----------------------------------------------------------------------------------
@@ -694,22 +712,22 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
 constexpr int kThreadsGen = 256;
 constexpr int kGenRing = 2;
 
+// one tile of the generic accumulate pass: z-chunk zi, x-plane x, block pair `slot`; the dynamic
+// shared memory `smem_raw` holds the tiles, twiddles, accumulators, orbital tiles and couple table
 template <typename T>
-__global__ void __launch_bounds__(kThreadsGen)
-k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
-                const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
-                const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0, const cx<T>* __restrict__ W,
-                const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale, int grp, int phi_smem,
-                int cap_max) {
+__device__ __forceinline__ void acc_generic_item(const Geo& g, const T* __restrict__ orb,
+                                                 const int4* __restrict__ couples, int slot,
+                                                 const int* __restrict__ slot_couple_base,
+                                                 const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0,
+                                                 const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g,
+                                                 double* __restrict__ V, double vscale, int grp, int phi_smem,
+                                                 int cap_max, unsigned char* smem_raw, int zi, int x) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
   constexpr int PER = 16 / int(sizeof(C));
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = g.n1, n2 = g.n2, n3 = g.n3;
-  const int z0 = blockIdx.x * ZC;
+  const int z0 = zi * ZC;
   const int zcn = min(ZC, n3 - z0);
-  const int x = blockIdx.y;
-  const int slot = slot_list[blockIdx.z];
   const int pts = n2 * ZC;
   const int LN = grp * ZC;
   const int nloc_max = 2 * bsize;
@@ -832,6 +850,19 @@ k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const 
     for (int u = 0; u < GF; ++u)
       if (on[u]) V[off[u]] = old[u] + vscale * double(acc[i0f + u * blockDim.x]);
   }
+}
+
+
+template <typename T>
+__global__ void __launch_bounds__(kThreadsGen)
+k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
+                const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
+                const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0, const cx<T>* __restrict__ W,
+                const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale, int grp, int phi_smem,
+                int cap_max) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  acc_generic_item(g, orb, couples, slot_list[blockIdx.z], slot_couple_base, slot_blocks, bsize, n_orb, c0, W, tw2g, V,
+                   vscale, grp, phi_smem, cap_max, smem_raw, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 }  // namespace hfx

@@ -11,7 +11,7 @@ cudaError_t Passes<Real>::set_smem_limit(int bytes) {
                       (const void*)k_y_acc_dense<Real, 8, 2>, (const void*)k_y_acc_dense<Real, 8, 4>,
                       (const void*)k_y_acc_generic<Real>,      (const void*)k_fwd_z_rows<Real>,
                       (const void*)k_fwd_y_cols<Real>,         (const void*)k_x_cols<Real>,
-                      (const void*)k_inv_z_rows<Real>};
+                      (const void*)k_inv_z_rows<Real>,         (const void*)k_batch_persistent<Real>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -91,6 +91,17 @@ template <>
 void Passes<Real>::inv_z_rows(const Geo& g, int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1,
                               int rb, cx<Real>* W, const cx<Real>* tw3) {
   k_inv_z_rows<Real><<<grid, kThreadsPencil, smem, st>>>(g, couples, c0, c1, rb, W, tw3);
+}
+
+template <>
+void Passes<Real>::batch(int grid, size_t smem, cudaStream_t st, const BatchProblem<Real>* probs, const BatchTask* tasks,
+                         int ntasks, long long total_items, BatchQueue* queue, long long budget) {
+  k_batch_persistent<Real><<<grid, kThreadsBatch, smem, st>>>(probs, tasks, ntasks, total_items, queue, budget);
+}
+
+template <>
+cudaError_t Passes<Real>::batch_occupancy(size_t smem, int* blocks) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_batch_persistent<Real>, kThreadsBatch, smem);
 }
 
 template struct Passes<Real>;

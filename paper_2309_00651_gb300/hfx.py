@@ -24,10 +24,11 @@ KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
 HFX_ENERGY_ONLY = 0x1
 HFX_ACCUMULATE = 0x2
 HFX_ORBITALS_F32 = 0x4
+HFX_TEST_STALL = 0x100
 
 # every symbol include/hfx.h and include/hfx_ace.h declare
 EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply", "hfx_apply_batched",
-            "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
+            "hfx_apply_sequential", "hfx_set_wait_budget", "hfx_apply_noalloc", "hfx_sync_status", "hfx_set_tuning", "hfx_plan_stats", "hfx_profile_enable",
             "hfx_profile_read",
             "hfx_last_error", "hfx_destroy",
             "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
@@ -85,6 +86,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_apply_noalloc.restype = ctypes.c_int
     L.hfx_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HfxApplyArgs), i32, vp]
     L.hfx_apply_batched.restype = ctypes.c_int
+    L.hfx_apply_sequential.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(HfxApplyArgs), i32, vp]
+    L.hfx_apply_sequential.restype = ctypes.c_int
+    L.hfx_set_wait_budget.argtypes = [vp, i64]
+    L.hfx_set_wait_budget.restype = ctypes.c_int
     L.hfx_sync_status.argtypes = [vp, vp]
     L.hfx_sync_status.restype = ctypes.c_int
     L.hfx_set_tuning.argtypes = [vp, i32, sz, i32]
@@ -181,15 +186,31 @@ def hfx_apply_noalloc(ctx, orbitals: torch.Tensor, pairs: torch.Tensor, ex: torc
                                             int(flags), _ptr(ex), _ptr(vxphi), _stream_handle(stream)))
 
 
-def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) -> None:
-    """ctxs: list of contexts; args: list of (orbitals, pairs, ex, vxphi, flags)."""
+def _batch_args(ctxs, args):
     n = len(ctxs)
     carr = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
     aarr = (HfxApplyArgs * n)()
     for k, (orb, pairs, ex, v, flags) in enumerate(args):
         aarr[k] = HfxApplyArgs(_ptr(orb), int(orb.shape[0]), _ptr(pairs), int(pairs.shape[0]), int(flags), _ptr(ex),
                                _ptr(v))
+    return n, carr, aarr
+
+
+def hfx_apply_batched(ctxs, args, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """All problems in one persistent launch.  ctxs: list of contexts; args: list of
+    (orbitals, pairs, ex, vxphi, flags)."""
+    n, carr, aarr = _batch_args(ctxs, args)
     _check(load_library().hfx_apply_batched(carr, aarr, n, _stream_handle(stream)))
+
+
+def hfx_apply_sequential(ctxs, args, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """The same problems as one hfx_apply each, back to back on the stream."""
+    n, carr, aarr = _batch_args(ctxs, args)
+    _check(load_library().hfx_apply_sequential(carr, aarr, n, _stream_handle(stream)))
+
+
+def hfx_set_wait_budget(ctx, cycles: int) -> None:
+    _check(load_library().hfx_set_wait_budget(ctx, int(cycles)))
 
 
 def hfx_sync_status(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:

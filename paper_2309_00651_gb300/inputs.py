@@ -277,3 +277,26 @@ def complex_plane_wave_orbitals(kset: np.ndarray, L: float, n: int) -> np.ndarra
         arg = 2.0 * np.pi * (m[0] * p[:, None, None] + m[1] * p[None, :, None] + m[2] * p[None, None, :])
         out.append(np.exp(1j * arg) / np.sqrt(L ** 3))
     return np.array(out)
+
+
+def _make_workload_task(w: Workload):
+    return make_workload(w)
+
+
+def make_workloads_parallel(ws: List[Workload], procs: Optional[int] = None):
+    """make_workload for several workloads at once, one spawned process per host core (spawn, so
+    it is safe in a process that has initialised CUDA).  Every workload is built from its own
+    seed, so the arrays equal those of make_workload called one by one; returned in order."""
+    import multiprocessing as mp
+    import os
+    procs = procs or max(1, min(len(ws), len(os.sched_getaffinity(0))))
+    if procs == 1 or len(ws) == 1:
+        return [make_workload(w) for w in ws]
+    # largest first, so the longest jobs do not start last
+    order = sorted(range(len(ws)), key=lambda k: -ws[k].n_orb * ws[k].n ** 3)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_make_workload_task, [ws[k] for k in order], chunksize=1)
+    out = [None] * len(ws)
+    for k, r in zip(order, res):
+        out[k] = r
+    return out

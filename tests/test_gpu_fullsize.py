@@ -6,8 +6,6 @@
   seeded sample of pairs, which the GPU evaluates as its own pair list.  Properties that hold at
   any size are checked on the full result: the homogeneity identity E_x = 1/2 (Omega/N) sum
   <phi_i, (V_x phi)_i>, and agreement between the FP32 and FP64 paths.
-* The uneven batch (independent water boxes of 32..256 orbitals on 48^3..96^3 grids) through
-  hfx_apply_batched: every problem checked on a sampled orbital row and on homogeneity.
 """
 import numpy as np
 import pytest
@@ -65,38 +63,6 @@ def test_full_workload_sampled(name, rows, n_sample):
     # the two precision paths agree to the FP32 tolerance
     assert abs(results["fp32"][0] - results["fp64"][0]) <= 1e-6 * abs(results["fp64"][0])
     assert rel(results["fp32"][1], results["fp64"][1]) <= 1e-6
-
-
-def test_uneven_batch_through_apply_batched():
-    from paper_2309_00651_gb300 import hfx
-    ws = I.batched_workloads()
-    # the smallest, the largest and three in between keep the oracle checks to seconds
-    order = np.argsort([w.n_orb * w.n ** 3 for w in ws])
-    pick = [ws[i] for i in (order[0], order[6], order[12], order[18], order[-1])]
-    ctxs, args, keep, data = [], [], [], []
-    for w in pick:
-        phi, pairs, _ = I.make_workload(w)
-        ex = hfx.Exchange(w.lattice, w.grid, precision="fp32")
-        ex.ensure_workspace(w.n_orb, len(pairs))
-        phi_d = torch.from_numpy(phi).cuda()
-        pairs_d = torch.from_numpy(pairs).cuda()
-        E = torch.zeros(1, dtype=torch.float64, device="cuda")
-        V = torch.empty_like(phi_d)
-        ctxs.append(ex.ctx)
-        args.append((phi_d, pairs_d, E, V, 0))
-        keep.append(ex)
-        data.append((w, phi, pairs))
-    hfx.hfx_apply_batched(ctxs, args)
-    torch.cuda.synchronize()
-    for (w, phi, pairs), (phi_d, _, E, V, _), ex in zip(data, args, keep):
-        ex.sync_status()
-        N = w.n ** 3
-        hom = 0.5 * (w.volume / N) * float(torch.sum(phi_d * V).item())
-        assert abs(hom - E.item()) <= 1e-5 * abs(E.item())
-        k = w.n_orb // 3
-        V_row = O.exchange_rows(phi, pairs, [k], w.lattice)[0]
-        assert rel(V[k].cpu().numpy(), V_row) <= 1e-6
-        ex.close()
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
