@@ -145,7 +145,7 @@ def test_flags_in_a_batch(precision):
     (Eb, Vb), (Es_, Vs_) = outs
     for k in range(len(ws)):
         assert abs(Eb[k].item() - Es_[k].item()) <= tol * max(abs(Es_[k].item()), 1e-300), k
-        if k != 1:
+        if k in (0, 2):  # 1: energy only, 3: empty list (both checked exactly below)
             assert float(torch.linalg.norm(Vb[k] - Vs_[k]) / torch.linalg.norm(Vs_[k])) <= tol, k
     assert Eb[3].item() == 0.0 and float(Vb[3].abs().max()) == 0.0
     assert bool(torch.all(Vb[1] == 0.25))  # energy only leaves V alone
