@@ -1049,12 +1049,15 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
     P.tw3 = (const cx<T>*)c->d_tw[2];
     P.slot_couple_base = S->d_slot_couple_base;
     P.slot_blocks = S->d_slot_blocks;
+    P.twct = (const cx<T>*)c->d_twct;
+    P.ct_n = (std::is_same<T, float>::value && c->ct && (c->grid[0] == 48 || c->grid[0] == 64 || c->grid[0] == 72 ||
+                                                        c->grid[0] == 96)) ? c->grid[0] : 0;
     P.err = c->d_err;
     P.vscale = -c->alpha / (double)c->N;
     P.escale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
     P.n_orb = a.n_orb;
     P.bsize = S->b;
-    P.grp = c->gen_grp;
+    P.grp = c->gen_grp;  // refitted below to the batch's shared-memory footprint
     P.phi_smem = c->gen_phi;
     P.cap_max = gen_cap_max(c);
     P.total_couples = (int)S->max_total_couples;
@@ -1085,9 +1088,27 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
     }
     add(kTaskEnergy, 1, 0, 0, 0);
     chains.push_back(ch);
-    smem = std::max({smem, smem_fwd(c), smem_x(c), eo ? (size_t)0 : smem_acc(c)});
+    smem = std::max({smem, smem_fwd(c), smem_x(c)});
   }
   if (probs.empty()) return HFX_OK;
+  // the accumulate tiles take at most the planes' footprint (largest couple group and orbital
+  // tiles on chip that fit), so they do not lower the launch's resident blocks per SM
+  {
+    int p = 0;
+    for (int32_t k = 0; k < n; ++k) {
+      if (args[k].n_pairs == 0) continue;
+      hfx_ctx* c = ctxs[k];
+      BatchProblem<T>& P = probs[p++];
+      if (P.energy_only) continue;
+      bool fit = false;
+      for (int grp : {4, 2, 1}) {
+        for (int phi : {1, 0})
+          if (smem_acc_cfg(c, grp, phi) <= smem) { P.grp = grp; P.phi_smem = phi; fit = true; break; }
+        if (fit) break;
+      }
+      if (!fit) { P.grp = 1; P.phi_smem = 0; smem = std::max(smem, smem_acc_cfg(c, 1, 0)); }
+    }
+  }
   if (smem + 512 > (size_t)lead->max_smem)
     return fail(HFX_ERR_UNSUPPORTED_GRID, "a batch tile needs %zu bytes of shared memory (limit %d)", smem, lead->max_smem);
   // interleave the chains level by level; each task waits for its predecessor in its own chain

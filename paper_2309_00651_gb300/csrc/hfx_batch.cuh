@@ -19,6 +19,9 @@
 // the problem's error word and an abort flag, and every block returns at its next item or wait;
 // the results of that call are then undefined and hfx_sync_status reports HFX_ERR_TIMEOUT.
 #pragma once
+#include <type_traits>
+
+#include "hfx_ct.cuh"
 #include "hfx_kernels.cuh"
 
 namespace hfx {
@@ -40,10 +43,43 @@ struct BatchProblem {
   const cx<T>* tw3;
   const int* slot_couple_base;
   const int2* slot_blocks;
+  const cx<T>* twct;            // per-stage twiddles of the compile-time passes (ct_n > 0)
   int* err;                     // the problem's context error word
   double vscale, escale;
   int n_orb, bsize, grp, phi_smem, cap_max, total_couples, accumulate, energy_only;
+  int ct_n;                     // cubic FP32 edge with compile-time forward and x passes, else 0
 };
+
+// forward / x item of an FP32 problem through the compile-time passes of its edge; false when the
+// problem has none (the runtime-geometry item runs instead)
+template <typename T, int N>
+__device__ __forceinline__ bool ct_item_n(const BatchProblem<T>& P, int kind, int a0, long long local,
+                                          unsigned char* smem_raw, float (*redf)[32], int par) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (P.ct_n != N) return false;
+    constexpr StagePlan SP = ct::Plan<N>::p;
+    float2* buf = reinterpret_cast<float2*>(smem_raw);
+    float2* tw = buf + N * (N + 1);
+    for (int i = threadIdx.x; i < SP.twtotal; i += blockDim.x) tw[i] = P.twct[i];
+    if (kind == kTaskFwd)
+      ct::fwd_yz_ct_item<float, N>(P.orb, P.g.N, P.couples, a0, P.W, buf, tw, (int)local);
+    else
+      ct::x_coulomb_ct_item<float, N>(P.couples, a0, P.W, P.vtab, P.epart, P.energy_only, buf, tw, redf, par,
+                                      (int)local);
+    return true;
+  } else {
+    return false;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool ct_item(const BatchProblem<T>& P, int kind, int a0, long long local,
+                                        unsigned char* smem_raw, float (*redf)[32], int par) {
+  return ct_item_n<T, 48>(P, kind, a0, local, smem_raw, redf, par) ||
+         ct_item_n<T, 64>(P, kind, a0, local, smem_raw, redf, par) ||
+         ct_item_n<T, 72>(P, kind, a0, local, smem_raw, redf, par) ||
+         ct_item_n<T, 96>(P, kind, a0, local, smem_raw, redf, par);
+}
 
 struct BatchTask {
   long long first;  // number of this task's first item
@@ -83,6 +119,8 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
   __shared__ long long s_item;
   __shared__ int s_task;
   __shared__ double red[32];
+  __shared__ float redf[2][32];  // warp partials of the compile-time x items, alternating
+  int par = 0;
   int* done = reinterpret_cast<int*>(queue + 1);
   for (;;) {
     if (threadIdx.x == 0) {
@@ -124,7 +162,10 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
     const BatchProblem<T>& P = probs[tk.prob];
     const long long local = s_item - tk.first;
     const Geo& g = P.g;
-    if (tk.kind == kTaskFwd) {
+    if ((tk.kind == kTaskFwd || tk.kind == kTaskX) && P.ct_n > 0 &&
+        ct_item(P, tk.kind, tk.a0, local, smem_raw, redf, par)) {
+      if (tk.kind == kTaskX) par ^= 1;
+    } else if (tk.kind == kTaskFwd) {
       C* buf = reinterpret_cast<C*>(smem_raw);
       C* tw2 = buf + g.n2 * g.S;
       C* tw3 = tw2 + g.n2;

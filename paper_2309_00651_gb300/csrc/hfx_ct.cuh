@@ -69,7 +69,8 @@ __device__ __forceinline__ void stages(C* buf, const C* tw) {
 }
 
 // forward stage 0 of column lines reading its input from global memory: line l's element e at
-// src[l + e*GES]; results go to buf[l*SLS + e*SES].  A barrier follows.
+// src[l + e*GES]; results go to buf[l*SLS + e*SES].  A barrier follows.  The loads go through L2
+// only (read once; in a persistent launch another block of the same launch may have written them).
 template <int R, int M, int LINES, int GES, int SLS, int SES, int N, int NT, typename C>
 __device__ __forceinline__ void stage_fwd_g2s(const C* __restrict__ src, C* __restrict__ buf,
                                               const C* __restrict__ twt) {
@@ -85,7 +86,7 @@ __device__ __forceinline__ void stage_fwd_g2s(const C* __restrict__ src, C* __re
     const int e0 = (q - j1) * R + j1;
     C v[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) v[k] = __ldg(src + line + (e0 + k * M) * GES);
+    for (int k = 0; k < R; ++k) v[k] = __ldcg(src + line + (e0 + k * M) * GES);
     Dft<R, -1, C>::run(v);
     if constexpr (M > 1) {
       const C* t = twt + j1 * R;
@@ -183,150 +184,172 @@ constexpr int kUnroll = 4;
 // ----------------------------------------------------------------------------------
 // pass 1: pair product + forward FFT along z and y of one x-plane
 // ----------------------------------------------------------------------------------
+// one item (couple cl = it / N, x-plane x = it mod N); buf holds the padded plane, tw the per-stage
+// twiddles in shared memory (loaded before the caller's first barrier)
+template <typename T, int N>
+__device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long long Ntot,
+                                               const int4* __restrict__ couples, int c0, cx<T>* __restrict__ W,
+                                               cx<T>* buf, const cx<T>* tw, int it) {
+  using C = cx<T>;
+  using T2 = typename Two<T>::type;
+  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr StagePlan P = Plan<N>::p;
+  const int cl = it / N;
+  const int x = it - cl * N;
+  const int4 cp = couples[c0 + cl];
+  if (couple_empty(cp)) return;
+  const long long off = (long long)x * PLANE;
+  const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
+  const T2* pa1 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.x : 0) * Ntot + off);
+  const T2* pa2 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.y : 0) * Ntot + off);
+  const T2* pb1 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.z : 0) * Ntot + off);
+  const T2* pb2 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.w : 0) * Ntot + off);
+  __syncthreads();  // the previous item's store is done with buf (and the table is loaded)
+  for (int i0 = threadIdx.x; i0 < NV; i0 += kUnroll * NT) {
+    T2 a1[kUnroll], a2[kUnroll], b1[kUnroll], b2[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * NT;
+      const bool in = (NV % (kUnroll * NT) == 0) || i < NV;
+      const T2 zero = {};
+      a1[u] = (in && hasa) ? __ldg(pa1 + i) : zero;
+      a2[u] = (in && hasa) ? __ldg(pa2 + i) : zero;
+      b1[u] = (in && hasb) ? __ldg(pb1 + i) : zero;
+      b2[u] = (in && hasb) ? __ldg(pb2 + i) : zero;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int i = i0 + u * NT;
+      if ((NV % (kUnroll * NT) == 0) || i < NV) {
+        const int p = 2 * i;
+        const int y = p / N, z = p - y * N;  // N even: both points in row y
+        buf[y * S + z] = mk<C>(a1[u].x * a2[u].x, b1[u].x * b2[u].x);
+        buf[y * S + z + 1] = mk<C>(a1[u].y * a2[u].y, b1[u].y * b2[u].y);
+      }
+    }
+  }
+  __syncthreads();
+  stages<N, false, 0, P.ns, N, S, 1, NT>(buf, tw);      // z: N rows
+  stages<N, false, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // y: N columns, all but the last stage
+  // last y stage straight to W[cl][x][y][z] (consecutive threads on consecutive z)
+  stage_fwd_last_s2g<P.r[P.ns - 1], N, 1, S, N, N, NT>(buf, W + ((long long)cl * N + x) * PLANE);
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreadsPlane, 3)
 k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples, int c0, int c1,
             cx<T>* __restrict__ W, const cx<T>* __restrict__ twg) {
   using C = cx<T>;
-  using T2 = typename Two<T>::type;
-  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr int S = N + 1;
   constexpr StagePlan P = Plan<N>::p;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
-  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
-
+  for (int i = threadIdx.x; i < P.twtotal; i += kThreadsPlane) tw[i] = twg[i];
   const int items = (c1 - c0) * N;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
-    const int cl = it / N;
-    const int x = it - cl * N;
-    const int4 cp = couples[c0 + cl];
-    if (couple_empty(cp)) continue;
-    const long long off = (long long)x * PLANE;
-    const bool hasa = cp.x >= 0, hasb = cp.z >= 0;
-    const T2* pa1 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.x : 0) * Ntot + off);
-    const T2* pa2 = reinterpret_cast<const T2*>(orb + (long long)(hasa ? cp.y : 0) * Ntot + off);
-    const T2* pb1 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.z : 0) * Ntot + off);
-    const T2* pb2 = reinterpret_cast<const T2*>(orb + (long long)(hasb ? cp.w : 0) * Ntot + off);
-    __syncthreads();  // the previous item's store is done with buf (and the table is loaded)
-    for (int i0 = threadIdx.x; i0 < NV; i0 += kUnroll * NT) {
-      T2 a1[kUnroll], a2[kUnroll], b1[kUnroll], b2[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * NT;
-        const bool in = (NV % (kUnroll * NT) == 0) || i < NV;
-        const T2 zero = {};
-        a1[u] = (in && hasa) ? __ldg(pa1 + i) : zero;
-        a2[u] = (in && hasa) ? __ldg(pa2 + i) : zero;
-        b1[u] = (in && hasb) ? __ldg(pb1 + i) : zero;
-        b2[u] = (in && hasb) ? __ldg(pb2 + i) : zero;
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const int i = i0 + u * NT;
-        if ((NV % (kUnroll * NT) == 0) || i < NV) {
-          const int p = 2 * i;
-          const int y = p / N, z = p - y * N;  // N even: both points in row y
-          buf[y * S + z] = mk<C>(a1[u].x * a2[u].x, b1[u].x * b2[u].x);
-          buf[y * S + z + 1] = mk<C>(a1[u].y * a2[u].y, b1[u].y * b2[u].y);
-        }
-      }
-    }
-    __syncthreads();
-    stages<N, false, 0, P.ns, N, S, 1, NT>(buf, tw);      // z: N rows
-    stages<N, false, 0, P.ns - 1, N, 1, S, NT>(buf, tw);  // y: N columns, all but the last stage
-    // last y stage straight to W[cl][x][y][z] (consecutive threads on consecutive z)
-    stage_fwd_last_s2g<P.r[P.ns - 1], N, 1, S, N, N, NT>(buf, W + ((long long)cl * N + x) * PLANE);
-  }
+  for (int it = blockIdx.x; it < items; it += gridDim.x) fwd_yz_ct_item<T, N>(orb, Ntot, couples, c0, W, buf, tw, it);
 }
 
 // ----------------------------------------------------------------------------------
 // pass 2: forward FFT along x, Coulomb multiply + energy, inverse along x and z
 // ----------------------------------------------------------------------------------
+// one item (couple cl = it / N, y-plane y = it mod N); red: [2][32] floats of shared memory used
+// alternately (par) by consecutive items of a block
+template <typename T, int N>
+__device__ __forceinline__ void x_coulomb_ct_item(const int4* __restrict__ couples, int c0, cx<T>* __restrict__ W,
+                                                  const T* __restrict__ vtab, double* __restrict__ epart,
+                                                  int energy_only, cx<T>* buf, const cx<T>* tw, float (*red)[32],
+                                                  int par, int it) {
+  using C = cx<T>;
+  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane;
+  constexpr StagePlan P = Plan<N>::p;
+  constexpr int RL = P.r[P.ns - 1];  // last forward stage (m = 1)
+  static_assert(P.ns >= 2, "compile-time x pass needs at least two stages");
+  const int cl = it / N;
+  const int y = it - cl * N;
+  if (couple_empty(couples[c0 + cl])) return;
+  C* wc = W + (long long)cl * N * PLANE + (long long)y * N;
+  __syncthreads();
+  // x stage 0 straight from W[cl][x][y][z] (line z, element x at stride PLANE)
+  stage_fwd_g2s<P.r[0], P.m[0], N, PLANE, 1, S, N, NT>(wc, buf, tw + P.twoff[0]);
+  stages<N, false, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // remaining x stages but the last
+  // last forward x stage (no twiddles) + Coulomb + energy + first inverse x stage
+  // the plane's energy partial in FP32 (a few terms per thread, then a tree over the block),
+  // widened once; the partials of all planes and couples are summed in FP64
+  T e_acc = T(0);
+  {
+    constexpr int TOTAL = N * (N / RL);
+    const T* vy = vtab + (long long)y * N;
+#pragma unroll 1
+    for (int id = threadIdx.x; id < TOTAL; id += NT) {
+      const int q = id / N, z = id - q * N;
+      C* p = buf + q * RL * S + z;
+      T vg[RL];
+#pragma unroll
+      for (int k = 0; k < RL; ++k) vg[k] = __ldg(vy + (long long)(q * RL + k) * PLANE + z);
+      C v[RL];
+#pragma unroll
+      for (int k = 0; k < RL; ++k) v[k] = p[k * S];
+      Dft<RL, -1, C>::run(v);
+      T e = T(0);
+#pragma unroll
+      for (int k = 0; k < RL; ++k) {
+        e += vg[k] * (v[k].x * v[k].x + v[k].y * v[k].y);
+        v[k].x *= vg[k];
+        v[k].y *= vg[k];
+      }
+      e_acc += e;
+      if (!energy_only) {
+        Dft<RL, 1, C>::run(v);
+#pragma unroll
+        for (int k = 0; k < RL; ++k) p[k * S] = v[k];
+      }
+    }
+  }
+  static_assert(sizeof(T) == 4, "compile-time passes are FP32");
+  // block sum without barriers of its own: a shuffle tree per warp, the warp partials to
+  // red[par] now, and warp 0 adds them (a second tree) after the barrier that the inverse
+  // stages need anyway
+  {
+    float v = e_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[par][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    constexpr int NW = (NT + 31) / 32;
+    float r = threadIdx.x < NW ? red[par][threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = widen_exact(r);
+  }
+  if (energy_only) return;
+  // inverse transforms along different axes commute: z first (rows), then the remaining x
+  // stages, the last of which writes W directly
+  stages<N, true, 0, P.ns, N, S, 1, NT>(buf, tw);      // z inverse: N rows
+  stages<N, true, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // x inverse stages ns-2 .. 1
+  stage_inv_s2g<P.r[0], P.m[0], N, 1, S, PLANE, N, NT>(buf, wc, tw + P.twoff[0]);
+}
+
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreadsPlane, 4)
 k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
                const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only) {
   using C = cx<T>;
-  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr int S = N + 1;
   constexpr StagePlan P = Plan<N>::p;
-  constexpr int RL = P.r[P.ns - 1];  // last forward stage (m = 1)
-  static_assert(P.ns >= 2, "compile-time x pass needs at least two stages");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
   __shared__ float red[2][32];  // warp partials of the plane energy, double-buffered by item parity
-  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
-
+  for (int i = threadIdx.x; i < P.twtotal; i += kThreadsPlane) tw[i] = twg[i];
   int par = 0;
   const int items = (c1 - c0) * N;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
-    const int cl = it / N;
-    const int y = it - cl * N;
-    if (couple_empty(couples[c0 + cl])) continue;
-    C* wc = W + (long long)cl * N * PLANE + (long long)y * N;
-    __syncthreads();
-    // x stage 0 straight from W[cl][x][y][z] (line z, element x at stride PLANE)
-    stage_fwd_g2s<P.r[0], P.m[0], N, PLANE, 1, S, N, NT>(wc, buf, tw + P.twoff[0]);
-    stages<N, false, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // remaining x stages but the last
-    // last forward x stage (no twiddles) + Coulomb + energy + first inverse x stage
-    // the plane's energy partial in FP32 (a few terms per thread, then a tree over the block),
-    // widened once; the partials of all planes and couples are summed in FP64
-    T e_acc = T(0);
-    {
-      constexpr int TOTAL = N * (N / RL);
-      const T* vy = vtab + (long long)y * N;
-#pragma unroll 1
-      for (int id = threadIdx.x; id < TOTAL; id += NT) {
-        const int q = id / N, z = id - q * N;
-        C* p = buf + q * RL * S + z;
-        T vg[RL];
-#pragma unroll
-        for (int k = 0; k < RL; ++k) vg[k] = __ldg(vy + (long long)(q * RL + k) * PLANE + z);
-        C v[RL];
-#pragma unroll
-        for (int k = 0; k < RL; ++k) v[k] = p[k * S];
-        Dft<RL, -1, C>::run(v);
-        T e = T(0);
-#pragma unroll
-        for (int k = 0; k < RL; ++k) {
-          e += vg[k] * (v[k].x * v[k].x + v[k].y * v[k].y);
-          v[k].x *= vg[k];
-          v[k].y *= vg[k];
-        }
-        e_acc += e;
-        if (!energy_only) {
-          Dft<RL, 1, C>::run(v);
-#pragma unroll
-          for (int k = 0; k < RL; ++k) p[k * S] = v[k];
-        }
-      }
-    }
-    static_assert(sizeof(T) == 4, "compile-time passes are FP32");
-    // block sum without barriers of its own: a shuffle tree per warp, the warp partials to
-    // red[par] now, and warp 0 adds them (a second tree) after the barrier that the inverse
-    // stages need anyway
-    {
-      float v = e_acc;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[par][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      constexpr int NW = (NT + 31) / 32;
-      float r = threadIdx.x < NW ? red[par][threadIdx.x] : 0.f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
-      if (threadIdx.x == 0) epart[(long long)(c0 + cl) * N + y] = widen_exact(r);
-    }
+    if (couple_empty(couples[c0 + it / N])) continue;
+    x_coulomb_ct_item<T, N>(couples, c0, W, vtab, epart, energy_only, buf, tw, red, par, it);
     par ^= 1;
-    if (energy_only) continue;
-    // inverse transforms along different axes commute: z first (rows), then the remaining x
-    // stages, the last of which writes W directly
-    stages<N, true, 0, P.ns, N, S, 1, NT>(buf, tw);      // z inverse: N rows
-    stages<N, true, 1, P.ns - 1, N, 1, S, NT>(buf, tw);  // x inverse stages ns-2 .. 1
-    stage_inv_s2g<P.r[0], P.m[0], N, 1, S, PLANE, N, NT>(buf, wc, tw + P.twoff[0]);
   }
 }
 
