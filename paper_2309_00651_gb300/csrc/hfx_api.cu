@@ -1109,7 +1109,7 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
       if (!fit) { P.grp = 1; P.phi_smem = 0; smem = std::max(smem, smem_acc_cfg(c, 1, 0)); }
     }
   }
-  if (smem + 512 > (size_t)lead->max_smem)
+  if (smem + 1024 > (size_t)lead->max_smem)  // the persistent kernel has 528 bytes of static shared memory
     return fail(HFX_ERR_UNSUPPORTED_GRID, "a batch tile needs %zu bytes of shared memory (limit %d)", smem, lead->max_smem);
   // interleave the chains level by level; each task waits for its predecessor in its own chain
   std::vector<BatchTask> tasks;

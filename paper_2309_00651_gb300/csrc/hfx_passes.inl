@@ -13,7 +13,13 @@ cudaError_t Passes<Real>::set_smem_limit(int bytes) {
                       (const void*)k_fwd_y_cols<Real>,         (const void*)k_x_cols<Real>,
                       (const void*)k_inv_z_rows<Real>,         (const void*)k_batch_persistent<Real>};
   for (const void* k : ks) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // `bytes` leaves 512 bytes of the per-block limit for static shared memory; a kernel with
+    // more static shared memory gets correspondingly less dynamic memory
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, k);
+    if (e != cudaSuccess) return e;
+    const int lim = fa.sharedSizeBytes > 512 ? bytes + 512 - (int)fa.sharedSizeBytes : bytes;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
