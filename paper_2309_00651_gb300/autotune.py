@@ -98,3 +98,58 @@ def tune(exch: Exchange, phi: torch.Tensor, pairs: torch.Tensor,
         table[key] = {"setting": best["setting"], "ms": best["ms"]}
         _store(path, table)
     return dict(result, cached=False)
+
+
+BATCH_BUDGETS = (1 << 30, 512 << 20, 256 << 20, 2 << 30)
+
+
+def tune_batch(exchanges, run_persistent, run_sequential, n_orbs, n_pairs,
+               budgets: Iterable[int] = BATCH_BUDGETS, steps: int = 2, timer=None) -> dict:
+    """Pick the pair-batch size (per-context transform budget) of the uneven batch's persistent
+    launch, then keep the persistent form or the one-call-per-problem form, whichever is faster.
+
+    exchanges: the Exchange of every problem; run_persistent / run_sequential: callables that
+    run the whole batch once in that form; n_orbs, n_pairs: per problem (for the workspaces).
+    Returns {"setting": {"batch_bytes", "mode"}, "ms": ..., "trials": [...]} with the setting
+    applied to every context."""
+    timer = timer or _time_batch
+
+    def apply(budget):
+        for ex, no, npair in zip(exchanges, n_orbs, n_pairs):
+            ex.set_tuning(8, budget, True)
+            ex.ensure_workspace(no, npair)
+
+    trials = []
+    for b in budgets:
+        try:
+            apply(b)
+            ms = timer(run_persistent, steps)
+        except Exception as err:  # a budget whose workspaces do not fit is skipped
+            trials.append({"setting": {"batch_bytes": b, "mode": "persistent"}, "error": str(err)})
+            continue
+        trials.append({"setting": {"batch_bytes": b, "mode": "persistent"}, "ms": ms})
+    ok = [t for t in trials if "ms" in t]
+    if not ok:
+        raise RuntimeError(f"no batch setting ran: {trials}")
+    best = min(ok, key=lambda t: t["ms"])
+    apply(best["setting"]["batch_bytes"])
+    try:
+        ms_seq = timer(run_sequential, steps)
+        trials.append({"setting": {"batch_bytes": best["setting"]["batch_bytes"], "mode": "sequential"}, "ms": ms_seq})
+        if ms_seq < best["ms"]:
+            best = trials[-1]
+    except Exception as err:
+        trials.append({"setting": {"mode": "sequential"}, "error": str(err)})
+    return {"setting": best["setting"], "ms": best["ms"], "trials": trials}
+
+
+def _time_batch(run, steps: int) -> float:
+    run()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        run()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps

@@ -69,3 +69,46 @@ def test_nothing_runs_raises(monkeypatch, tmp_path):
     times = {(8, 1 << 30, True): None, (8, 1 << 29, True): None, (4, 1 << 30, False): None}
     with pytest.raises(RuntimeError):
         run(monkeypatch, tmp_path, times)
+
+
+class FakeBatchExchange:
+    def __init__(self, log):
+        self.log = log
+
+    def set_tuning(self, block, batch_bytes, pipeline):
+        self.log.append(("tune", batch_bytes))
+
+    def ensure_workspace(self, n_orb, n_pairs):
+        self.log.append(("ws", n_orb, n_pairs))
+
+
+def test_batch_tuner_picks_budget_then_form():
+    """The batch tuner times the persistent launch per transform budget (a budget that raises is
+    skipped), applies the fastest to every context with its workspace, then keeps the
+    one-call-per-problem form only if that is faster."""
+    log = []
+    exs = [FakeBatchExchange(log), FakeBatchExchange(log)]
+    current = {"b": None}
+    orig = exs[0].set_tuning
+
+    def set_tuning(block, batch_bytes, pipeline):
+        current["b"] = batch_bytes
+        orig(block, batch_bytes, pipeline)
+    exs[0].set_tuning = set_tuning
+    ms_of = {1 << 30: 9.0, 512 << 20: 7.0, 256 << 20: None, 2 << 30: 8.0}
+
+    def timer(run, steps):
+        return run()
+
+    def persistent():
+        ms = ms_of[current["b"]]
+        if ms is None:
+            raise RuntimeError("does not fit")
+        return ms
+
+    res = T.tune_batch(exs, persistent, lambda: 7.5, [10, 20], [55, 210], timer=timer)
+    assert res["setting"] == {"batch_bytes": 512 << 20, "mode": "persistent"} and res["ms"] == 7.0
+    assert any("error" in t for t in res["trials"])
+    assert log[-4:] == [("tune", 512 << 20), ("ws", 10, 55), ("tune", 512 << 20), ("ws", 20, 210)]
+    res2 = T.tune_batch(exs, persistent, lambda: 6.0, [10, 20], [55, 210], timer=timer)
+    assert res2["setting"]["mode"] == "sequential" and res2["ms"] == 6.0
