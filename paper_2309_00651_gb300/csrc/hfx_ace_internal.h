@@ -53,6 +53,15 @@ long long lmul_ldt(bool fp32, int m);
 // out[i][p] (+)= sum_k T[i][k] Y[k][p] with T given transposed, tt[k][i] (compute type)
 cudaError_t lmul(bool fp32, const void* tt, long long ldt, int m, int k, bool lower, const double* y, long long ldy,
                  long long n, bool accumulate, double* out, long long ldo, int sm_count, cudaStream_t st);
+// The same two contractions on the tensor cores (hfx_ace_tc.cu; FP32 contexts): TF32 x 3 split
+// products, FP32 accumulation in TMEM.  *_ok tells whether the operands meet their alignment
+// and size conditions; a device-side wait that runs out sets the timeout bit of *err.
+bool gram_tc_ok(const double* x, long long ldx, const double* y, long long ldy, long long K, const GramPlan& plan);
+cudaError_t gram_tc(bool absval, const double* x, long long ldx, int nx, const double* y, long long ldy, int ny,
+                    long long K, const GramPlan& plan, double* partials, int* err, int sm_count, cudaStream_t st);
+bool lmul_tc_ok(const void* tt, int m, const double* y, double* out);
+cudaError_t lmul_tc(const float* tt, long long ldt, int m, int k, const double* y, long long ldy, long long n,
+                    bool accumulate, double* out, long long ldo, int* err, int sm_count, cudaStream_t st);
 // L (row-major n x n, zeros above the diagonal) with L L^T = -(M + M^T)/2; `work` holds
 // n*n + n doubles when the matrix does not fit in shared memory
 cudaError_t cholesky_neg_sym(const double* m, long long ldm, int n, double* l, double* work, int* err,

@@ -239,6 +239,9 @@ struct hfx_ctx {
   void* d_batch = nullptr;
   size_t batch_bytes = 0;
   long long wait_budget = 1LL << 34;  // clock cycles a device-side wait may take (~8 s)
+  // FP32 contexts: the ACE contractions on the tensor cores (tcgen05, TF32 x 3); HFX_NO_TC=1
+  // keeps them on the FP32 SIMT kernels
+  bool ace_tc = true;
   // optional per-pass device timing (hfx_profile_enable)
   bool prof_on = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -496,6 +499,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (const char* s = std::getenv("HFX_BLOCK")) c->bsize = std::max(1, std::min(32, atoi(s)));
   if (const char* s = std::getenv("HFX_BATCH_MB")) c->transform_budget = (size_t)std::max(1, atoi(s)) << 20;
   if (const char* s = std::getenv("HFX_PIPELINE")) c->pipeline = atoi(s) != 0;
+  if (const char* s = std::getenv("HFX_NO_TC")) c->ace_tc = atoi(s) == 0;
 
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
@@ -1486,6 +1490,22 @@ hfx_status ace_check_ws(const void* ws, size_t have, size_t need) {
     if (e_ != cudaSuccess) return fail(HFX_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_)); \
   } while (0)
 
+// the grid contractions of the ACE rows: tensor cores on FP32 contexts when the operands allow,
+// the SIMT kernels otherwise (FP64 contexts always)
+static cudaError_t ace_gram(hfx_ctx* c, bool fp32, bool absval, const double* x, long long ldx, int nx, const double* y,
+                            long long ldy, int ny, long long K, const ace::GramPlan& gp, double* part, cudaStream_t st) {
+  if (fp32 && c->ace_tc && ace::gram_tc_ok(x, ldx, y, ldy, K, gp))
+    return ace::gram_tc(absval, x, ldx, nx, y, ldy, ny, K, gp, part, c->d_err, c->sm_count, st);
+  return ace::gram(fp32, absval, x, ldx, nx, y, ldy, ny, K, gp, part, c->sm_count, st);
+}
+static cudaError_t ace_lmul(hfx_ctx* c, bool fp32, const void* tt, long long ldt, int m, int k, bool lower,
+                            const double* y, long long ldy, long long n, bool accumulate, double* out, long long ldo,
+                            cudaStream_t st) {
+  if (fp32 && c->ace_tc && ace::lmul_tc_ok(tt, m, y, out))
+    return ace::lmul_tc((const float*)tt, ldt, m, k, y, ldy, n, accumulate, out, ldo, c->d_err, c->sm_count, st);
+  return ace::lmul(fp32, tt, ldt, m, k, lower, y, ldy, n, accumulate, out, ldo, c->sm_count, st);
+}
+
 extern "C" size_t hfx_ace_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int32_t n_psi) {
   if (!c || n_orb < 1 || n_psi < 0) return 0;
   size_t need = std::max(ace_ws_build(c, n_orb).total, ace_ws_screen(c, n_orb).total);
@@ -1515,7 +1535,7 @@ extern "C" hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const do
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
   // M_kl = <psi_k | W_l> = (Omega/N) sum_p psi_k(p) W_l(p)
   cudaEvent_t t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::gram(fp32, false, orbitals, N, n_orb, w, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace_gram(c, fp32, false, orbitals, N, n_orb, w, N, n_orb, N, gp, part, st));
   prof_close(c, kProfAceGram, t0, st);
   t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, M, n_orb, nullptr, 0, st));
@@ -1525,7 +1545,7 @@ extern "C" hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const do
   HFX_ACE_TRY(ace::tri_inverse(fp32, L, n_orb, Linvt, ldt, c->max_smem, st));
   prof_close(c, kProfAceSmall, t0, st);
   t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::lmul(fp32, Linvt, ldt, n_orb, n_orb, true, w, N, N, false, p, N, c->sm_count, st));
+  HFX_ACE_TRY(ace_lmul(c, fp32, Linvt, ldt, n_orb, n_orb, true, w, N, N, false, p, N, st));
   prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
 }
@@ -1550,14 +1570,14 @@ extern "C" hfx_status hfx_ace_apply(hfx_ctx* c, const double* p, int32_t n_orb, 
   const ace::GramPlan gp = ace::gram_plan(n_psi, n_orb, N, c->sm_count);
   // X[i][k] = -<psi_i | P_k> (held transposed), then out_i (+)= sum_k X[i][k] P_k
   cudaEvent_t t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::gram(fp32, false, psi, N, n_psi, p, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace_gram(c, fp32, false, psi, N, n_psi, p, N, n_orb, N, gp, part, st));
   prof_close(c, kProfAceGram, t0, st);
   t0 = prof_mark(c, st);
   const long long ldt = ace::lmul_ldt(fp32, n_psi);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_psi, n_orb, -c->omega / (double)N, nullptr, 0, Xt, ldt, st));
   prof_close(c, kProfAceSmall, t0, st);
   t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::lmul(fp32, Xt, ldt, n_psi, n_orb, false, p, N, N, (flags & HFX_ACCUMULATE) != 0, out, N, c->sm_count,
+  HFX_ACE_TRY(ace_lmul(c, fp32, Xt, ldt, n_psi, n_orb, false, p, N, N, (flags & HFX_ACCUMULATE) != 0, out, N,
                         st));
   prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
@@ -1584,7 +1604,7 @@ extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32
   const long long N = c->N;
   const ace::GramPlan gp = ace::gram_plan(n_orb, n_orb, N, c->sm_count);
   cudaEvent_t t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::gram(fp32, true, orbitals, N, n_orb, orbitals, N, n_orb, N, gp, part, c->sm_count, st));
+  HFX_ACE_TRY(ace_gram(c, fp32, true, orbitals, N, n_orb, orbitals, N, n_orb, N, gp, part, st));
   prof_close(c, kProfAceGram, t0, st);
   t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, nullptr, 0, st));
@@ -1633,7 +1653,7 @@ extern "C" hfx_status hfx_scdm_localise(hfx_ctx* c, const double* orbitals, int3
                                  c->sm_count, st));
   prof_close(c, kProfAceSmall, t0, st);
   t0 = prof_mark(c, st);
-  HFX_ACE_TRY(ace::lmul(fp32, qt, ldt, n_orb, n_orb, false, orbitals, N, N, false, phi_loc, N, c->sm_count, st));
+  HFX_ACE_TRY(ace_lmul(c, fp32, qt, ldt, n_orb, n_orb, false, orbitals, N, N, false, phi_loc, N, st));
   prof_close(c, kProfAceLmul, t0, st);
   return HFX_OK;
 }

@@ -1,0 +1,118 @@
+// Fifth-generation tensor-core building blocks (tcgen05, sm_100 family) written as inline PTX:
+// shared-memory matrix descriptors for the SWIZZLE_128B K-major operand layout, the instruction
+// descriptor of kind::tf32 with FP32 accumulation, TMEM allocation, MMA issue and commit, mbarrier
+// waits with an iteration limit, and TMEM loads.
+//
+// Operand layout (both A and B K-major): rows of 32 four-byte elements (128 bytes of K); groups
+// of 8 rows form a 1024-byte atom in which the 16-byte chunk c of row r is stored at chunk
+// c ^ (r mod 8); atoms follow each other along M (or N) every 1024 bytes.  Tiles start on a
+// 1024-byte boundary.  One MMA takes K = 8 (32 bytes); the k-th step of a 128-byte row starts
+// 32 k bytes into the atom (the hardware applies the XOR to the address it forms).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hfx {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of 4-byte element (r, k), k < 32, in a SWIZZLE_128B K-major tile
+__host__ __device__ __forceinline__ uint32_t swz128(int r, int k) {
+  const uint32_t L = (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + 4 * k);
+  return L ^ ((uint32_t)(r & 7) << 4);
+}
+
+// shared-memory matrix descriptor: start address, leading-byte offset (unused by swizzled
+// K-major tiles), stride-byte offset 1024 (the next 8-row atom), descriptor version 1, layout
+// SWIZZLE_128B
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// TMEM allocation of `ncols` columns (a power of two >= 32) by one whole warp; the base address
+// is written to *dst (shared memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy writes of shared memory become visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// D (+)= A . B^T, one kind::tf32 MMA issued by the calling thread
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// one arrival on the mbarrier once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               ::"r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// wait until the phase of parity `parity` has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
+  const uint32_t a = smem_u32(mbar);
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 (w mod 4) ...)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+               "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                 "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                 "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                 "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// split of an FP32 value into two TF32 values: hi = x rounded to the nearest TF32 (10 fraction
+// bits, ties away from zero), lo = x - hi exactly (|lo| <= half a TF32 unit of x).  The tensor
+// core reads the top 19 bits of each operand, so hi is taken exactly and lo to 11 significant
+// bits: hi + lo represents x to about 2^-21 relative, and the three products hi.hi + hi.lo +
+// lo.hi reproduce an FP32 product to about that accuracy.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t h = (u + 0x1000u) & 0xFFFFE000u;
+  hi = ((u & 0x7F800000u) == 0x7F800000u) ? x : __uint_as_float(h);
+  lo = x - hi;
+}
+
+}  // namespace tc
+}  // namespace hfx

@@ -115,6 +115,33 @@ def test_build_and_apply_parity(precision, n_orb, n, seed):
     ex.close()
 
 
+@pytest.mark.parametrize("no_tc", ["0", "1"])
+@pytest.mark.parametrize("n_orb,n_psi,n,seed", [(40, 40, 14, 4), (120, 270, 16, 5), (200, 64, 12, 6)])
+def test_tensor_core_and_simt_contractions(no_tc, n_orb, n_psi, n, seed, monkeypatch):
+    """FP32 contexts run the grid contractions on the tensor cores (tcgen05, TF32 x 3 split
+    products, FP32 accumulation in TMEM); HFX_NO_TC=1 keeps them on the FP32 SIMT kernels.  Both
+    against the oracle: M (Gram form, several output tiles when n_orb > 128), P and V_x^ACE psi
+    (left multiply with up to 128 or 256 columns; 270 functions exceed that and take the SIMT
+    kernel), and the screen (absolute values)."""
+    monkeypatch.setenv("HFX_NO_TC", no_tc)
+    L = 7.5
+    lat = np.diag([L, L, L])
+    phi = small_orbitals(n_orb, n, L, seed)
+    W = synthetic_action(phi, seed)
+    M0, L0, P0 = A.ace_build(phi, W, lat)
+    ex = make_exchange(L, n, "fp32")
+    M, Lf, P = ex.ace_build(dev(phi), dev(W))
+    psi = np.random.default_rng(seed + 10).standard_normal((n_psi, n, n, n))
+    Y = ex.ace_apply(P, dev(psi))
+    ex.sync_status()
+    assert rel(M.cpu().numpy(), M0) < TOL["fp32"]
+    assert rel(P.cpu().numpy(), P0) < 10 * TOL["fp32"]
+    Y0 = A.ace_apply(P0, psi, lat)
+    assert rel(Y.cpu().numpy(), Y0) < 10 * TOL["fp32"]
+    assert np.max(np.abs(Y.cpu().numpy() - Y0)) < 10 * TOL["fp32"] * np.max(np.abs(Y0))
+    ex.close()
+
+
 @pytest.mark.parametrize("n_orb", [200, 256, 257])
 def test_cholesky_paths(n_orb):
     # 200 and 256 orbitals: the cluster factorisation with one and two local rows per warp (256 is
