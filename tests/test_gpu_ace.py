@@ -116,7 +116,7 @@ def test_build_and_apply_parity(precision, n_orb, n, seed):
 
 
 @pytest.mark.parametrize("no_tc", ["0", "1"])
-@pytest.mark.parametrize("n_orb,n_psi,n,seed", [(40, 40, 18, 4), (120, 270, 16, 5), (200, 64, 12, 6)])
+@pytest.mark.parametrize("n_orb,n_psi,n,seed", [(40, 40, 18, 4), (120, 270, 16, 5), (200, 64, 18, 6)])
 def test_tensor_core_and_simt_contractions(no_tc, n_orb, n_psi, n, seed, monkeypatch):
     """FP32 contexts run the grid contractions on the tensor cores (tcgen05, TF32 x 3 split
     products, FP32 accumulation in TMEM); HFX_NO_TC=1 keeps them on the FP32 SIMT kernels.  Both
