@@ -695,6 +695,26 @@ cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx,
 #undef HFX_ACE_GRAM
 }
 
+// m <- (m + m^T) / 2 in place (exact when m is already symmetric): a symmetric quantity whose two
+// halves were summed in different orders (split tensor-core products) becomes exactly symmetric
+__global__ void k_symmetrise(double* __restrict__ m, int n, long long ld) {
+  const long long total = (long long)n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(i / n), b = (int)(i % n);
+    if (a >= b) continue;
+    const double v = 0.5 * (m[(long long)a * ld + b] + m[(long long)b * ld + a]);
+    m[(long long)a * ld + b] = v;
+    m[(long long)b * ld + a] = v;
+  }
+}
+
+cudaError_t symmetrise(double* m, int n, long long ld, cudaStream_t st) {
+  const long long total = (long long)n * n;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((total + 255) / 256, 1024));
+  k_symmetrise<<<grid, 256, 0, st>>>(m, n, ld);
+  return cudaGetLastError();
+}
+
 cudaError_t gram_reduce(bool fp32, const double* partials, int splits, int nx, int ny, double scale, double* out,
                         long long ldo, void* outt, long long ldt, cudaStream_t st) {
   const long long total = (long long)nx * ny;

@@ -48,6 +48,8 @@ cudaError_t gram(bool fp32, bool absval, const double* x, long long ldx, int nx,
 // to outt[b][a] (FP32 if fp32 else FP64, row stride ldt); either may be NULL
 cudaError_t gram_reduce(bool fp32, const double* partials, int splits, int nx, int ny, double scale, double* out,
                         long long ldo, void* outt, long long ldt, cudaStream_t st);
+// m <- (m + m^T) / 2 in place (n x n, row stride ld)
+cudaError_t symmetrise(double* m, int n, long long ld, cudaStream_t st);
 // row stride of a transposed small operand with m columns (16-byte rows)
 long long lmul_ldt(bool fp32, int m);
 // out[i][p] (+)= sum_k T[i][k] Y[k][p] with T given transposed, tt[k][i] (compute type)

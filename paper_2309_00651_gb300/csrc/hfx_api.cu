@@ -1608,6 +1608,7 @@ extern "C" hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32
   prof_close(c, kProfAceGram, t0, st);
   t0 = prof_mark(c, st);
   HFX_ACE_TRY(ace::gram_reduce(fp32, part, gp.splits, n_orb, n_orb, c->omega / (double)N, S, n_orb, nullptr, 0, st));
+  HFX_ACE_TRY(ace::symmetrise(S, n_orb, n_orb, st));  // s_ij = s_ji exactly, whatever the summation order
   HFX_ACE_TRY(ace::screen_compact(S, n_orb, cut, pairs, n_pairs, rowbuf, st));
   prof_close(c, kProfAceSmall, t0, st);
   return HFX_OK;
