@@ -4,8 +4,14 @@
 //
 // Every FP64 operand value is rounded once to FP32 and split into two TF32 values, hi + lo
 // (tc::split_tf32); a product is formed as hi.hi + hi.lo + lo.hi, which reproduces the FP32
-// product to about 2^-21 relative.  The three MMAs of a k-step accumulate into one FP32
-// accumulator in TMEM.
+// product to about 2^-21 relative.  The tensor core rounds each addition into its FP32
+// accumulator toward zero, so a long accumulation drifts: about half a unit of the running sum
+// per MMA, always in the same direction (measured: 6e-6 on the 373248-point Gram of 128 water
+// orbitals when one accumulator took a whole run).  Hence the hi.hi products and the two
+// correction products (2^-10 smaller) go to separate accumulators, and the Gram form restarts
+// its accumulators every k-block of 32 points and adds them to round-to-nearest FP32 sums in
+// registers (4 MMAs per accumulator and k-block: about 1e-7 of drift).  The left multiply
+// contracts over the orbitals only (K <= a few hundred) and keeps its accumulators for the job.
 //
 // Block: 256 threads (8 warps), one per SM (two pipeline stages of shared memory).  Per k-block
 // of 32 contraction steps the threads load the FP64 operands of the next k-block into registers
@@ -70,24 +76,46 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const MmArgs a, int* 
     tc::mbar_init_fence();
     s_abort = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, 128);
+  // TMEM: k-block buffer b in {0, 1}: hi.hi accumulator at column 256 b, corrections at 256 b + 128
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 512);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   constexpr uint32_t idesc = tc::idesc_tf32(kTcTile, kTcTile);
   const double* X = reinterpret_cast<const double*>(a.x);
-  const int cp = tid & 15, r0 = tid >> 4;  // this thread: column pair cp, rows r0 + 16 i
+  const int cp = tid & 15, r0 = tid >> 4;  // loads: column pair cp, rows r0 + 16 i
+  const int q = warp & 3, h = warp >> 2;   // drains: TMEM lanes 32q.. (rows a), columns 64h.. (b)
+  const uint32_t lane_off = (uint32_t)(32 * q) << 16;
   const int tiles = a.tiles_x * a.tiles_y;
 
-  long long g = 0;  // k-blocks this block has issued (stage = g & 1, use of the stage = g >> 1)
+  long long g = 0;  // k-blocks this block has issued: stage and TMEM buffer g & 1, use g >> 1
   bool aborted = false;
   double2 xr[8], yr[8];
+  float acc[64];
+  // k-block g - 1's products (its commit) into the round-to-nearest sums
+  auto drain = [&](long long gd) -> bool {
+    if (!tc::mbar_wait(&mbar[gd & 1], (uint32_t)((gd >> 1) & 1), kWaitLimit)) return false;
+    tc::fence_after_sync();
+    const uint32_t tb0 = tmem + lane_off + 256u * (uint32_t)(gd & 1) + 64u * h;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+      float vm[32], vc[32];
+      tc::tmem_ld32(tb0 + 32u * cc, vm);
+      tc::tmem_ld32(tb0 + 128u + 32u * cc, vc);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[32 * cc + j] += vm[j] + vc[j];
+    }
+    tc::fence_before_sync();
+    return true;
+  };
   for (int job = blockIdx.x; job < a.njobs && !aborted; job += gridDim.x) {
     const int s = job / tiles, t = job - s * tiles;
     const int ta = t % a.tiles_x, tb = t / a.tiles_x;
     const long long p0 = (long long)s * a.chunk, p1 = min(a.K, p0 + a.chunk);
     const int nkb = (int)((p1 - p0 + kTcBK - 1) / kTcBK);
+#pragma unroll
+    for (int j = 0; j < 64; ++j) acc[j] = 0.f;
     auto load = [&](int kb) {
       const long long p = p0 + (long long)kb * kTcBK + 2 * cp;
       const bool pin = p < p1;  // runs start and end on even points, so p + 1 < p1 as well
@@ -107,8 +135,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const MmArgs a, int* 
       unsigned char* sal = sah + kTileBytes;
       unsigned char* sbh = sah + 2 * kTileBytes;
       unsigned char* sbl = sah + 3 * kTileBytes;
-      // the stage was last read by the MMAs of k-block g - 2
-      if (g >= 2 && !tc::mbar_wait(&mbar[st], (uint32_t)(((g >> 1) - 1) & 1), kWaitLimit)) s_abort = 1;
+      // stage st and TMEM buffer st were last used by k-block g - 2, drained in the previous
+      // iteration (or at the end of the previous job)
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int r = r0 + 16 * i;
@@ -129,41 +157,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const MmArgs a, int* 
       if (tid == 0) {
         tc::fence_after_sync();
         const uint32_t ah = tc::smem_u32(sah), al = tc::smem_u32(sal), bh = tc::smem_u32(sbh), bl = tc::smem_u32(sbl);
+        const uint32_t dm = tmem + 256u * (uint32_t)st, dc = dm + 128u;
 #pragma unroll
         for (int ks = 0; ks < kTcBK / 8; ++ks) {
           const uint32_t off = 32u * ks;
-          tc::mma_tf32(tmem, tc::desc_sw128(ah + off), tc::desc_sw128(bh + off), idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-          tc::mma_tf32(tmem, tc::desc_sw128(ah + off), tc::desc_sw128(bl + off), idesc, 1u);
-          tc::mma_tf32(tmem, tc::desc_sw128(al + off), tc::desc_sw128(bh + off), idesc, 1u);
+          tc::mma_tf32(dm, tc::desc_sw128(ah + off), tc::desc_sw128(bh + off), idesc, ks > 0 ? 1u : 0u);
+          tc::mma_tf32(dc, tc::desc_sw128(ah + off), tc::desc_sw128(bl + off), idesc, ks > 0 ? 1u : 0u);
+          tc::mma_tf32(dc, tc::desc_sw128(al + off), tc::desc_sw128(bh + off), idesc, 1u);
         }
         tc::mma_commit(&mbar[st]);
       }
       if (kb + 1 < nkb) load(kb + 1);
+      if (kb > 0 && !drain(g - 1)) s_abort = 1;
     }
     if (aborted) break;
-    // the job's accumulator is complete once its last commit arrives
-    const long long gl = g - 1;
-    if (!tc::mbar_wait(&mbar[gl & 1], (uint32_t)((gl >> 1) & 1), kWaitLimit)) s_abort = 1;
+    // the job's last k-block
+    if (!drain(g - 1)) s_abort = 1;
     __syncthreads();
     if (s_abort) { aborted = true; break; }
-    tc::fence_after_sync();
-    const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q.. (rows a), columns 64h.. (b)
     const int ga = ta * kTcTile + 32 * q + (tid & 31);
-    double* out = a.out + (size_t)s * a.nx * a.ny;
+    if (ga < a.nx) {
+      double* out = a.out + (size_t)s * a.nx * a.ny + (size_t)ga * a.ny;
 #pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(64 * h + 32 * cc), v);
-      if (ga < a.nx) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int gb = tb * kTcTile + 64 * h + 32 * cc + j;
-          if (gb < a.ny) out[(size_t)ga * a.ny + gb] = f32_to_f64_exact(v[j]);
-        }
+      for (int j = 0; j < 64; ++j) {
+        const int gb = tb * kTcTile + 64 * h + j;
+        if (gb < a.ny) out[gb] = f32_to_f64_exact(acc[j]);
       }
     }
-    tc::fence_before_sync();
-    __syncthreads();  // TMEM read before the next job's first MMA overwrites it
   }
   if (aborted) {
     if (tid == 0) atomicOr(err, kErrTimeout);
@@ -173,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(const MmArgs a, int* 
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, 128);
+    tc::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -197,7 +217,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_lmul_tc(const MmArgs a, int* 
     tc::mbar_init_fence();
     s_abort = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tmem_base, NCOL);
+  // TMEM: hi.hi accumulator at column 0, corrections at column NCOL
+  if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * NCOL);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -276,9 +297,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_lmul_tc(const MmArgs a, int* 
 #pragma unroll
         for (int ks = 0; ks < kTcBK / 8; ++ks) {
           const uint32_t off = 32u * ks;
-          tc::mma_tf32(tmem, tc::desc_sw128(ah + off), tc::desc_sw128(bh + off), idesc, (kb > 0 || ks > 0) ? 1u : 0u);
-          tc::mma_tf32(tmem, tc::desc_sw128(ah + off), tc::desc_sw128(bl + off), idesc, 1u);
-          tc::mma_tf32(tmem, tc::desc_sw128(al + off), tc::desc_sw128(bh + off), idesc, 1u);
+          const uint32_t first = (kb > 0 || ks > 0) ? 1u : 0u;
+          tc::mma_tf32(tmem, tc::desc_sw128(ah + off), tc::desc_sw128(bh + off), idesc, first);
+          tc::mma_tf32(tmem + NCOL, tc::desc_sw128(ah + off), tc::desc_sw128(bl + off), idesc, first);
+          tc::mma_tf32(tmem + NCOL, tc::desc_sw128(al + off), tc::desc_sw128(bh + off), idesc, 1u);
         }
         tc::mma_commit(&mbar[st]);
       }
@@ -294,16 +316,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_lmul_tc(const MmArgs a, int* 
     const long long gp = p0 + 32 * q + (tid & 31);
 #pragma unroll 1
     for (int cc = 0; cc < NCOL / 64; ++cc) {
-      float v[32];
+      float v[32], vc[32];
       const int m0 = (NCOL / 2) * h + 32 * cc;
       tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)m0, v);
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(NCOL + m0), vc);
       if (gp < a.N) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int m = m0 + j;
           if (m < a.nx) {
             double* o = a.out + (long long)m * a.ldo + gp;
-            const double w = f32_to_f64_exact(v[j]);
+            const double w = f32_to_f64_exact(v[j] + vc[j]);
             *o = a.accumulate ? *o + w : w;
           }
         }
@@ -320,7 +343,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_lmul_tc(const MmArgs a, int* 
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, NCOL);
+    tc::tmem_dealloc(tmem, 2 * NCOL);
   }
 }
 
