@@ -450,7 +450,7 @@ def measure_workload(name, precision, hfx, I, O, dev, reps=3, n_check=12):
     torch.cuda.synchronize()
     hfx.hfx_profile_enable(ex.ctx, False)
     prof = hfx.hfx_profile_read(ex.ctx)
-    csize = 8 if precision == "fp32" else 16
+    csize = 16 if precision == "fp64" else 8
     peak = measured_peak_hbm()[0]
     E_val = float(E.item())
     hom = 0.5 * (w.volume / N) * float(torch.sum(phi * V).item())
@@ -841,6 +841,8 @@ def main():
         del V, phi
         torch.cuda.empty_cache()
         extra = {"water64_n96": measure_workload("water64_n96", args.precision, hfx, I, O, dev),
+                 # the same workload with the forward DFTs on the tensor cores (split TF32 GEMMs)
+                 "water64_n96_mixed_tc": measure_workload("water64_n96", "mixed_tc", hfx, I, O, dev),
                  "uneven_batch": measure_batch(hfx, I, dev, args.precision)}
         if args.with_128:
             extra["water128_n128"] = measure_workload("water128_n128", args.precision, hfx, I, O, dev, reps=2, n_check=8)

@@ -63,9 +63,14 @@ typedef enum {
 } hfx_kernel;
 
 typedef enum {
-  HFX_PREC_FP64 = 0,  /* all arithmetic in FP64                                          */
-  HFX_PREC_FP32 = 1   /* pair products and FFTs in FP32; energy sums and the V_x phi
-                         accumulation in FP64                                              */
+  HFX_PREC_FP64 = 0,     /* all arithmetic in FP64                                       */
+  HFX_PREC_FP32 = 1,     /* pair products and FFTs in FP32; energy sums and the V_x phi
+                            accumulation in FP64                                          */
+  HFX_PREC_MIXED_TC = 2  /* as HFX_PREC_FP32, but the forward DFTs of the plane pass (along
+                            z and y) run on the tensor cores: each axis one complex DFT as a
+                            dense GEMM with split TF32 operands (hi + lo, three products)
+                            and FP32 accumulation; cubic grids of edge 32, 48, 64 or 96
+                            (HFX_ERR_UNSUPPORTED_GRID otherwise)                          */
 } hfx_precision;
 
 /* flags for hfx_apply */

@@ -20,6 +20,7 @@
 #include "../../include/hfx_sinr.h"
 #include "hfx_ace_internal.h"
 #include "hfx_internal.h"
+#include "tc_sm100.cuh"
 
 using namespace hfx;
 
@@ -234,6 +235,10 @@ struct hfx_ctx {
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
   int blocks_fwd_ct = 1, blocks_x_ct = 1;
+  // HFX_PREC_MIXED_TC: the forward plane pass's DFTs on the tensor cores (pre-split DFT matrix)
+  bool tc_dft = false;
+  void* d_dftb = nullptr;
+  int blocks_fwd_tc = 1;
   std::map<int, std::unique_ptr<Schedule>> sched;  // by n_orb
   // queue tables of hfx_apply_batched when this context comes first in a batch
   void* d_batch = nullptr;
@@ -370,6 +375,8 @@ static void free_ctx_tables(hfx_ctx* c) {
   c->d_twct = nullptr;
   if (c->d_batch) cudaFree(c->d_batch);
   c->d_batch = nullptr;
+  if (c->d_dftb) cudaFree(c->d_dftb);
+  c->d_dftb = nullptr;
   c->batch_bytes = 0;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   c->ev_pending.clear();
@@ -465,6 +472,41 @@ static hfx_status build_tables(hfx_ctx* c) {
   return HFX_OK;
 }
 
+// The DFT matrix of edge n for the tensor-core forward pass: B[j][k] over outputs j (Re of the
+// frequency at position j for j < n, Im of the one at position j - n beyond) and inputs k (Re of
+// point k for k < n, Im of point k - n beyond), forward sign; per k-block of 32 inputs a TF32 hi
+// tile and a lo tile (x = hi + lo, hi rounded to the nearest TF32) in the SWIZZLE_128B K-major
+// layout of 2n rows.
+static std::vector<uint32_t> dft_tc_table(const DimPlan& d) {
+  const int n = d.n, nb = 2 * n, kb_count = 2 * n / 32;
+  const size_t tile_words = (size_t)nb * 32;
+  std::vector<uint32_t> t((size_t)kb_count * 2 * tile_words, 0u);
+  for (int j = 0; j < nb; ++j) {
+    const int f = freq_of_pos(d, j % n);
+    const bool im_out = j >= n;
+    for (int k = 0; k < 2 * n; ++k) {
+      const int tin = k % n;
+      const bool im_in = k >= n;
+      const cs_pair w = cossin_2pi_frac((long long)tin * f, n);
+      const double v = im_out ? (im_in ? w.c : -w.s) : (im_in ? w.s : w.c);
+      const float x = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &x, 4);
+      const uint32_t hu = (u + 0x1000u) & 0xFFFFE000u;
+      float hi;
+      std::memcpy(&hi, &hu, 4);
+      const float lo = x - hi;
+      uint32_t lu;
+      std::memcpy(&lu, &lo, 4);
+      const int kb = k / 32;
+      const size_t w0 = (size_t)kb * 2 * tile_words + tc::swz128(j, k % 32) / 4;
+      t[w0] = hu;
+      t[w0 + tile_words] = lu;
+    }
+  }
+  return t;
+}
+
 extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hfx_kernel kernel,
                                  double alpha, hfx_precision prec, hfx_ctx** out) {
   g_last_error.clear();
@@ -473,7 +515,10 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (!box || !grid) return fail(HFX_ERR_INVALID_ARG, "box or grid is NULL");
   if (kernel != HFX_KERNEL_COULOMB && kernel != HFX_KERNEL_COULOMB_SPHERE)
     return fail(HFX_ERR_INVALID_ARG, "unknown kernel %d", (int)kernel);
-  if (prec != HFX_PREC_FP64 && prec != HFX_PREC_FP32) return fail(HFX_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  if (prec != HFX_PREC_FP64 && prec != HFX_PREC_FP32 && prec != HFX_PREC_MIXED_TC)
+    return fail(HFX_ERR_INVALID_ARG, "unknown precision %d", (int)prec);
+  const bool mixed_tc = prec == HFX_PREC_MIXED_TC;
+  if (mixed_tc) prec = HFX_PREC_FP32;  // FP32 data and SIMT stages elsewhere; the forward DFTs on tensor cores
   if (kernel == HFX_KERNEL_COULOMB_SPHERE && !(ecut > 0.0)) return fail(HFX_ERR_INVALID_ARG, "ecut must be > 0");
   if (!std::isfinite(alpha)) return fail(HFX_ERR_INVALID_ARG, "alpha is not finite");
   std::unique_ptr<hfx_ctx> c(new hfx_ctx());
@@ -560,6 +605,20 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
       c->blocks_x_ct = std::max(1, c->blocks_x_ct);
       c->ct = f;
     }
+  }
+  if (mixed_tc) {
+    const int n = grid[0];
+    if (!c->ct || !dft::tc_edge(n))
+      return fail(HFX_ERR_UNSUPPORTED_GRID,
+                  "HFX_PREC_MIXED_TC needs a cubic grid of edge 32, 48, 64 or 96 (got %d x %d x %d)", (int)grid[0],
+                  (int)grid[1], (int)grid[2]);
+    e = dft::tc_prepare(n, &c->blocks_fwd_tc);
+    if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
+    const std::vector<uint32_t> tb = dft_tc_table(c->geo.d[2]);
+    st = upload(&c->d_dftb, tb.data(), tb.size() * sizeof(uint32_t));
+    if (st != HFX_OK) { free_ctx_tables(c.get()); return st; }
+    c->blocks_fwd_tc = std::max(1, c->blocks_fwd_tc);
+    c->tc_dft = true;
   }
   *out = c.release();
   return HFX_OK;
@@ -828,7 +887,11 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
         Passes<T>::inv_z_rows(g, gr, smem_rows(c, c->rb), fs, couples, c0, c1, c->rb, W, (const C*)c->d_tw[2]);
       close(kProfX, e0, fs);
     } else {
-      if (ct) {
+      if (ct && c->tc_dft) {
+        const int gt = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_tc);
+        dft::fwd_yz_tc(g.n1, std::max(gt, 1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
+                       (const unsigned char*)c->d_dftb, c->d_err);
+      } else if (ct) {
         const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
         ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
                    (const float2*)c->d_twct);

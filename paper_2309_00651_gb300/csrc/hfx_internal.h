@@ -71,6 +71,17 @@ struct CtFns {
                      const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
 };
 
+// Forward plane pass with the DFT stages on the tensor cores (hfx_dft_tc.cu): cubic FP32 grids of
+// edge 32, 48, 64 or 96; `dftb` is the pre-split, pre-swizzled DFT matrix of the edge
+// (tc_table_bytes(n) bytes, built by the host library).
+namespace dft {
+bool tc_edge(int n);
+size_t tc_table_bytes(int n);
+cudaError_t tc_prepare(int n, int* blocks_per_sm);
+void fwd_yz_tc(int n, int grid, cudaStream_t st, const float* orb, long long Ntot, const int4* couples, int c0,
+               int c1, float2* W, const unsigned char* dftb, int* err);
+}  // namespace dft
+
 #define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128)
 #define HFX_CT_DECLARE(NN) const CtFns* ct_fns_##NN();
 HFX_CT_SIZES(HFX_CT_DECLARE)

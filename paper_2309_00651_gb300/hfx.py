@@ -19,7 +19,7 @@ HFX_OK = 0
 STATUS_NAMES = {0: "HFX_OK", -1: "HFX_ERR_INVALID_ARG", -2: "HFX_ERR_UNSUPPORTED_GRID", -3: "HFX_ERR_OOM",
                 -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT",
                 -7: "HFX_ERR_NOT_POSITIVE_DEFINITE", -8: "HFX_ERR_RANK_DEFICIENT"}
-PRECISION = {"fp64": 0, "fp32": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "mixed_tc": 2}
 KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
 HFX_ENERGY_ONLY = 0x1
 HFX_ACCUMULATE = 0x2
