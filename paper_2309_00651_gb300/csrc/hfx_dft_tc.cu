@@ -140,8 +140,11 @@ k_fwd_yz_tc(const float* __restrict__ orb, long long Ntot, const int4* __restric
 
     // ---- z: rows y, inputs [Re z | Im z] -> P[y][column]
     for (int kb = 0; kb < KB && !aborted; ++kb) {
-      const bool re = kb < KB / 2;
-      const int z0 = 32 * (re ? kb : kb - KB / 2) + 16 * hf;
+      // this thread's 16 inputs 32 kb + 16 hf ..: all real or all imaginary parts (N is a
+      // multiple of 16), of points z0 .. z0 + 15
+      const int k0 = 32 * kb + 16 * hf;
+      const bool re = k0 < N;
+      const int z0 = re ? k0 : k0 - N;
       const bool live = rr < N && (re ? hasa : hasb);
       const float* p1 = (re ? pa1 : pb1) + rr * N + z0;
       const float* p2 = (re ? pa2 : pb2) + rr * N + z0;
@@ -184,8 +187,9 @@ k_fwd_yz_tc(const float* __restrict__ orb, long long Ntot, const int4* __restric
 #pragma unroll
     for (int j = 0; j < NB / 2; ++j) acc[j] = 0.f;
     for (int kb = 0; kb < KB && !aborted; ++kb) {
-      const bool re = kb < KB / 2;
-      const int y0 = 32 * (re ? kb : kb - KB / 2) + 16 * hf;
+      const int k0 = 32 * kb + 16 * hf;
+      const bool re = k0 < N;
+      const int y0 = re ? k0 : k0 - N;
       const int col = rr + (re ? 0 : N);
 #pragma unroll
       for (int q4 = 0; q4 < 4; ++q4) {
