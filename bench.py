@@ -125,6 +125,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_peak_tf32():
+    """Dense TF32 tensor rate: the measured BF16 burst rate x the nominal TF32/BF16 ratio (1.1/2.25)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 burst x nominal tf32/bf16 ratio"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16 ratio"
+
+
 def measured_peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -252,13 +261,21 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
     peak_tf = FP32_FFMA_PEAK_TFLOPS if precision == "fp32" else FP64_PEAK_TFLOPS
     hbm = measured_peak_hbm()[0]
 
+    tf32_peak, tf32_kind = measured_peak_tf32()
+
     def roof(ms, nbytes, kernel):
         tf = flops / (ms / 1e3) / 1e12
+        gbs = nbytes / (ms / 1e3) / 1e9
+        if precision == "fp32":
+            # tcgen05 TF32 x 3: three tensor-core products per FP32 product; the FP64 operands
+            # stream from HBM once, which is the bound
+            return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                    "avg_launch_ms": ms, "alg_bytes_per_launch": nbytes, "alg_flops_per_launch": flops,
+                    "tensor_tflops": 3 * tf, "tensor_peak_tflops": tf32_peak, "tensor_frac": 3 * tf / tf32_peak,
+                    "tensor_peak_kind": tf32_kind, "peak_kind": "measured"}
         return {"bound": "alu", "kernel": kernel, "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": tf / peak_tf, "avg_launch_ms": ms, "alg_flops_per_launch": flops,
-                "alg_bytes_per_launch": nbytes, "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm,
-                "peak_kind": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz" if precision == "fp32"
-                              else "nominal FP64 rate")}
+                "alg_bytes_per_launch": nbytes, "hbm_frac": gbs / hbm, "peak_kind": "nominal FP64 rate"}
 
     # SCDM: n - 1 residual updates, each a pass over the orbital copy in the compute type plus the
     # FP64 residual norms (read + write); the picks between them are latency-bound single blocks
@@ -271,8 +288,10 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
                           "alg_bytes_per_call": scdm_bytes,
                           "measured": "whole call (picks included) with CUDA events"},
         "apply_vs_exchange_call": None,
-        "roofline": roof(g_ms, gram_bytes, "k_ace_mm (split grid contraction, <psi|P>)"),
-        "roofline_lmul": roof(l_ms, lmul_bytes, "k_ace_mm (left multiply, -X P)"),
+        "roofline": roof(g_ms, gram_bytes, ("k_gram_tc (tcgen05 TF32x3" if precision == "fp32" else "k_ace_mm (FP64") +
+                         ", split grid contraction <psi|P>)"),
+        "roofline_lmul": roof(l_ms, lmul_bytes, ("k_lmul_tc (tcgen05 TF32x3" if precision == "fp32" else "k_ace_mm (FP64") +
+                              ", left multiply -X P)"),
         "kernel_ms_per_apply": {k: v["ms"] / reps for k, v in kp.items()},
         "checks": {"span_rel_err": float(torch.linalg.norm(Y - V) / torch.linalg.norm(V)),
                    "half_trace_M_vs_E_rel": abs(0.5 * float(torch.trace(M)) - E) / abs(E)},
@@ -841,9 +860,23 @@ def main():
         del V, phi
         torch.cuda.empty_cache()
         extra = {"water64_n96": measure_workload("water64_n96", args.precision, hfx, I, O, dev),
-                 # the same workload with the forward DFTs on the tensor cores (split TF32 GEMMs)
-                 "water64_n96_mixed_tc": measure_workload("water64_n96", "mixed_tc", hfx, I, O, dev),
+
                  "uneven_batch": measure_batch(hfx, I, dev, args.precision)}
+        # the 96^3 workload with the forward DFTs on the tensor cores (HFX_PREC_MIXED_TC: each
+        # axis one dense split-TF32 GEMM), beside the FP32 SIMT stages on the same inputs
+        mt = measure_workload("water64_n96", "mixed_tc", hfx, I, O, dev)
+        f32 = extra["water64_n96"]
+        line["mixed_tc"] = {
+            "config": mt["config"], "value": mt["value"], "unit": UNIT, "ms_per_call": mt["ms_per_call_median"],
+            "fwd_pass_ms": mt["roofline_passes"]["fwd_yz"]["ms_per_step"],
+            "errors": {"E_rel_err_vs_oracle_on_sample": mt["checks"]["E_rel_err_vs_oracle_on_sample"],
+                       "homogeneity_rel_err": mt["checks"]["homogeneity_rel_err"],
+                       "sample": mt["checks"]["sample"]},
+            "fp32_simt_same_inputs": {"value": f32["value"], "ms_per_call": f32["ms_per_call_median"],
+                                      "fwd_pass_ms": f32["roofline_passes"]["fwd_yz"]["ms_per_step"],
+                                      "E_rel_err_vs_oracle_on_sample": f32["checks"]["E_rel_err_vs_oracle_on_sample"]},
+            "tc_over_simt": mt["value"] / f32["value"],
+            "roofline_passes": mt["roofline_passes"]}
         if args.with_128:
             extra["water128_n128"] = measure_workload("water128_n128", args.precision, hfx, I, O, dev, reps=2, n_check=8)
         line["other_workloads"] = extra
