@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="libhfx", choices=["libhfx", "reference"])
     ap.add_argument("--workload", default="water32_n72")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed_tc"])
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -258,7 +258,7 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
     flops = 2.0 * n_orb * n_orb * N            # one contraction over the grid, n_psi = n_orb
     gram_bytes = 2.0 * n_orb * N * 8           # both FP64 operands read once
     lmul_bytes = 2.0 * n_orb * N * 8           # Y read once, C written once
-    peak_tf = FP32_FFMA_PEAK_TFLOPS if precision == "fp32" else FP64_PEAK_TFLOPS
+    peak_tf = FP32_FFMA_PEAK_TFLOPS if precision != "fp64" else FP64_PEAK_TFLOPS
     hbm = measured_peak_hbm()[0]
 
     tf32_peak, tf32_kind = measured_peak_tf32()
@@ -266,7 +266,7 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
     def roof(ms, nbytes, kernel):
         tf = flops / (ms / 1e3) / 1e12
         gbs = nbytes / (ms / 1e3) / 1e9
-        if precision == "fp32":
+        if precision != "fp64":
             # tcgen05 TF32 x 3: three tensor-core products per FP32 product; the FP64 operands
             # stream from HBM once, which is the bound
             return {"bound": "hbm", "kernel": kernel, "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
@@ -279,7 +279,7 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
 
     # SCDM: n - 1 residual updates, each a pass over the orbital copy in the compute type plus the
     # FP64 residual norms (read + write); the picks between them are latency-bound single blocks
-    esize = 4 if precision == "fp32" else 8
+    esize = 4 if precision != "fp64" else 8
     scdm_bytes = (n_orb - 1) * (n_orb * N * esize + 16 * N)
     scdm_gbs = scdm_bytes / (t_scdm / 1e3) / 1e9
     row = {
@@ -288,9 +288,9 @@ def ace_rows(ex, phi, V, E, w, precision, hfx, reps=10):
                           "alg_bytes_per_call": scdm_bytes,
                           "measured": "whole call (picks included) with CUDA events"},
         "apply_vs_exchange_call": None,
-        "roofline": roof(g_ms, gram_bytes, ("k_gram_tc (tcgen05 TF32x3" if precision == "fp32" else "k_ace_mm (FP64") +
+        "roofline": roof(g_ms, gram_bytes, ("k_gram_tc (tcgen05 TF32x3" if precision != "fp64" else "k_ace_mm (FP64") +
                          ", split grid contraction <psi|P>)"),
-        "roofline_lmul": roof(l_ms, lmul_bytes, ("k_lmul_tc (tcgen05 TF32x3" if precision == "fp32" else "k_ace_mm (FP64") +
+        "roofline_lmul": roof(l_ms, lmul_bytes, ("k_lmul_tc (tcgen05 TF32x3" if precision != "fp64" else "k_ace_mm (FP64") +
                               ", left multiply -X P)"),
         "kernel_ms_per_apply": {k: v["ms"] / reps for k, v in kp.items()},
         "checks": {"span_rel_err": float(torch.linalg.norm(Y - V) / torch.linalg.norm(V)),
@@ -657,7 +657,7 @@ def main():
     # roofline of the dominant kernel (largest device time), algorithmic bytes per couple:
     #   fwd_yz writes the packed transform (8 N B per couple, FP32 complex);
     #   x_coulomb reads and writes it (16 N B); the accumulate passes read it (8 N B).
-    csize = 8 if args.precision == "fp32" else 16
+    csize = 16 if args.precision == "fp64" else 8
     per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_acc_dense": csize * N,
                   "y_acc_generic": csize * N}
     # couples handled by each kernel per call (full pair list: every block pair full)
@@ -762,7 +762,7 @@ def main():
         "timing": "each step is one replay of a CUDA graph of the full call; value = K steps / CUDA-event time "
                   "of the K-step region (max over ranks); median over the K per-replay event times beside it",
         "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded water-box-shaped orbitals; no dataset)",
         "config": dict(workload_desc(w, P), precision=args.precision,
                        l2="inputs larger than L2 (FP64 orbitals %.0f MB + transform batches %.0f MB per step)" % (

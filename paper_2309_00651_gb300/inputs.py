@@ -75,6 +75,9 @@ WORKLOADS = {
     "water32_n72": Workload("water32_n72", 128, 18.6, 72, 40.0, "gauss", seed=0, sigma=1.2),
     # 64 H2O box (paper's Fe3+/64-water cell size), 256 random-PW orbitals, 96^3, 20 Ha.
     "water64_n96": Workload("water64_n96", 256, 23.5, 96, 20.0, "pw", seed=0),
+    # the 96^3 box with 64 random-PW orbitals (16 H2O worth): a profiling case of the 96^3 kernels
+    # whose transforms and orbital copies still exceed L2 (2080 pairs, about 2 GB on the device)
+    "water16_n96": Workload("water16_n96", 64, 23.5, 96, 20.0, "pw", seed=0),
     # small case of the water-box workload for profiling captures: 32 orbitals in the same
     # 18.6 bohr cell and 72^3 grid (528 pairs; one batch of transforms still exceeds L2).
     "water8_n72": Workload("water8_n72", 32, 18.6, 72, 40.0, "gauss", seed=0, sigma=1.2),
