@@ -100,7 +100,8 @@ hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hf
 
 /* hfx_workspace_bytes -- device scratch that hfx_apply needs for n_orb orbitals and a list
  * of n_pairs pairs (pair staging, the per-batch transforms and the per-couple energy sums;
- * plus an FP32 copy of the orbitals on the FP32 path).  Returns 0 on bad arguments. */
+ * plus, on the FP32 paths, an FP32 copy of the orbitals and the FP32 accumulator of V_x phi that
+ * is widened into the caller's FP64 array at the end of the call).  Returns 0 on bad arguments. */
 size_t hfx_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs);
 
 /* hfx_set_workspace -- hand the context a caller-owned device buffer (e.g. a torch tensor)

@@ -646,7 +646,7 @@ extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes)
 // workspace layout
 // ------------------------------------------------------------------------------------
 struct Layout {
-  size_t orb32, W, W2, epart, eblk, couples, total;
+  size_t orb32, v32, W, W2, epart, eblk, couples, total;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -667,6 +667,8 @@ static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, bool sec
   auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
   const size_t orb32_bytes = (c->prec == HFX_PREC_FP32) ? (size_t)n_orb * c->N * 4 : 0;
   L.orb32 = take(orb32_bytes);
+  // FP32 path: the call's FP32 accumulator of V_x phi (widened into the caller's FP64 array once)
+  L.v32 = take(c->prec == HFX_PREC_FP32 ? (size_t)n_orb * c->N * 4 : 0);
   L.W = take((size_t)S.max_batch_couples * c->N * cplx_size(c));
   // a second transform buffer when batches are pipelined on two streams
   L.W2 = take(second_buffer ? (size_t)S.max_batch_couples * c->N * cplx_size(c) : 0);
@@ -797,6 +799,26 @@ static void launch_energy(const double* epart, const int4* couples, int total, i
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// V_x phi (FP64) = (accumulate ? V_x phi : 0) + the call's FP32 accumulator, widened exactly with
+// integer operations (FP32 subnormals flush to zero); n is a multiple of 4
+__device__ __forceinline__ void widen_v4(const float* __restrict__ v32, double* __restrict__ v, long long i4,
+                                         int accumulate) {
+  const float4 a = __ldcs(reinterpret_cast<const float4*>(v32) + i4);
+  double2 lo = make_double2(ct::widen_exact(a.x), ct::widen_exact(a.y));
+  double2 hi = make_double2(ct::widen_exact(a.z), ct::widen_exact(a.w));
+  double2* d = reinterpret_cast<double2*>(v) + 2 * i4;
+  if (accumulate) {
+    const double2 o0 = d[0], o1 = d[1];
+    lo.x += o0.x; lo.y += o0.y; hi.x += o1.x; hi.y += o1.y;
+  }
+  d[0] = lo;
+  d[1] = hi;
+}
+__global__ void k_widen_v(const float* __restrict__ v32, double* __restrict__ v, long long n, int accumulate) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n / 4; i += (long long)gridDim.x * blockDim.x)
+    widen_v4(v32, v, i, accumulate);
+}
+
 // Small tables reach device memory as kernel arguments (8 KiB per launch): no host buffer has to
 // outlive the call (it may be captured in a graph) and no pageable-memory copy is involved.
 constexpr int kTableWords = 2048;
@@ -840,6 +862,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   char* ws = env.ws;
   using C = cx<T>;
   const bool pipe = S.nbatches > 1 && env.side != nullptr && c->pipeline;
+  // what the accumulate passes add into: V_x phi itself (FP64), or the call's FP32 accumulator
+  T* vacc = std::is_same<T, float>::value ? (T*)(ws + L.v32) : (T*)vxphi;
   auto mark = [&](cudaStream_t s) { return env.prof ? prof_mark(c, s) : nullptr; };
   auto close = [&](int slot, cudaEvent_t e, cudaStream_t s) { if (env.prof) prof_close(c, slot, e, s); };
   C* Wbuf[2] = {(C*)(ws + L.W), (C*)(ws + (pipe ? L.W2 : L.W))};
@@ -922,28 +946,34 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       if (nd > 0 && ct && S.b == 8)  // [dense block pairs]
         ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                         S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
-                        (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
+                        (const float2*)W, (const float2*)c->d_twct, (float*)vacc, vscale);
       else if (nd > 0)
         Passes<T>::y_acc_dense(g, dim3(nzc, g.n1, nd), dense_threads, smem_dense(c), st, S.b, orb, couples,
                                S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0, W,
-                               (const C*)c->d_tw[1], vxphi, vscale);
+                               (const C*)c->d_tw[1], vacc, vscale);
       if (nd > 0) close(kProfAcc, e0, st);
       const int ndg = S.diag_begin[b + 1] - S.diag_begin[b];
       e0 = mark(st);
       if (ndg > 0)  // [full diagonal block pairs]; the generic pass takes whatever is left
         ct->y_acc_diag(dim3(nzc, g.n1, ndg), smem_diag_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                        S.d_diag_slots + S.diag_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
-                       (const float2*)W, (const float2*)c->d_twct, vxphi, vscale);
+                       (const float2*)W, (const float2*)c->d_twct, (float*)vacc, vscale);
       if (ndg > 0) close(kProfAccGeneric, e0, st);
       e0 = mark(st);
       if (ng > 0)
         Passes<T>::y_acc_generic(g, dim3(nzc, g.n1, ng), smem_acc(c), st, orb, couples,
                                  S.d_generic_slots + S.generic_begin[b], S.d_slot_couple_base, S.d_slot_blocks, S.b,
-                                 n_orb, c0, W, (const C*)c->d_tw[1], vxphi, vscale, c->gen_grp, c->gen_phi,
+                                 n_orb, c0, W, (const C*)c->d_tw[1], vacc, vscale, c->gen_grp, c->gen_phi,
                                  gen_cap_max(c));
       if (ng > 0) close(kProfAccGeneric, e0, st);
     }
     if (pipe) HFX_CUDA_TRY(cudaEventRecord(c->ev_p3[b & 1], st));
+  }
+  if (std::is_same<T, float>::value && !energy_only) {
+    const long long n = (long long)n_orb * g.N;
+    const int blocks = (int)std::min<long long>((n / 4 + 255) / 256, (long long)c->sm_count * 16);
+    k_widen_v<<<std::max(blocks, 1), 256, 0, st>>>((const float*)vacc, vxphi, n, (flags & HFX_ACCUMULATE) ? 1 : 0);
+    HFX_CUDA_TRY(cudaGetLastError());
   }
   return HFX_OK;
 }
@@ -985,8 +1015,12 @@ static hfx_status stage_call(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   char* ws = env.ws;
   const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
   const bool energy_only = (flags & HFX_ENERGY_ONLY) != 0;
-  if (!accumulate && !energy_only)
+  if (c->prec == HFX_PREC_FP32) {
+    // the FP32 accumulator starts at zero; V_x phi itself is written (or added to) at the end
+    if (!energy_only) HFX_CUDA_TRY(cudaMemsetAsync(ws + L.v32, 0, (size_t)n_orb * c->N * sizeof(float), st));
+  } else if (!accumulate && !energy_only) {
     HFX_CUDA_TRY(cudaMemsetAsync(vxphi, 0, (size_t)n_orb * c->N * sizeof(double), st));
+  }
   int4* couples = (int4*)(ws + L.couples);
   HFX_CUDA_TRY(cudaMemsetAsync(couples, 0xff, (size_t)S.max_total_couples * sizeof(int4), st));
   {
@@ -1108,7 +1142,11 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
     P.couples = (const int4*)(env.ws + L.couples);
     P.W = (cx<T>*)(env.ws + L.W);
     P.epart = (double*)(env.ws + L.epart);
-    P.V = a.vxphi;
+    // the accumulate items add into V_x phi itself (FP64) or into the call's FP32 accumulator,
+    // which a widening task then turns into V_x phi
+    P.V = std::is_same<T, float>::value ? (T*)(env.ws + L.v32) : (T*)a.vxphi;
+    P.V64 = a.vxphi;
+    P.n_v = (long long)a.n_orb * c->N;
     P.ex = a.ex_dev;
     P.vtab = (const T*)c->d_vtab;
     P.tw1 = (const cx<T>*)c->d_tw[0];
@@ -1153,6 +1191,7 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
       add(kTaskX, (long long)(c1 - c0) * c->grid[1], c0, c1, c0);
       if (!eo) add(kTaskAcc, (long long)nzc * c->grid[0] * (s1 - s0), s0, s1, c0);
     }
+    if (std::is_same<T, float>::value && !eo) add(kTaskWiden, (P.n_v + kWidenPerItem - 1) / kWidenPerItem, 0, 0, 0);
     add(kTaskEnergy, 1, 0, 0, 0);
     chains.push_back(ch);
     smem = std::max({smem, smem_fwd(c), smem_x(c)});
@@ -1294,6 +1333,7 @@ extern "C" hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_
         launches += (S.dense_begin[b + 1] > S.dense_begin[b]) + (S.generic_begin[b + 1] > S.generic_begin[b]) +
                     (S.diag_begin[b + 1] > S.diag_begin[b]);
     if (c->prec == HFX_PREC_FP32 && !(flags & HFX_ORBITALS_F32)) launches += 1; /* FP64 -> FP32 orbitals */
+    if (c->prec == HFX_PREC_FP32 && !eo) launches += 1;                         /* FP32 V accumulator -> V */
   } else if (!(flags & HFX_ACCUMULATE)) {
     launches = 1;
   }

@@ -26,7 +26,9 @@
 
 namespace hfx {
 
-enum BatchKind : int { kTaskFwd = 0, kTaskX = 1, kTaskAcc = 2, kTaskEnergy = 3 };
+enum BatchKind : int { kTaskFwd = 0, kTaskX = 1, kTaskAcc = 2, kTaskEnergy = 3, kTaskWiden = 4 };
+
+constexpr int kWidenPerItem = 4096;  // elements of V_x phi per widening item
 
 template <typename T>
 struct BatchProblem {
@@ -35,7 +37,9 @@ struct BatchProblem {
   const int4* couples;          // staged pair couples
   cx<T>* W;                     // the problem's transform buffer (one batch at a time)
   double* epart;                // per-couple, per-y-plane energy partial sums
-  double* V;                    // V_x phi (FP64)
+  T* V;                         // V_x phi accumulator (FP64, or the call's FP32 one)
+  double* V64;                  // V_x phi (FP64) the FP32 accumulator is widened into
+  long long n_v;                // elements of V_x phi
   double* ex;                   // E_x (FP64 scalar)
   const T* vtab;                // v(G) in storage order
   const cx<T>* tw1;
@@ -188,6 +192,23 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
       const int slot = tk.a0 + int(rest / g.n1);
       acc_generic_item(g, P.orb, P.couples, slot, P.slot_couple_base, P.slot_blocks, P.bsize, P.n_orb, tk.cbase, P.W,
                        P.tw2, P.V, P.vscale, P.grp, P.phi_smem, P.cap_max, smem_raw, zi, x);
+    } else if (tk.kind == kTaskWiden) {
+      // V_x phi (FP64) = (accumulate ? V_x phi : 0) + the FP32 accumulator, widened exactly
+      const long long e0 = local * kWidenPerItem;
+      for (int i = threadIdx.x; i < kWidenPerItem / 4; i += blockDim.x) {
+        const long long e = e0 + 4LL * i;
+        if (e + 4 > P.n_v) break;
+        const float4 a = __ldcg(reinterpret_cast<const float4*>(P.V) + e / 4);
+        double2* d = reinterpret_cast<double2*>(P.V64 + e);
+        double2 lo = make_double2(ct::widen_exact(a.x), ct::widen_exact(a.y));
+        double2 hi = make_double2(ct::widen_exact(a.z), ct::widen_exact(a.w));
+        if (P.accumulate) {
+          const double2 o0 = d[0], o1 = d[1];
+          lo.x += o0.x; lo.y += o0.y; hi.x += o1.x; hi.y += o1.y;
+        }
+        d[0] = lo;
+        d[1] = hi;
+      }
     } else {  // energy: E_x = scale * sum_g w_g sum_y epart[g][y], in a fixed order
       double sacc = 0.0;
       for (int c = threadIdx.x; c < P.total_couples; c += blockDim.x) {

@@ -246,8 +246,13 @@ k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ 
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
   for (int i = threadIdx.x; i < P.twtotal; i += kThreadsPlane) tw[i] = twg[i];
-  const int items = (c1 - c0) * N;
-  for (int it = blockIdx.x; it < items; it += gridDim.x) fwd_yz_ct_item<T, N>(orb, Ntot, couples, c0, W, buf, tw, it);
+  const int ncl = c1 - c0, items = ncl * N;
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    // x-major order: the blocks in flight work on the same x-plane of many couples, whose orbital
+    // planes (the batch's orbitals at that x) are then read from DRAM once and from L2 after
+    const int x = it / ncl, cl = it - x * ncl;
+    fwd_yz_ct_item<T, N>(orb, Ntot, couples, c0, W, buf, tw, cl * N + x);
+  }
 }
 
 // ----------------------------------------------------------------------------------
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
                  const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                  const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
-                 const cx<T>* __restrict__ twg, double* __restrict__ V, double vscale) {
+                 const cx<T>* __restrict__ twg, T* __restrict__ V, double vscale) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
   constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
@@ -504,32 +509,31 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
     }
     __syncthreads();
   }
-  // flush, FP64 read-modify-write of V_J (registers) and V_I (shared memory): every load is issued
-  // before any store (a store could alias a later load, which would serialise the round trips);
-  // the contribution is scaled in FP32 and widened exactly, so one FP64 add per element remains
-  const float vs = (float)vscale;
-  double old[NP][B];
+  // flush into the call's FP32 accumulator of V_x phi (widened to FP64 once at the end of the
+  // call): read-modify-write of V_J (registers) and V_I (shared memory), every load issued before
+  // any store (a store could alias a later load, which would serialise the round trips)
+  const T vs = (T)vscale;
+  T old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * Ntot + goff[k]) : 0.0;
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * Ntot + goff[k]) : T(0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * accJ[k][j]);
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + vs * accJ[k][j];
   }
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : 0.0;
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : T(0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
     const int p = threadIdx.x + k * NT;
 #pragma unroll
-    for (int j = 0; j < B; ++j)
-      V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * accI[j * PTS + p]);
+    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vs * accI[j * PTS + p];
   }
 }
 

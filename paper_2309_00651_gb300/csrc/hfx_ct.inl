@@ -38,14 +38,14 @@ void x_coulomb(int grid, size_t smem, cudaStream_t st, const int4* couples, int 
 
 void y_acc_dense(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
                  const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* W,
-                 const float2* tw, double* V, double vscale) {
+                 const float2* tw, float* V, double vscale) {
   ct::k_y_acc_dense_ct<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }
 
 void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
                 const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* W,
-                const float2* tw, double* V, double vscale) {
+                const float2* tw, float* V, double vscale) {
   ct::k_y_acc_diag_ct<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
                 const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                 const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
-                const cx<T>* __restrict__ twg, double* __restrict__ V, double vscale) {
+                const cx<T>* __restrict__ twg, T* __restrict__ V, double vscale) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
   using D = DiagLayout<B>;
@@ -172,19 +172,19 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
     __syncthreads();
   });
 
-  // FP64 read-modify-write of the block's V rows: every load before any store; the contribution is
-  // scaled in FP32 and widened exactly (one FP64 add per element)
-  const float vs = (float)vscale;
-  double old[NP][B];
+  // read-modify-write of the block's rows of the call's FP32 accumulator of V_x phi: every load
+  // before any store
+  const T vs = (T)vscale;
+  T old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : 0.0;
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : T(0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + widen_exact(vs * acc[k][j]);
+    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vs * acc[k][j];
   }
 }
 

@@ -33,14 +33,14 @@ struct Passes {
                          int rb, cx<T>* W, const cx<T>* tw3);
   static void y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b, const T* orb,
                           const int4* couples, const int* slot_list, const int* slot_couple_base,
-                          const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale);
+                          const int2* slot_blocks, int c0, const cx<T>* W, const cx<T>* tw2, T* V, double vscale);
   // one persistent launch over the task list of a batch of problems (hfx_batch.cuh)
   static void batch(int grid, size_t smem, cudaStream_t st, const BatchProblem<T>* probs, const BatchTask* tasks,
                     int ntasks, long long total_items, BatchQueue* queue, long long budget);
   static cudaError_t batch_occupancy(size_t smem, int* blocks);
   static void y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const T* orb, const int4* couples,
                             const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int bsize,
-                            int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, double* V, double vscale, int grp,
+                            int n_orb, int c0, const cx<T>* W, const cx<T>* tw2, T* V, double vscale, int grp,
                             int phi_smem, int cap_max);
 };
 
@@ -64,11 +64,11 @@ struct CtFns {
                     const float* vtab, const float2* tw, double* epart, int energy_only);
   void (*y_acc_dense)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                       const int4* couples, const int* slot_list, const int* slot_couple_base,
-                      const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
+                      const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale);
   // full diagonal block pairs (B = 8), same arguments and threads as the dense pass
   void (*y_acc_diag)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                      const int4* couples, const int* slot_list, const int* slot_couple_base,
-                     const int2* slot_blocks, int c0, const float2* W, const float2* tw, double* V, double vscale);
+                     const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale);
 };
 
 // Forward plane pass with the DFT stages on the tensor cores (hfx_dft_tc.cu): cubic FP32 grids of

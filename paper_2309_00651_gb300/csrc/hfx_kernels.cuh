@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(DenseBounds<NP>::threads, DenseBounds<NP>::blo
 k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
               const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
               const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
-              const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale) {
+              const cx<T>* __restrict__ tw2g, T* __restrict__ V, double vscale) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
   constexpr int HB = B / 2;
@@ -673,30 +673,31 @@ k_y_acc_dense(const __grid_constant__ Geo g, const T* __restrict__ orb, const in
     }
     __syncthreads();  // buffer r % kDenseRing is refilled by the copies issued in the next iteration
   }
-  // flush, FP64 read-modify-write: V_J from registers, V_I from shared memory; all loads first
-  // (a store could alias a later load, which would serialise the round trips)
-  double old[NP][B];
+  // flush, read-modify-write of V (FP64 on the FP64 path, the call's FP32 accumulator on the FP32
+  // path): V_J from registers, V_I from shared memory; all loads first (a store could alias a later
+  // load, which would serialise the round trips)
+  const T vs = (T)vscale;
+  T old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * g.N + goff[k]) : 0.0;
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * g.N + goff[k]) : T(0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * g.N + goff[k]] = old[k][j] + vscale * double(accJ[k][j]);
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * g.N + goff[k]] = old[k][j] + vs * accJ[k][j];
   }
 #pragma unroll
   for (int k = 0; k < NP; ++k)
 #pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * g.N + goff[k]) : 0.0;
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * g.N + goff[k]) : T(0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     if (!ok[k]) continue;
     const int p = pp[k];
 #pragma unroll
-    for (int j = 0; j < B; ++j)
-      V[(long long)(I0 + j) * g.N + goff[k]] = old[k][j] + vscale * double(accI[j * pts + p]);
+    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * g.N + goff[k]] = old[k][j] + vs * accI[j * pts + p];
   }
 }
 
@@ -720,7 +721,7 @@ __device__ __forceinline__ void acc_generic_item(const Geo& g, const T* __restri
                                                  const int* __restrict__ slot_couple_base,
                                                  const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0,
                                                  const cx<T>* __restrict__ W, const cx<T>* __restrict__ tw2g,
-                                                 double* __restrict__ V, double vscale, int grp, int phi_smem,
+                                                 T* __restrict__ V, double vscale, int grp, int phi_smem,
                                                  int cap_max, unsigned char* smem_raw, int zi, int x) {
   using C = cx<T>;
   constexpr int ZC = ZChunk<T>::value;
@@ -832,8 +833,9 @@ __device__ __forceinline__ void acc_generic_item(const Geo& g, const T* __restri
   // flush: V[o][x][y][z0 + zz] += vscale * acc, in groups whose loads all precede their stores
   constexpr int GF = 8;
   const int total = nloc * pts;
+  const T vs = (T)vscale;
   for (int i0f = threadIdx.x; i0f < total; i0f += GF * blockDim.x) {
-    double old[GF];
+    T old[GF];
     long long off[GF];
     bool on[GF];
 #pragma unroll
@@ -844,11 +846,11 @@ __device__ __forceinline__ void acc_generic_item(const Geo& g, const T* __restri
       const int yy = p / ZC, zz = p - yy * ZC;
       on[u] = i < total && zz < zcn;
       off[u] = (long long)orbital(lo) * g.N + rowoff + (long long)yy * n3 + zz;
-      old[u] = on[u] ? __ldcg(V + off[u]) : 0.0;
+      old[u] = on[u] ? __ldcg(V + off[u]) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < GF; ++u)
-      if (on[u]) V[off[u]] = old[u] + vscale * double(acc[i0f + u * blockDim.x]);
+      if (on[u]) V[off[u]] = old[u] + vs * acc[i0f + u * blockDim.x];
   }
 }
 
@@ -858,7 +860,7 @@ __global__ void __launch_bounds__(kThreadsGen)
 k_y_acc_generic(const __grid_constant__ Geo g, const T* __restrict__ orb, const int4* __restrict__ couples,
                 const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                 const int2* __restrict__ slot_blocks, int bsize, int n_orb, int c0, const cx<T>* __restrict__ W,
-                const cx<T>* __restrict__ tw2g, double* __restrict__ V, double vscale, int grp, int phi_smem,
+                const cx<T>* __restrict__ tw2g, T* __restrict__ V, double vscale, int grp, int phi_smem,
                 int cap_max) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   acc_generic_item(g, orb, couples, slot_list[blockIdx.z], slot_couple_base, slot_blocks, bsize, n_orb, c0, W, tw2g, V,

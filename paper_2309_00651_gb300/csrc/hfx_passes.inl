@@ -53,7 +53,7 @@ void Passes<Real>::x_coulomb(const Geo& g, int grid, size_t smem, cudaStream_t s
 template <>
 void Passes<Real>::y_acc_dense(const Geo& g, dim3 grid, int threads, size_t smem, cudaStream_t st, int b,
                                const Real* orb, const int4* couples, const int* slot_list, const int* slot_couple_base,
-                               const int2* slot_blocks, int c0, const cx<Real>* W, const cx<Real>* tw2, double* V,
+                               const int2* slot_blocks, int c0, const cx<Real>* W, const cx<Real>* tw2, Real* V,
                                double vscale) {
   // points per thread so that one block of at most kDenseMaxThreads threads covers the tile
   const int pts = g.n2 * ZChunk<Real>::value;
@@ -70,7 +70,7 @@ template <>
 void Passes<Real>::y_acc_generic(const Geo& g, dim3 grid, size_t smem, cudaStream_t st, const Real* orb,
                                  const int4* couples, const int* slot_list, const int* slot_couple_base,
                                  const int2* slot_blocks, int bsize, int n_orb, int c0, const cx<Real>* W,
-                                 const cx<Real>* tw2, double* V, double vscale, int grp, int phi_smem, int cap_max) {
+                                 const cx<Real>* tw2, Real* V, double vscale, int grp, int phi_smem, int cap_max) {
   k_y_acc_generic<Real><<<grid, kThreadsGen, smem, st>>>(g, orb, couples, slot_list, slot_couple_base, slot_blocks,
                                                         bsize, n_orb, c0, W, tw2, V, vscale, grp, phi_smem, cap_max);
 }
