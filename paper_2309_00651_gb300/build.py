@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhfx.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu", "hfx_ace.cu", "hfx_ace_tc.cu", "hfx_dft_tc.cu", "hfx_scdm.cu", "hfx_sinr.cu"] + [
+SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu", "hfx_ace.cu", "hfx_ace_tc.cu", "hfx_dft_tc.cu", "hfx_scdm.cu", "hfx_sinr.cu", "hfx_peak.cu"] + [
     f"hfx_ct_{n}.cu" for n in (32, 48, 64, 72, 96, 128)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE] + ARCH

@@ -33,7 +33,7 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_last_error", "hfx_destroy",
             "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
             "hfx_scdm_workspace_bytes", "hfx_scdm_localise",
-            "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x")
+            "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x", "hfx_fma_peak")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
@@ -125,6 +125,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_sinr_update_v.restype = ctypes.c_int
     L.hfx_sinr_update_x.argtypes = [sp, i64, dbl, vp, vp, vp, vp, vp]
     L.hfx_sinr_update_x.restype = ctypes.c_int
+    L.hfx_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl), vp]
+    L.hfx_fma_peak.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -465,3 +467,10 @@ class Exchange:
             self.close()
         except Exception:
             pass
+
+
+def hfx_fma_peak(fp64: bool, iters: int = 20000, stream: Optional[torch.cuda.Stream] = None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (FP64 or FP32)."""
+    out = ctypes.c_double(0.0)
+    _check(load_library().hfx_fma_peak(1 if fp64 else 0, int(iters), ctypes.byref(out), _stream_handle(stream)))
+    return float(out.value)
