@@ -53,8 +53,11 @@ typedef enum {
   HFX_ERR_TIMEOUT = -6,          /* (device-detected) a bounded device-side wait gave up  */
   HFX_ERR_NOT_POSITIVE_DEFINITE = -7, /* (device-detected) ACE construction: -M had a pivot
                                     <= 0 in its Cholesky factorisation (include/hfx_ace.h) */
-  HFX_ERR_RANK_DEFICIENT = -8    /* (device-detected) SCDM: no grid point with a positive
+  HFX_ERR_RANK_DEFICIENT = -8,   /* (device-detected) SCDM: no grid point with a positive
                                     residual norm was left to pick (include/hfx_ace.h)     */
+  HFX_ERR_CORRUPTION = -9        /* (device-detected, HFX_DEBUG builds) a guard band of the
+                                    workspace was overwritten, or a placed couple broke the
+                                    canonical layout of its block pair                     */
 } hfx_status;
 
 typedef enum {
@@ -245,6 +248,15 @@ hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint
  * 5 inverse-y/accumulate pass for the other block pairs.  Not for use inside stream capture. */
 hfx_status hfx_profile_enable(hfx_ctx* c, int on);
 hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]);
+
+/* hfx_debug_check_guards -- HFX_DEBUG builds (libhfx_debug.so): enqueue on cuda_stream a check of
+ * the guard bands that separate the slices of the context's workspace as the last hfx_apply laid
+ * them out (every call fills them before its first pass and checks them after its last one); a
+ * band that lost its pattern sets the corruption bit of the error word (hfx_sync_status:
+ * HFX_ERR_CORRUPTION).  Debug builds also check, after the pair placement of every call, that each
+ * placed couple sits at its canonical place in its block pair.  Release builds return
+ * HFX_ERR_INVALID_ARG. */
+hfx_status hfx_debug_check_guards(hfx_ctx* c, void* cuda_stream);
 
 /* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
  * thread's next libhfx call. */

@@ -18,6 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhfx.so")
+LIB_DEBUG = os.path.join(PKG, "libhfx_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu", "hfx_ace.cu", "hfx_ace_tc.cu", "hfx_dft_tc.cu", "hfx_scdm.cu", "hfx_sinr.cu", "hfx_peak.cu"] + [
@@ -73,20 +74,24 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
-    """Compile (if needed) and return the path of libhfx.so."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_file = os.path.join(BUILD, "stamp")
-    stamp = _stamp()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Compile (if needed) and return the path of libhfx.so, or of libhfx_debug.so with debug=True
+    (HFX_DEBUG: workspace guard bands and the device-side couple-layout check)."""
+    build_dir = BUILD + ("_debug" if debug else "")
+    lib = LIB_DEBUG if debug else LIB
+    flags = NVCC_FLAGS + (["-DHFX_DEBUG"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
+    stamp_file = os.path.join(build_dir, "stamp")
+    stamp = _stamp() + ("-debug" if debug else "")
+    if not force and os.path.exists(lib) and os.path.exists(stamp_file):
         with open(stamp_file) as f:
             if f.read().strip() == stamp:
-                return LIB
+                return lib
     nvcc = nvcc_path()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
+        cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -96,15 +101,15 @@ def build(verbose: bool = False, force: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fPIC", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

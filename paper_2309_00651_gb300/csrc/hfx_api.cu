@@ -15,6 +15,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hfx.h"
 #include "../../include/hfx_ace.h"
 #include "../../include/hfx_sinr.h"
@@ -23,6 +25,12 @@
 #include "tc_sm100.cuh"
 
 using namespace hfx;
+
+// an NVTX range around the enqueueing of one pass (host side; near free without a tool attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ------------------------------------------------------------------------------------
 // error reporting
@@ -198,6 +206,16 @@ static void build_schedule(Schedule& S, int n_orb, int b, size_t transform_budge
   }
 }
 
+// workspace slices of one call (offsets from the workspace base)
+struct Layout {
+  size_t orb32, v32, W, W2, epart, eblk, couples, total;
+  // HFX_DEBUG builds: guard bands after the slices (offsets), filled before and checked after a call
+  int nguard = 0;
+  size_t guard[8] = {};
+};
+constexpr size_t kGuardBytes = 256;
+constexpr uint32_t kGuardWord = 0xA5C3F00Du;
+
 // ------------------------------------------------------------------------------------
 // context
 // ------------------------------------------------------------------------------------
@@ -244,6 +262,9 @@ struct hfx_ctx {
   void* d_batch = nullptr;
   size_t batch_bytes = 0;
   long long wait_budget = 1LL << 34;  // clock cycles a device-side wait may take (~8 s)
+  // HFX_DEBUG builds: the guard bands of the last call's workspace layout
+  Layout dbg_layout;
+  char* dbg_ws = nullptr;
   // FP32 contexts: the ACE contractions on the tensor cores (tcgen05, TF32 x 3); HFX_NO_TC=1
   // keeps them on the FP32 SIMT kernels
   bool ace_tc = true;
@@ -645,9 +666,6 @@ extern "C" hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes)
 // ------------------------------------------------------------------------------------
 // workspace layout
 // ------------------------------------------------------------------------------------
-struct Layout {
-  size_t orb32, v32, W, W2, epart, eblk, couples, total;
-};
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -664,7 +682,15 @@ static bool two_buffers(const hfx_ctx* c, const Schedule& S) { return S.nbatches
 static Layout layout_of(const hfx_ctx* c, const Schedule& S, int n_orb, bool second_buffer) {
   Layout L;
   size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off += align256(bytes); return o; };
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+#ifdef HFX_DEBUG
+    if (L.nguard < 8) L.guard[L.nguard++] = off;
+    off += kGuardBytes;
+#endif
+    return o;
+  };
   const size_t orb32_bytes = (c->prec == HFX_PREC_FP32) ? (size_t)n_orb * c->N * 4 : 0;
   L.orb32 = take(orb32_bytes);
   // FP32 path: the call's FP32 accumulator of V_x phi (widened into the caller's FP64 array once)
@@ -799,6 +825,66 @@ static void launch_energy(const double* epart, const int4* couples, int total, i
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// HFX_DEBUG builds: fill / check the workspace guard bands (up to 8 bands of kGuardBytes)
+struct GuardSet {
+  int n;
+  size_t off[8];
+};
+__global__ void k_guard_fill(char* ws, GuardSet g) {
+  for (int b = 0; b < g.n; ++b)
+    for (int i = threadIdx.x; i < (int)(kGuardBytes / 4); i += blockDim.x)
+      reinterpret_cast<uint32_t*>(ws + g.off[b])[i] = kGuardWord ^ (uint32_t)(b * 977 + i);
+}
+__global__ void k_guard_check(const char* ws, GuardSet g, int* err) {
+  for (int b = 0; b < g.n; ++b)
+    for (int i = threadIdx.x; i < (int)(kGuardBytes / 4); i += blockDim.x)
+      if (reinterpret_cast<const uint32_t*>(ws + g.off[b])[i] != (kGuardWord ^ (uint32_t)(b * 977 + i)))
+        atomicOr(err, kErrGuard);
+}
+// HFX_DEBUG builds: every placed couple holds pairs of its slot's block pair, at their canonical
+// places (the layout the accumulate passes assume)
+__global__ void k_check_couples(const int4* __restrict__ couples, const int* __restrict__ slot_couple_base,
+                                const int2* __restrict__ slot_blocks, int nslots, int n_orb, int bsize,
+                                int* err) {
+  for (int s = blockIdx.x; s < nslots; s += gridDim.x) {
+    const int2 bp = slot_blocks[s];
+    const int I0 = bp.x * bsize, J0 = bp.y * bsize;
+    const int si = min(bsize, n_orb - I0), sj = min(bsize, n_orb - J0);
+    const int base = slot_couple_base[s], cap = slot_couple_base[s + 1] - base;
+    for (int c = threadIdx.x; c < cap; c += blockDim.x) {
+      const int4 cp = couples[base + c];
+      for (int h = 0; h < 2; ++h) {
+        const int i = h ? cp.z : cp.x, j = h ? cp.w : cp.y;
+        if (i < 0) continue;
+        bool ok = i <= j && i >= I0 && i < I0 + si && j >= J0 && j < J0 + sj;
+        if (ok) {
+          int t, cc;
+          if (bp.x != bp.y) {
+            t = (i - I0) * sj + (j - J0);
+            cc = t >> 1;
+          } else if (i != j) {
+            const int a = i - I0, b = j - I0;
+            t = a * si - a * (a + 1) / 2 + (b - a - 1);
+            cc = t >> 1;
+          } else {
+            const int noff = si * (si - 1) / 2;
+            t = i - I0;
+            cc = (noff + 1) / 2 + (t >> 1);
+          }
+          ok = cc == c && (t & 1) == h;
+        }
+        if (!ok) atomicOr(err, kErrLayout);
+      }
+    }
+  }
+}
+static GuardSet guard_set(const Layout& L) {
+  GuardSet g;
+  g.n = L.nguard;
+  for (int k = 0; k < 8; ++k) g.off[k] = L.guard[k];
+  return g;
+}
+
 // V_x phi (FP64) = (accumulate ? V_x phi : 0) + the call's FP32 accumulator, widened exactly with
 // integer operations (FP32 subnormals flush to zero); n is a multiple of 4
 __device__ __forceinline__ void widen_v4(const float* __restrict__ v32, double* __restrict__ v, long long i4,
@@ -894,6 +980,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
     const int grid1 = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd * 8);
     const int grid2 = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x * 8);
     const CtFns* ct = std::is_same<T, float>::value ? c->ct : nullptr;
+    NvtxRange nv_batch("hfx batch: forward, x/Coulomb, accumulate passes");
     cudaEvent_t e0 = mark(fs);
     if (c->pencil) {
       const int nzc3 = g.n3 / zc, nrb = (g.n2 + c->rb - 1) / c->rb;
@@ -1050,21 +1137,54 @@ static hfx_status apply_with(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
                              double* vxphi, cudaStream_t st) {
   char* ws = env.ws;
   const bool accumulate = (flags & HFX_ACCUMULATE) != 0;
+#ifdef HFX_DEBUG
+  k_guard_fill<<<1, 64, 0, st>>>(ws, guard_set(L));
+  c->dbg_layout = L;
+  c->dbg_ws = ws;
+#endif
   cudaEvent_t e_stage = env.prof ? prof_mark(c, st) : nullptr;
   const void* orb = nullptr;
-  hfx_status rs = stage_call(c, S, L, env, orbitals, n_orb, pairs, n_pairs, flags, vxphi, st, &orb);
+  hfx_status rs;
+  {
+    NvtxRange r("hfx stage: V clear, pair placement, FP32 copy");
+    rs = stage_call(c, S, L, env, orbitals, n_orb, pairs, n_pairs, flags, vxphi, st, &orb);
+  }
   if (rs != HFX_OK) return rs;
+#ifdef HFX_DEBUG
+  k_check_couples<<<std::max(1, std::min(S.nslots, c->sm_count * 4)), 128, 0, st>>>(
+      (const int4*)(ws + L.couples), S.d_slot_couple_base, S.d_slot_blocks, S.nslots, n_orb, S.b, c->d_err);
+#endif
   if (env.prof) prof_close(c, kProfStage, e_stage, st);
   if (c->prec == HFX_PREC_FP64) rs = run_passes<double>(c, S, L, env, (const double*)orb, n_orb, flags, vxphi, st);
   else rs = run_passes<float>(c, S, L, env, (const float*)orb, n_orb, flags, vxphi, st);
   if (rs != HFX_OK) return rs;
   const double scale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);
   cudaEvent_t e_en = env.prof ? prof_mark(c, st) : nullptr;
-  launch_energy((const double*)(ws + L.epart), (const int4*)(ws + L.couples), (int)S.max_total_couples, eparts(c),
-                (double*)(ws + L.eblk), scale, accumulate, ex_dev, st);
+  {
+    NvtxRange r("hfx energy sum");
+    launch_energy((const double*)(ws + L.epart), (const int4*)(ws + L.couples), (int)S.max_total_couples, eparts(c),
+                  (double*)(ws + L.eblk), scale, accumulate, ex_dev, st);
+  }
   if (env.prof) prof_close(c, kProfEnergy, e_en, st);
+#ifdef HFX_DEBUG
+  k_guard_check<<<1, 64, 0, st>>>(ws, guard_set(L), c->d_err);
+#endif
   HFX_CUDA_TRY(cudaGetLastError());
   return HFX_OK;
+}
+
+extern "C" hfx_status hfx_debug_check_guards(hfx_ctx* c, void* cuda_stream) {
+  g_last_error.clear();
+  if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
+#ifdef HFX_DEBUG
+  if (!c->dbg_ws) return fail(HFX_ERR_INVALID_ARG, "no call has laid out the workspace yet");
+  k_guard_check<<<1, 64, 0, (cudaStream_t)cuda_stream>>>(c->dbg_ws, guard_set(c->dbg_layout), c->d_err);
+  HFX_CUDA_TRY(cudaGetLastError());
+  return HFX_OK;
+#else
+  (void)cuda_stream;
+  return fail(HFX_ERR_INVALID_ARG, "guard bands exist in HFX_DEBUG builds (libhfx_debug.so) only");
+#endif
 }
 
 static hfx_status apply_impl(hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs, int64_t n_pairs,
@@ -1311,6 +1431,8 @@ extern "C" hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream) {
     HFX_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
     HFX_CUDA_TRY(cudaStreamSynchronize(st));
   }
+  if (h & kErrGuard) return fail(HFX_ERR_CORRUPTION, "a guard band of the workspace was overwritten");
+  if (h & kErrLayout) return fail(HFX_ERR_CORRUPTION, "a placed couple is off its canonical place in its block pair");
   if (h & kErrTimeout) return fail(HFX_ERR_TIMEOUT, "a device-side wait timed out");
   if (h & ace::kErrNotPosDef)
     return fail(HFX_ERR_NOT_POSITIVE_DEFINITE, "ACE construction: -(M + M^T)/2 is not positive definite; L and P are undefined");

@@ -62,6 +62,9 @@ struct Geo {
 // Error bits of the device error word.
 constexpr int kErrBadPair = 1;
 constexpr int kErrTimeout = 2;
+// HFX_DEBUG builds: a workspace guard band lost its pattern; a placed couple is off its canonical place
+constexpr int kErrGuard = 16;
+constexpr int kErrLayout = 32;
 
 constexpr int kThreadsPlane = 256;  // k_fwd_yz / k_x_coulomb
 

@@ -14,11 +14,13 @@ import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhfx.so")
+LIB_DEBUG_PATH = os.path.join(_PKG, "libhfx_debug.so")
 
 HFX_OK = 0
 STATUS_NAMES = {0: "HFX_OK", -1: "HFX_ERR_INVALID_ARG", -2: "HFX_ERR_UNSUPPORTED_GRID", -3: "HFX_ERR_OOM",
                 -4: "HFX_ERR_CUDA", -5: "HFX_ERR_BAD_PAIR_LIST", -6: "HFX_ERR_TIMEOUT",
-                -7: "HFX_ERR_NOT_POSITIVE_DEFINITE", -8: "HFX_ERR_RANK_DEFICIENT"}
+                -7: "HFX_ERR_NOT_POSITIVE_DEFINITE", -8: "HFX_ERR_RANK_DEFICIENT",
+                -9: "HFX_ERR_CORRUPTION"}
 PRECISION = {"fp64": 0, "fp32": 1, "mixed_tc": 2}
 KERNEL = {"coulomb": 0, "coulomb_sphere": 1}
 HFX_ENERGY_ONLY = 0x1
@@ -33,7 +35,8 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_last_error", "hfx_destroy",
             "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
             "hfx_scdm_workspace_bytes", "hfx_scdm_localise",
-            "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x", "hfx_fma_peak")
+            "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x", "hfx_fma_peak",
+            "hfx_debug_check_guards")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
@@ -63,11 +66,14 @@ class HFXError(RuntimeError):
 _lib = None
 
 
-def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load libhfx.so (built by paper_2309_00651_gb300.build.build()); raises if it is absent."""
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load libhfx.so (built by paper_2309_00651_gb300.build.build()), or libhfx_debug.so when the
+    environment sets HFX_DEBUG_LIB=1 (build(debug=True)); raises if it is absent."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_DEBUG_PATH if os.environ.get("HFX_DEBUG_LIB") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"libhfx.so not found at {path}: build it with paper_2309_00651_gb300.build.build()")
     L = ctypes.CDLL(path)
@@ -127,6 +133,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.hfx_sinr_update_x.restype = ctypes.c_int
     L.hfx_fma_peak.argtypes = [i32, i32, ctypes.POINTER(dbl), vp]
     L.hfx_fma_peak.restype = ctypes.c_int
+    L.hfx_debug_check_guards.argtypes = [vp, vp]
+    L.hfx_debug_check_guards.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -474,3 +482,8 @@ def hfx_fma_peak(fp64: bool, iters: int = 20000, stream: Optional[torch.cuda.Str
     out = ctypes.c_double(0.0)
     _check(load_library().hfx_fma_peak(1 if fp64 else 0, int(iters), ctypes.byref(out), _stream_handle(stream)))
     return float(out.value)
+
+
+def hfx_debug_check_guards(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
+    """HFX_DEBUG builds: enqueue the check of the workspace guard bands (see hfx_sync_status)."""
+    _check(load_library().hfx_debug_check_guards(ctx, _stream_handle(stream)))
