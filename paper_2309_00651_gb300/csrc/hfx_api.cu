@@ -1,5 +1,6 @@
 // libhfx host side: contexts, tables, the pair-block schedule, workspace layout, the
 // device-side pair-list staging kernels and the per-call launch sequence.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -217,6 +218,55 @@ constexpr size_t kGuardBytes = 256;
 constexpr uint32_t kGuardWord = 0xA5C3F00Du;
 
 // ------------------------------------------------------------------------------------
+// tensor maps (TMA)
+// ------------------------------------------------------------------------------------
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point (the library does not
+// link the driver library itself); NULL when the driver does not offer it
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// a 4-D FP32 tensor map over `base`: extents dims (dims[0] contiguous), byte strides of dimensions
+// 1..3 (any order), box sizes; elements outside the tensor read as zero.  False when the driver
+// refuses the description (alignment, sizes) or offers no encoder.
+static bool encode_f32_4d(CUtensorMap* m, const void* base, const cuuint64_t dims[4], const cuuint64_t strides[3],
+                          const cuuint32_t box[4]) {
+  const EncodeTiledFn f = encode_tiled();
+  if (!f) return false;
+  const cuuint32_t unit[4] = {1, 1, 1, 1};
+  return f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, unit,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the maps the TMA dense accumulate pass reads for a cubic grid of edge n: a transform buffer of
+// `cap` couples, W[couple][x][y][z] complex FP32, as (z reals, couple, y, x) with boxes of 8
+// complex x `cpi` couples x n rows; the FP32 orbitals orb[orbital][x][y][z] as (z, y, orbital, x)
+// with boxes of 8 x n x 8
+static bool encode_dense_maps(CUtensorMap* tmW, const void* W, long long cap, int cpi, CUtensorMap* tmOrb,
+                              const void* orb, int n_orb, int n) {
+  const cuuint64_t nn = (cuuint64_t)n, N3 = nn * nn * nn;
+  const cuuint64_t dw[4] = {2 * nn, (cuuint64_t)cap, nn, nn};
+  const cuuint64_t sw[3] = {N3 * 8, nn * 8, nn * nn * 8};
+  const cuuint32_t bw[4] = {16, (cuuint32_t)cpi, (cuuint32_t)n, 1};
+  const cuuint64_t dorb[4] = {nn, nn, (cuuint64_t)n_orb, nn};
+  const cuuint64_t sorb[3] = {nn * 4, N3 * 4, nn * nn * 4};
+  const cuuint32_t borb[4] = {8, (cuuint32_t)n, 8, 1};
+  return cap > 0 && encode_f32_4d(tmW, W, dw, sw, bw) && encode_f32_4d(tmOrb, orb, dorb, sorb, borb);
+}
+
+// ------------------------------------------------------------------------------------
 // context
 // ------------------------------------------------------------------------------------
 struct hfx_ctx {
@@ -253,6 +303,9 @@ struct hfx_ctx {
   const CtFns* ct = nullptr;
   void* d_twct = nullptr;        // per-stage twiddle tables of the edge
   int blocks_fwd_ct = 1, blocks_x_ct = 1;
+  // the compile-time dense accumulate pass moves its tiles by TMA (HFX_DENSE_TMA=0: per-thread
+  // asynchronous copies)
+  bool dense_tma = true;
   // HFX_PREC_MIXED_TC: the forward plane pass's DFTs on the tensor cores (pre-split DFT matrix)
   bool tc_dft = false;
   void* d_dftb = nullptr;
@@ -345,6 +398,8 @@ static size_t smem_dense_ct(int n, int b) {
   const int zc = 8, ln = dense_rows_ct(n) * (b / 2) * zc, pts = n * zc;
   return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)2 * b * pts * sizeof(float);
 }
+// the TMA form: 128 more bytes, so that its tensor-copy destinations can start on 128-byte boundaries
+static size_t smem_dense_tma_ct(int n) { return smem_dense_ct(n, 8) + 128; }
 static size_t smem_diag_ct(int n, int b) {
   const int zc = 8, ln = kDiagCouplesPerItCt * zc, pts = n * zc;
   return (size_t)(kDenseRingCt * n * ln + stage_plan(n).twtotal) * sizeof(float2) + (size_t)b * pts * sizeof(float);
@@ -566,6 +621,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (const char* s = std::getenv("HFX_BATCH_MB")) c->transform_budget = (size_t)std::max(1, atoi(s)) << 20;
   if (const char* s = std::getenv("HFX_PIPELINE")) c->pipeline = atoi(s) != 0;
   if (const char* s = std::getenv("HFX_NO_TC")) c->ace_tc = atoi(s) == 0;
+  if (const char* s = std::getenv("HFX_DENSE_TMA")) c->dense_tma = atoi(s) != 0;
 
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
@@ -616,7 +672,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (prec == HFX_PREC_FP32 && !c->pencil && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
     const CtFns* f = ct_fns(grid[0]);
     const int n = grid[0];
-    if (f && std::max({smem_plane_ct(n), smem_dense_ct(n, 8), smem_diag_ct(n, 8)}) + 512 <= (size_t)c->max_smem) {
+    if (f && std::max({smem_plane_ct(n), smem_dense_tma_ct(n), smem_diag_ct(n, 8)}) + 512 <= (size_t)c->max_smem) {
       e = f->prepare(c->max_smem - 512, smem_plane_ct(n), &c->blocks_fwd_ct, &c->blocks_x_ct);
       if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
       auto tw = to_real_vec<float>(stage_twiddles(n));
@@ -625,6 +681,8 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
       c->blocks_fwd_ct = std::max(1, c->blocks_fwd_ct);
       c->blocks_x_ct = std::max(1, c->blocks_x_ct);
       c->ct = f;
+      // TMA needs the driver's tensor-map encoder; without it the dense pass copies per thread
+      if (!encode_tiled()) c->dense_tma = false;
     }
   }
   if (mixed_tc) {
@@ -964,6 +1022,16 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   const int dense_np = pts > 2 * DenseBounds<2>::threads ? 4 : 2;
   const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
                                      (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
+  // the tensor maps of the TMA dense accumulate pass (one per transform buffer)
+  CUtensorMap tmW[2], tmOrb;
+  bool dense_tma = false;
+  if (std::is_same<T, float>::value && c->ct && S.b == 8 && c->dense_tma && !energy_only) {
+    const int cpi = dense_rows_ct(g.n1) * (S.b / 2);
+    dense_tma = encode_dense_maps(&tmW[0], Wbuf[0], S.max_batch_couples, cpi, &tmOrb, orb, n_orb, g.n1) &&
+                encode_dense_maps(&tmW[1], Wbuf[1], S.max_batch_couples, cpi, &tmOrb, orb, n_orb, g.n1);
+    // the buffers are 16-byte aligned and the edges multiples of 4, so the driver has no reason to refuse
+    if (!dense_tma) return fail(HFX_ERR_CUDA, "cuTensorMapEncodeTiled refused the dense pass's tensor maps");
+  }
   // forward and x passes on `fs`, accumulate passes on the caller's stream `st`
   cudaStream_t fs = pipe ? env.side : st;
   if (pipe) {
@@ -1030,7 +1098,11 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       e0 = mark(st);
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
-      if (nd > 0 && ct && S.b == 8)  // [dense block pairs]
+      if (nd > 0 && ct && S.b == 8 && dense_tma)  // [dense block pairs]
+        ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, g.N, couples,
+                            S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
+                            (const float2*)c->d_twct, (float*)vacc, vscale, c->d_err);
+      else if (nd > 0 && ct && S.b == 8)
         ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                         S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
                         (const float2*)W, (const float2*)c->d_twct, (float*)vacc, vscale);

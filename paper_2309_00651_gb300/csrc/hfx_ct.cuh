@@ -7,6 +7,7 @@
 // each stage reads its twiddles from its own [m][r] table (w_L^{j1 k}), one row per butterfly.
 #pragma once
 #include "hfx_kernels.cuh"
+#include "tma_sm100.cuh"
 
 namespace hfx {
 namespace ct {
@@ -512,6 +513,182 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   // flush into the call's FP32 accumulator of V_x phi (widened to FP64 once at the end of the
   // call): read-modify-write of V_J (registers) and V_I (shared memory), every load issued before
   // any store (a store could alias a later load, which would serialise the round trips)
+  const T vs = (T)vscale;
+  T old[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * Ntot + goff[k]) : T(0);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+#pragma unroll
+    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + vs * accJ[k][j];
+  }
+#pragma unroll
+  for (int k = 0; k < NP; ++k)
+#pragma unroll
+    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : T(0);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    if (!ok[k]) continue;
+    const int p = threadIdx.x + k * NT;
+#pragma unroll
+    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vs * accI[j * PTS + p];
+  }
+}
+
+// pass 3a with compile-time geometry, tiles moved by TMA: the work of k_y_acc_dense_ct, but one
+// thread issues each iteration's couple tile as one tensor copy (the 4-D box of 2 ZC reals x
+// RPI * HB couples x N rows of y at plane x, landing as [y][couple][zz]) and the two blocks'
+// orbital tiles as two more (box ZC x N x B, landing as [orbital][y][zz]); the copies complete on
+// mbarriers that every thread waits on with an iteration limit.  Couples without pairs are read
+// like the others (their slots of W hold stale values) and cleared in shared memory before the
+// transform.
+constexpr long long kTmaWaitCycles = 1LL << 30;  // about half a second
+
+template <typename T, int N, int B>
+__global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
+k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmOrb,
+                  const int4* __restrict__ couples, const int* __restrict__ slot_list,
+                  const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
+                  const cx<T>* __restrict__ twg, T* __restrict__ V, long long Ntot, double vscale,
+                  int* __restrict__ err) {
+  using C = cx<T>;
+  using G = DenseGeo<T, N>;
+  constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
+  constexpr int HB = B / 2;
+  constexpr int RPI = G::RPI;        // orbital rows per iteration
+  constexpr int CPI = RPI * HB;      // couples per iteration
+  constexpr int LN = CPI * ZC;       // lines of the tile [y][couple][zz]
+  constexpr int RING = kDenseRingCt;
+  constexpr int ITERS = B / RPI;
+  constexpr uint32_t kTileBytes = N * LN * sizeof(C);
+  constexpr uint32_t kOrbTileBytes = B * PTS * sizeof(T);
+  constexpr int PLANE = N * N;
+  constexpr StagePlan P = Plan<N>::p;
+  static_assert(B % RPI == 0, "rows per iteration must divide the block");
+  static_assert(B * HB <= 32, "one mask word per block pair");
+  static_assert(kTileBytes % 128 == 0 && kOrbTileBytes % 128 == 0, "tensor-copy destinations stay 128-byte aligned");
+  // the host encodes boxes of 16 x couples x N (transforms) and 8 x N x 8 (orbitals): the byte
+  // counts the mbarriers expect are those boxes only when ZC = 8 and B = 8
+  static_assert(ZC == 8 && B == 8, "box sizes of the host's tensor maps");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[RING + 1];  // the ring's slots, then the orbital tiles
+  __shared__ unsigned live_mask;
+  unsigned char* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  C* tiles = reinterpret_cast<C*>(base);                   // RING x [N][LN]
+  T* phiI = reinterpret_cast<T*>(tiles + RING * N * LN);   // [B][PTS]
+  T* accI = phiI + B * PTS;                                // [B][PTS]: phi_J on arrival, then the V_I sums
+  C* tw = reinterpret_cast<C*>(accI + B * PTS);
+  const CUtensorMap* mapW = &tmW;
+  const CUtensorMap* mapOrb = &tmOrb;
+
+  const int z0 = blockIdx.x * ZC;
+  const int zcn = min(ZC, N - z0);
+  const int x = blockIdx.y;
+  const int slot = slot_list[blockIdx.z];
+  const int2 blk = slot_blocks[slot];
+  const int I0 = blk.x * B, J0 = blk.y * B;
+  const int cs = slot_couple_base[slot];
+  const long long rowoff = (long long)x * PLANE + z0;
+  __shared__ int skip;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i <= RING; ++i) tc::mbar_init(&bars[i], 1);
+    tc::mbar_init_fence();
+    // a block of this launch whose copies never arrived: the result is void, start no more copies
+    skip = *(volatile const int*)err & kErrTimeout;
+  }
+  // which couples of the block pair hold pairs (bit t of the mask: couple cs + t)
+  if (threadIdx.x < 32) {
+    const unsigned m = __ballot_sync(0xffffffffu, threadIdx.x < B * HB && !couple_empty(couples[cs + threadIdx.x]));
+    if (threadIdx.x == 0) live_mask = m;
+  }
+  __syncthreads();
+  if (skip) return;  // the same for every thread of the block
+  const unsigned live = live_mask;
+
+  // iteration k's couple tile -> ring slot k % RING (thread 0 only)
+  auto issue = [&](int k) {
+    if (k >= ITERS) return;
+    uint64_t* bar = &bars[k % RING];
+    tma::expect_tx(bar, kTileBytes);
+    tma::load4d(tiles + (k % RING) * N * LN, mapW, 2 * z0, cs - c0 + k * CPI, 0, x, bar);
+  };
+  if (threadIdx.x == 0) {
+    tma::expect_tx(&bars[RING], 2 * kOrbTileBytes);
+    tma::load4d(phiI, mapOrb, z0, 0, I0, x, &bars[RING]);
+    tma::load4d(accI, mapOrb, z0, 0, J0, x, &bars[RING]);
+#pragma unroll
+    for (int k = 0; k < RING - 1; ++k) issue(k);
+  }
+  for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
+
+  // a wait that runs out is retried once (the copy may still land); after that the block reports
+  // the timeout and waits no more
+  bool waits_ok = true;
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    if (waits_ok && !tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles) &&
+        !tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles))
+      waits_ok = false;
+  };
+  wait(&bars[RING], 0);
+
+  long long goff[NP];
+  bool ok[NP];
+  T phiJ[NP][B], accJ[NP][B];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int p = threadIdx.x + k * NT;
+    const int y = p / ZC, zz = p - y * ZC;
+    ok[k] = p < PTS && zz < zcn;
+    goff[k] = rowoff + (long long)y * N + zz;
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      phiJ[k][j] = ok[k] ? accI[j * PTS + p] : T(0);
+      accJ[k][j] = T(0);
+    }
+  }
+  __syncthreads();  // twiddles stored; phi_J read (accI is rewritten from the first row on)
+
+  for (int kk = 0; kk < ITERS; ++kk) {
+    if (threadIdx.x == 0) issue(kk + RING - 1);
+    C* buf = tiles + (kk % RING) * N * LN;
+    wait(&bars[kk % RING], (uint32_t)((kk / RING) & 1));
+    const unsigned dead = (~live >> (kk * CPI)) & ((1u << CPI) - 1u);
+    if (dead) {  // the same for every thread of the block
+      for (int i = threadIdx.x; i < N * LN; i += NT)
+        if ((dead >> ((i / ZC) % CPI)) & 1u) buf[i] = C{};
+      __syncthreads();
+    }
+    stages<N, true, 0, P.ns, LN, 1, LN, NT>(buf, tw);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = threadIdx.x + k * NT;
+      if (!ok[k]) continue;
+      const int y = p / ZC, zz = p - y * ZC;
+#pragma unroll
+      for (int u = 0; u < RPI; ++u) {
+        const int r = kk * RPI + u;
+        const C* vp = buf + y * LN + u * HB * ZC + zz;
+        const T phii = phiI[r * PTS + p];
+        T acci = T(0);
+#pragma unroll
+        for (int t = 0; t < HB; ++t) {
+          const C v = vp[t * ZC];
+          acci += v.x * phiJ[k][2 * t] + v.y * phiJ[k][2 * t + 1];
+          accJ[k][2 * t] += v.x * phii;
+          accJ[k][2 * t + 1] += v.y * phii;
+        }
+        accI[r * PTS + p] = acci;
+      }
+    }
+    // this thread's writes of the slot are ordered before the tensor copy that refills it
+    tc::fence_proxy_async();
+    __syncthreads();
+  }
+  if (!waits_ok) atomicOr(err, kErrTimeout);
+  // flush into the call's FP32 accumulator of V_x phi, every load before any store
   const T vs = (T)vscale;
   T old[NP][B];
 #pragma unroll

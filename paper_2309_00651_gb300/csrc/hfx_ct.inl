@@ -12,7 +12,8 @@ constexpr int kB = 8;
 
 cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x) {
   const void* ks[] = {(const void*)ct::k_fwd_yz_ct<float, kN>, (const void*)ct::k_x_coulomb_ct<float, kN>,
-                      (const void*)ct::k_y_acc_dense_ct<float, kN, kB>, (const void*)ct::k_y_acc_diag_ct<float, kN, kB>};
+                      (const void*)ct::k_y_acc_dense_ct<float, kN, kB>, (const void*)ct::k_y_acc_dense_tma<float, kN, kB>,
+                      (const void*)ct::k_y_acc_diag_ct<float, kN, kB>};
   for (const void* k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dynamic_smem);
     if (e != cudaSuccess) return e;
@@ -43,6 +44,13 @@ void y_acc_dense(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }
 
+void y_acc_dense_tma(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& tmW, const CUtensorMap& tmOrb,
+                     long long Ntot, const int4* couples, const int* slot_list, const int* slot_couple_base,
+                     const int2* slot_blocks, int c0, const float2* tw, float* V, double vscale, int* err) {
+  ct::k_y_acc_dense_tma<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
+      tmW, tmOrb, couples, slot_list, slot_couple_base, slot_blocks, c0, tw, V, Ntot, vscale, err);
+}
+
 void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
                 const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* W,
                 const float2* tw, float* V, double vscale) {
@@ -50,7 +58,8 @@ void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long 
       orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
 }
 
-const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense, &y_acc_diag};
+const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense,
+                    &y_acc_dense_tma, &y_acc_diag};
 
 }  // namespace
 

@@ -86,6 +86,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long 
   return false;
 }
 
+// the same wait bounded by `cycles` clock cycles of this SM instead of a poll count
+__device__ __forceinline__ bool mbar_wait_cycles(uint64_t* mbar, uint32_t parity, long long cycles) {
+  const uint32_t a = smem_u32(mbar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+    if (clock64() - t0 > cycles) return false;
+  }
+}
+
 // 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 (w mod 4) ...)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];

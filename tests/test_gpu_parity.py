@@ -346,3 +346,35 @@ def test_compile_time_passes_with_sparse_pair_list():
     E, V = run_gpu(phi, sub, w.lattice, "fp32")
     assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
     assert_v_close(V, V_ref, TOL["fp32"])
+
+
+@pytest.mark.parametrize("dense_tma", ["1", "0"])
+@pytest.mark.parametrize("n,n_orb", [(32, 16), (48, 24)])
+def test_dense_pass_ignores_stale_transforms_of_empty_couples(dense_tma, n, n_orb, monkeypatch):
+    """The compile-time dense accumulate pass reads whole couple tiles of the transform buffer (by
+    TMA, or with HFX_DENSE_TMA=0 by per-thread copies).  Couples whose two pairs are both missing
+    are never transformed, so their slots hold whatever was there before; they must contribute
+    nothing.  The workspace is filled with NaN bytes first and a sparse pair list leaves such
+    couples in the full off-diagonal block pairs."""
+    monkeypatch.setenv("HFX_DENSE_TMA", dense_tma)
+    from paper_2309_00651_gb300 import hfx
+    L = 0.4 * n
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=n + 5, frac=0.2)
+    allp = I.all_pairs(n_orb)
+    rng = np.random.default_rng(n)
+    sub = allp[np.sort(rng.permutation(len(allp))[: len(allp) // 4])]
+    E_ref, V_ref = O.exchange(phi, sub, lat)
+    ex = hfx.Exchange(lat, (n, n, n), precision="fp32")
+    st = hfx.hfx_plan_stats(ex.ctx, n_orb, len(sub))
+    ex.ensure_workspace(n_orb, len(sub))
+    ex._ws.fill_(0xFF)  # every FP32 word of the workspace is a NaN
+    phi_d = torch.from_numpy(phi).cuda()
+    E, V = ex.apply(phi_d, torch.from_numpy(sub.astype(np.int32)).cuda())
+    ex.sync_status()
+    V = V.cpu().numpy()
+    ex.close()
+    assert st["dense_couples"] > 0
+    assert np.isfinite(V).all()
+    assert abs(E.item() - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert_v_close(V, V_ref, TOL["fp32"])
