@@ -306,6 +306,8 @@ struct hfx_ctx {
   // the compile-time dense accumulate pass moves its tiles by TMA (HFX_DENSE_TMA=0: per-thread
   // asynchronous copies)
   bool dense_tma = true;
+  // the compile-time forward and x passes prefetch their next work item into L2 (HFX_PREFETCH=0: no)
+  bool prefetch = true;
   // HFX_PREC_MIXED_TC: the forward plane pass's DFTs on the tensor cores (pre-split DFT matrix)
   bool tc_dft = false;
   void* d_dftb = nullptr;
@@ -622,6 +624,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (const char* s = std::getenv("HFX_PIPELINE")) c->pipeline = atoi(s) != 0;
   if (const char* s = std::getenv("HFX_NO_TC")) c->ace_tc = atoi(s) == 0;
   if (const char* s = std::getenv("HFX_DENSE_TMA")) c->dense_tma = atoi(s) != 0;
+  if (const char* s = std::getenv("HFX_PREFETCH")) c->prefetch = atoi(s) != 0;
 
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
@@ -1073,7 +1076,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       } else if (ct) {
         const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
         ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
-                   (const float2*)c->d_twct);
+                   (const float2*)c->d_twct, c->prefetch ? 1 : 0);
       } else {
         Passes<T>::fwd_yz(g, std::max(grid1, 1), smem_fwd(c), fs, orb, couples, c0, c1, W, (const C*)c->d_tw[1],
                           (const C*)c->d_tw[2]);
@@ -1083,7 +1086,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       if (ct) {
         const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
         ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
-                      (const float2*)c->d_twct, epart, energy_only ? 1 : 0);
+                      (const float2*)c->d_twct, epart, energy_only ? 1 : 0, c->prefetch ? 1 : 0);
       } else {
         Passes<T>::x_coulomb(g, std::max(grid2, 1), smem_x(c), fs, couples, c0, c1, W, (const T*)c->d_vtab,
                              (const C*)c->d_tw[0], (const C*)c->d_tw[2], epart, energy_only ? 1 : 0);

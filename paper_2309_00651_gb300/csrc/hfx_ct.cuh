@@ -182,6 +182,12 @@ __device__ __forceinline__ double widen_exact(float v) {
 
 constexpr int kUnroll = 4;
 
+// an asynchronous prefetch of `bytes` (a multiple of 16) at the 16-byte-aligned global address p
+// into L2; nothing is returned to the issuing thread
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ----------------------------------------------------------------------------------
 // pass 1: pair product + forward FFT along z and y of one x-plane
 // ----------------------------------------------------------------------------------
@@ -239,7 +245,7 @@ __device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long l
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreadsPlane, 3)
 k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples, int c0, int c1,
-            cx<T>* __restrict__ W, const cx<T>* __restrict__ twg) {
+            cx<T>* __restrict__ W, const cx<T>* __restrict__ twg, int prefetch) {
   using C = cx<T>;
   constexpr int S = N + 1;
   constexpr StagePlan P = Plan<N>::p;
@@ -252,6 +258,14 @@ k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ 
     // x-major order: the blocks in flight work on the same x-plane of many couples, whose orbital
     // planes (the batch's orbitals at that x) are then read from DRAM once and from L2 after
     const int x = it / ncl, cl = it - x * ncl;
+    // the four orbital planes of this block's next item head for L2 while this one runs
+    const int nx = it + gridDim.x;
+    if (prefetch && nx < items && threadIdx.x < 4) {
+      const int x2 = nx / ncl;
+      const int4 cp = couples[c0 + nx - x2 * ncl];
+      const int o = threadIdx.x == 0 ? cp.x : threadIdx.x == 1 ? cp.y : threadIdx.x == 2 ? cp.z : cp.w;
+      if (o >= 0) prefetch_l2(orb + (long long)o * Ntot + (long long)x2 * N * N, N * N * sizeof(T));
+    }
     fwd_yz_ct_item<T, N>(orb, Ntot, couples, c0, W, buf, tw, cl * N + x);
   }
 }
@@ -341,7 +355,7 @@ __device__ __forceinline__ void x_coulomb_ct_item(const int4* __restrict__ coupl
 template <typename T, int N>
 __global__ void __launch_bounds__(kThreadsPlane, 4)
 k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
-               const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only) {
+               const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only, int prefetch) {
   using C = cx<T>;
   constexpr int S = N + 1;
   constexpr StagePlan P = Plan<N>::p;
@@ -353,6 +367,10 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
   int par = 0;
   const int items = (c1 - c0) * N;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    // the N rows (576 bytes at N = 72) of this block's next y-plane head for L2 while this one runs
+    const int nx = it + gridDim.x;
+    if (prefetch && nx < items && threadIdx.x < N)
+      prefetch_l2(W + ((long long)nx / N * N + threadIdx.x) * N * N + (long long)(nx % N) * N, N * sizeof(C));
     if (couple_empty(couples[c0 + it / N])) continue;
     x_coulomb_ct_item<T, N>(couples, c0, W, vtab, epart, energy_only, buf, tw, red, par, it);
     par ^= 1;

@@ -28,13 +28,14 @@ cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, in
 }
 
 void fwd_yz(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples, int c0,
-            int c1, float2* W, const float2* tw) {
-  ct::k_fwd_yz_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(orb, Ntot, couples, c0, c1, W, tw);
+            int c1, float2* W, const float2* tw, int prefetch) {
+  ct::k_fwd_yz_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(orb, Ntot, couples, c0, c1, W, tw, prefetch);
 }
 
 void x_coulomb(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
-               const float* vtab, const float2* tw, double* epart, int energy_only) {
-  ct::k_x_coulomb_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(couples, c0, c1, W, vtab, tw, epart, energy_only);
+               const float* vtab, const float2* tw, double* epart, int energy_only, int prefetch) {
+  ct::k_x_coulomb_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(couples, c0, c1, W, vtab, tw, epart, energy_only,
+                                                                    prefetch);
 }
 
 void y_acc_dense(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,

@@ -59,10 +59,11 @@ struct CtFns {
   int n;
   int dense_threads;                    // threads per block of the dense accumulation pass (B = 8)
   cudaError_t (*prepare)(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x);
+  // prefetch != 0: each block sends the data of its next work item to L2 while it works on one
   void (*fwd_yz)(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
-                 int c0, int c1, float2* W, const float2* tw);
+                 int c0, int c1, float2* W, const float2* tw, int prefetch);
   void (*x_coulomb)(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
-                    const float* vtab, const float2* tw, double* epart, int energy_only);
+                    const float* vtab, const float2* tw, double* epart, int energy_only, int prefetch);
   void (*y_acc_dense)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                       const int4* couples, const int* slot_list, const int* slot_couple_base,
                       const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale);
