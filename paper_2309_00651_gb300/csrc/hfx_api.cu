@@ -252,10 +252,10 @@ static bool encode_f32_4d(CUtensorMap* m, const void* base, const cuuint64_t dim
 
 // the maps the TMA dense accumulate pass reads for a cubic grid of edge n: a transform buffer of
 // `cap` couples, W[couple][x][y][z] complex FP32, as (z reals, couple, y, x) with boxes of 8
-// complex x `cpi` couples x n rows; the FP32 orbitals orb[orbital][x][y][z] as (z, y, orbital, x)
-// with boxes of 8 x n x 8
+// complex x `cpi` couples x n rows; the FP32 orbitals orb[orbital][x][y][z] and the FP32
+// accumulator V (same layout) as (z, y, orbital, x) with boxes of 8 x n x 8
 static bool encode_dense_maps(CUtensorMap* tmW, const void* W, long long cap, int cpi, CUtensorMap* tmOrb,
-                              const void* orb, int n_orb, int n) {
+                              const void* orb, CUtensorMap* tmV, const void* V, int n_orb, int n) {
   const cuuint64_t nn = (cuuint64_t)n, N3 = nn * nn * nn;
   const cuuint64_t dw[4] = {2 * nn, (cuuint64_t)cap, nn, nn};
   const cuuint64_t sw[3] = {N3 * 8, nn * 8, nn * nn * 8};
@@ -263,7 +263,8 @@ static bool encode_dense_maps(CUtensorMap* tmW, const void* W, long long cap, in
   const cuuint64_t dorb[4] = {nn, nn, (cuuint64_t)n_orb, nn};
   const cuuint64_t sorb[3] = {nn * 4, N3 * 4, nn * nn * 4};
   const cuuint32_t borb[4] = {8, (cuuint32_t)n, 8, 1};
-  return cap > 0 && encode_f32_4d(tmW, W, dw, sw, bw) && encode_f32_4d(tmOrb, orb, dorb, sorb, borb);
+  return cap > 0 && encode_f32_4d(tmW, W, dw, sw, bw) && encode_f32_4d(tmOrb, orb, dorb, sorb, borb) &&
+         encode_f32_4d(tmV, V, dorb, sorb, borb);
 }
 
 // ------------------------------------------------------------------------------------
@@ -1026,12 +1027,13 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
                                      (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
   // the tensor maps of the TMA dense accumulate pass (one per transform buffer)
-  CUtensorMap tmW[2], tmOrb;
+  CUtensorMap tmW[2], tmOrb, tmV;
   bool dense_tma = false;
   if (std::is_same<T, float>::value && c->ct && S.b == 8 && c->dense_tma && !energy_only) {
     const int cpi = dense_rows_ct(g.n1) * (S.b / 2);
-    dense_tma = encode_dense_maps(&tmW[0], Wbuf[0], S.max_batch_couples, cpi, &tmOrb, orb, n_orb, g.n1) &&
-                encode_dense_maps(&tmW[1], Wbuf[1], S.max_batch_couples, cpi, &tmOrb, orb, n_orb, g.n1);
+    dense_tma =
+        encode_dense_maps(&tmW[0], Wbuf[0], S.max_batch_couples, cpi, &tmOrb, orb, &tmV, vacc, n_orb, g.n1) &&
+        encode_dense_maps(&tmW[1], Wbuf[1], S.max_batch_couples, cpi, &tmOrb, orb, &tmV, vacc, n_orb, g.n1);
     // the buffers are 16-byte aligned and the edges multiples of 4, so the driver has no reason to refuse
     if (!dense_tma) return fail(HFX_ERR_CUDA, "cuTensorMapEncodeTiled refused the dense pass's tensor maps");
   }
@@ -1102,7 +1104,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
       if (nd > 0 && ct && S.b == 8 && dense_tma)  // [dense block pairs]
-        ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, g.N, couples,
+        ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, tmV, g.N, couples,
                             S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
                             (const float2*)c->d_twct, (float*)vacc, vscale, c->d_err);
       else if (nd > 0 && ct && S.b == 8)

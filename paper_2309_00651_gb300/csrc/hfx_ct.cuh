@@ -560,7 +560,8 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
 // thread issues each iteration's couple tile as one tensor copy (the 4-D box of 2 ZC reals x
 // RPI * HB couples x N rows of y at plane x, landing as [y][couple][zz]) and the two blocks'
 // orbital tiles as two more (box ZC x N x B, landing as [orbital][y][zz]); the copies complete on
-// mbarriers that every thread waits on with an iteration limit.  Couples without pairs are read
+// mbarriers that every thread waits on with a time limit.  The same boxes of the FP32 V_x phi
+// accumulator (tmV, laid out like the orbitals) are prefetched into L2 for the final flush.  Couples without pairs are read
 // like the others (their slots of W hold stale values) and cleared in shared memory before the
 // transform.
 constexpr long long kTmaWaitCycles = 1LL << 30;  // about half a second
@@ -568,7 +569,7 @@ constexpr long long kTmaWaitCycles = 1LL << 30;  // about half a second
 template <typename T, int N, int B>
 __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmOrb,
-                  const int4* __restrict__ couples, const int* __restrict__ slot_list,
+                  const __grid_constant__ CUtensorMap tmV, const int4* __restrict__ couples, const int* __restrict__ slot_list,
                   const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
                   const cx<T>* __restrict__ twg, T* __restrict__ V, long long Ntot, double vscale,
                   int* __restrict__ err) {
@@ -639,6 +640,9 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
     tma::load4d(accI, mapOrb, z0, 0, J0, x, &bars[RING]);
 #pragma unroll
     for (int k = 0; k < RING - 1; ++k) issue(k);
+    // the V_x phi tiles that the flush reads and rewrites at the end head for L2 now
+    tma::prefetch4d(&tmV, z0, 0, I0, x);
+    tma::prefetch4d(&tmV, z0, 0, J0, x);
   }
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
 

@@ -29,5 +29,13 @@ __device__ __forceinline__ void load4d(void* dst, const CUtensorMap* map, int c0
       : "memory");
 }
 
+// the same box sent to L2 only (no shared memory, no mbarrier): a prefetch of data read later
+__device__ __forceinline__ void prefetch4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
 }  // namespace tma
 }  // namespace hfx
