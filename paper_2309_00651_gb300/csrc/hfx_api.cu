@@ -309,6 +309,9 @@ struct hfx_ctx {
   bool dense_tma = true;
   // the compile-time forward and x passes prefetch their next work item into L2 (HFX_PREFETCH=0: no)
   bool prefetch = true;
+  // blocks of the compile-time forward and x passes per resident block slot (each block loops over
+  // items; HFX_GRID_WAVES)
+  int ct_waves = 16;
   // HFX_PREC_MIXED_TC: the forward plane pass's DFTs on the tensor cores (pre-split DFT matrix)
   bool tc_dft = false;
   void* d_dftb = nullptr;
@@ -626,6 +629,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (const char* s = std::getenv("HFX_NO_TC")) c->ace_tc = atoi(s) == 0;
   if (const char* s = std::getenv("HFX_DENSE_TMA")) c->dense_tma = atoi(s) != 0;
   if (const char* s = std::getenv("HFX_PREFETCH")) c->prefetch = atoi(s) != 0;
+  if (const char* s = std::getenv("HFX_GRID_WAVES")) c->ct_waves = std::max(1, std::min(64, atoi(s)));
 
   HFX_CUDA_TRY(cudaGetDevice(&c->device));
   HFX_CUDA_TRY(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device));
@@ -1076,7 +1080,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
         dft::fwd_yz_tc(g.n1, std::max(gt, 1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
                        (const unsigned char*)c->d_dftb, c->d_err);
       } else if (ct) {
-        const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * 8);
+        const int gct = (int)std::min<long long>(items1, (long long)c->sm_count * c->blocks_fwd_ct * c->ct_waves);
         ct->fwd_yz(std::max(gct, 1), smem_plane_ct(g.n1), fs, (const float*)orb, g.N, couples, c0, c1, (float2*)W,
                    (const float2*)c->d_twct, c->prefetch ? 1 : 0);
       } else {
@@ -1086,7 +1090,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       close(kProfFwd, e0, fs);
       e0 = mark(fs);
       if (ct) {
-        const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * 8);
+        const int gct = (int)std::min<long long>(items2, (long long)c->sm_count * c->blocks_x_ct * c->ct_waves);
         ct->x_coulomb(std::max(gct, 1), smem_plane_ct(g.n1), fs, couples, c0, c1, (float2*)W, (const float*)c->d_vtab,
                       (const float2*)c->d_twct, epart, energy_only ? 1 : 0, c->prefetch ? 1 : 0);
       } else {
