@@ -611,22 +611,6 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   const int I0 = blk.x * B, J0 = blk.y * B;
   const int cs = slot_couple_base[slot];
   const long long rowoff = (long long)x * PLANE + z0;
-  __shared__ int skip;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i <= RING; ++i) tc::mbar_init(&bars[i], 1);
-    tc::mbar_init_fence();
-    // a block of this launch whose copies never arrived: the result is void, start no more copies
-    skip = *(volatile const int*)err & kErrTimeout;
-  }
-  // which couples of the block pair hold pairs (bit t of the mask: couple cs + t)
-  if (threadIdx.x < 32) {
-    const unsigned m = __ballot_sync(0xffffffffu, threadIdx.x < B * HB && !couple_empty(couples[cs + threadIdx.x]));
-    if (threadIdx.x == 0) live_mask = m;
-  }
-  __syncthreads();
-  if (skip) return;  // the same for every thread of the block
-  const unsigned live = live_mask;
-
   // iteration k's couple tile -> ring slot k % RING (thread 0 only)
   auto issue = [&](int k) {
     if (k >= ITERS) return;
@@ -634,17 +618,33 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
     tma::expect_tx(bar, kTileBytes);
     tma::load4d(tiles + (k % RING) * N * LN, mapW, 2 * z0, cs - c0 + k * CPI, 0, x, bar);
   };
+  // thread 0 starts the copies at once: they do not depend on which couples hold pairs
+  __shared__ int skip;
   if (threadIdx.x == 0) {
-    tma::expect_tx(&bars[RING], 2 * kOrbTileBytes);
-    tma::load4d(phiI, mapOrb, z0, 0, I0, x, &bars[RING]);
-    tma::load4d(accI, mapOrb, z0, 0, J0, x, &bars[RING]);
+    for (int i = 0; i <= RING; ++i) tc::mbar_init(&bars[i], 1);
+    tc::mbar_init_fence();
+    // a block of this launch whose copies never arrived: the result is void, start no more copies
+    skip = *(volatile const int*)err & kErrTimeout;
+    if (!skip) {
+      tma::expect_tx(&bars[RING], 2 * kOrbTileBytes);
+      tma::load4d(phiI, mapOrb, z0, 0, I0, x, &bars[RING]);
+      tma::load4d(accI, mapOrb, z0, 0, J0, x, &bars[RING]);
 #pragma unroll
-    for (int k = 0; k < RING - 1; ++k) issue(k);
-    // the V_x phi tiles that the flush reads and rewrites at the end head for L2 now
-    tma::prefetch4d(&tmV, z0, 0, I0, x);
-    tma::prefetch4d(&tmV, z0, 0, J0, x);
+      for (int k = 0; k < RING - 1; ++k) issue(k);
+      // the V_x phi tiles that the flush reads and rewrites at the end head for L2 now
+      tma::prefetch4d(&tmV, z0, 0, I0, x);
+      tma::prefetch4d(&tmV, z0, 0, J0, x);
+    }
+  }
+  // which couples of the block pair hold pairs (bit t of the mask: couple cs + t)
+  if (threadIdx.x < 32) {
+    const unsigned m = __ballot_sync(0xffffffffu, threadIdx.x < B * HB && !couple_empty(couples[cs + threadIdx.x]));
+    if (threadIdx.x == 0) live_mask = m;
   }
   for (int i = threadIdx.x; i < P.twtotal; i += NT) tw[i] = twg[i];
+  __syncthreads();
+  if (skip) return;  // the same for every thread of the block
+  const unsigned live = live_mask;
 
   // a wait that runs out is retried once (the copy may still land); after that the block reports
   // the timeout and waits no more
@@ -671,7 +671,7 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
       accJ[k][j] = T(0);
     }
   }
-  __syncthreads();  // twiddles stored; phi_J read (accI is rewritten from the first row on)
+  // (a thread rewrites accI only at its own points, after it has read phi_J there)
 
   for (int kk = 0; kk < ITERS; ++kk) {
     if (threadIdx.x == 0) issue(kk + RING - 1);
