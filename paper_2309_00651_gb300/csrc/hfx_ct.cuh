@@ -230,8 +230,14 @@ __device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long l
       if ((NV % (kUnroll * NT) == 0) || i < NV) {
         const int p = 2 * i;
         const int y = p / N, z = p - y * N;  // N even: both points in row y
-        buf[y * S + z] = mk<C>(a1[u].x * a2[u].x, b1[u].x * b2[u].x);
-        buf[y * S + z + 1] = mk<C>(a1[u].y * a2[u].y, b1[u].y * b2[u].y);
+        const C c0 = mk<C>(a1[u].x * a2[u].x, b1[u].x * b2[u].x);
+        const C c1 = mk<C>(a1[u].y * a2[u].y, b1[u].y * b2[u].y);
+        // which of its two points a thread stores first: with ((i / 8) ^ y) odd the second, so that
+        // each store instruction of a warp covers every shared-memory bank twice (consecutive
+        // threads' points are 16 bytes apart; in one order they would use half of the banks)
+        const int sw = ((i >> 3) ^ y) & 1;
+        buf[y * S + z + sw] = sw ? c1 : c0;
+        buf[y * S + z + 1 - sw] = sw ? c0 : c1;
       }
     }
   }
