@@ -378,3 +378,21 @@ def test_dense_pass_ignores_stale_transforms_of_empty_couples(dense_tma, n, n_or
     assert np.isfinite(V).all()
     assert abs(E.item() - E_ref) <= TOL["fp32"] * abs(E_ref)
     assert_v_close(V, V_ref, TOL["fp32"])
+
+
+@pytest.mark.parametrize("prefetch,waves", [("0", "1"), ("1", "1"), ("0", "64")])
+def test_compile_time_passes_launch_shapes(prefetch, waves, monkeypatch):
+    """The compile-time forward and x passes loop over work items with a grid of HFX_GRID_WAVES
+    blocks per resident slot and send the next item's data to L2 ahead (HFX_PREFETCH); neither
+    setting may change the result."""
+    monkeypatch.setenv("HFX_PREFETCH", prefetch)
+    monkeypatch.setenv("HFX_GRID_WAVES", waves)
+    n, n_orb = 48, 20
+    L = 0.4 * n
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=n + 9, frac=0.2)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, "fp32")
+    assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert_v_close(V, V_ref, TOL["fp32"])
