@@ -22,7 +22,7 @@ LIB_DEBUG = os.path.join(PKG, "libhfx_debug.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["hfx_api.cu", "hfx_passes_f32.cu", "hfx_passes_f64.cu", "hfx_ace.cu", "hfx_ace_tc.cu", "hfx_dft_tc.cu", "hfx_scdm.cu", "hfx_sinr.cu", "hfx_peak.cu"] + [
-    f"hfx_ct_{n}.cu" for n in (32, 48, 64, 72, 96, 128)]
+    f"hfx_ct_{n}.cu" for n in (32, 48, 64, 72, 80, 90, 96, 128)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE] + ARCH
 

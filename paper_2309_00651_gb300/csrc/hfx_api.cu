@@ -1033,7 +1033,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   // the tensor maps of the TMA dense accumulate pass (one per transform buffer)
   CUtensorMap tmW[2], tmOrb, tmV;
   bool dense_tma = false;
-  if (std::is_same<T, float>::value && c->ct && S.b == 8 && c->dense_tma && !energy_only) {
+  // (tensor maps need 16-byte row strides: FP32 orbital rows of an edge that is a multiple of 4)
+  if (std::is_same<T, float>::value && c->ct && S.b == 8 && c->dense_tma && !energy_only && g.n1 % 4 == 0) {
     const int cpi = dense_rows_ct(g.n1) * (S.b / 2);
     dense_tma =
         encode_dense_maps(&tmW[0], Wbuf[0], S.max_batch_couples, cpi, &tmOrb, orb, &tmV, vacc, n_orb, g.n1) &&
@@ -1357,7 +1358,9 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
     P.slot_blocks = S->d_slot_blocks;
     P.twct = (const cx<T>*)c->d_twct;
     P.ct_n = (std::is_same<T, float>::value && c->ct && (c->grid[0] == 48 || c->grid[0] == 64 || c->grid[0] == 72 ||
-                                                        c->grid[0] == 96)) ? c->grid[0] : 0;
+                                                        c->grid[0] == 80 || c->grid[0] == 90 || c->grid[0] == 96))
+                 ? c->grid[0]
+                 : 0;
     P.err = c->d_err;
     P.vscale = -c->alpha / (double)c->N;
     P.escale = -0.5 * c->alpha * c->omega / ((double)c->N * (double)c->N);

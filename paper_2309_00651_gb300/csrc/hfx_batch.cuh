@@ -82,6 +82,8 @@ __device__ __forceinline__ bool ct_item(const BatchProblem<T>& P, int kind, int 
   return ct_item_n<T, 48>(P, kind, a0, local, smem_raw, redf, par) ||
          ct_item_n<T, 64>(P, kind, a0, local, smem_raw, redf, par) ||
          ct_item_n<T, 72>(P, kind, a0, local, smem_raw, redf, par) ||
+         ct_item_n<T, 80>(P, kind, a0, local, smem_raw, redf, par) ||
+         ct_item_n<T, 90>(P, kind, a0, local, smem_raw, redf, par) ||
          ct_item_n<T, 96>(P, kind, a0, local, smem_raw, redf, par);
 }
 

@@ -445,7 +445,10 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
   // phi_I (kept) and phi_J (staged in the accI area until it moves to registers) tiles, rows of
   // ZC reals; they join the first copy group
   {
-    constexpr int RPER = 16 / int(sizeof(T));  // reals per 16-byte copy
+    // reals per copy: 16 bytes where every orbital row starts on a 16-byte boundary (N a multiple
+    // of 16 / sizeof(T)), else 8 bytes
+    constexpr int CPB = (N * int(sizeof(T))) % 16 == 0 ? 16 : 8;
+    constexpr int RPER = CPB / int(sizeof(T));
     constexpr int VPR = ZC / RPER;
     for (int i = threadIdx.x; i < 2 * B * N * VPR; i += NT) {
       const int v = i % VPR;
@@ -455,9 +458,10 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
       const int o = oo < B ? I0 + oo : J0 + (oo - B);
       T* dst = (oo < B ? phiI + oo * PTS : accI + (oo - B) * PTS) + y * ZC + v * RPER;
       const int valid = zcn - v * RPER;
-      const int bytes = valid >= RPER ? 16 : (valid > 0 ? valid * int(sizeof(T)) : 0);
+      const int bytes = valid >= RPER ? CPB : (valid > 0 ? valid * int(sizeof(T)) : 0);
       const T* src = orb + (long long)o * Ntot + rowoff + (long long)y * N + v * RPER;
-      cp_async16(dst, bytes ? (const void*)src : (const void*)orb, bytes);
+      if constexpr (CPB == 16) cp_async16(dst, bytes ? (const void*)src : (const void*)orb, bytes);
+      else cp_async8(dst, bytes ? (const void*)src : (const void*)orb, bytes);
     }
   }
 

@@ -79,7 +79,10 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
 
   // the block's orbital tiles (rows of ZC reals) join the first copy group
   {
-    constexpr int RPER = 16 / int(sizeof(T));
+    // reals per copy: 16 bytes where every orbital row starts on a 16-byte boundary (N a multiple
+    // of 16 / sizeof(T)), else 8 bytes
+    constexpr int CPB = (N * int(sizeof(T))) % 16 == 0 ? 16 : 8;
+    constexpr int RPER = CPB / int(sizeof(T));
     constexpr int VPR = ZC / RPER;
     for (int i = threadIdx.x; i < B * N * VPR; i += NT) {
       const int v = i % VPR;
@@ -88,9 +91,10 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
       const int o = rest / N;
       T* dst = phis + o * PTS + y * ZC + v * RPER;
       const int valid = zcn - v * RPER;
-      const int bytes = valid >= RPER ? 16 : (valid > 0 ? valid * int(sizeof(T)) : 0);
+      const int bytes = valid >= RPER ? CPB : (valid > 0 ? valid * int(sizeof(T)) : 0);
       const T* src = orb + (long long)(I0 + o) * Ntot + rowoff + (long long)y * N + v * RPER;
-      cp_async16(dst, bytes ? (const void*)src : (const void*)orb, bytes);
+      if constexpr (CPB == 16) cp_async16(dst, bytes ? (const void*)src : (const void*)orb, bytes);
+      else cp_async8(dst, bytes ? (const void*)src : (const void*)orb, bytes);
     }
   }
 

@@ -90,7 +90,7 @@ void fwd_yz_tc(int n, int grid, cudaStream_t st, const float* orb, long long Nto
                int c1, float2* W, const unsigned char* dftb, int* err);
 }  // namespace dft
 
-#define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(96) X(128)
+#define HFX_CT_SIZES(X) X(32) X(48) X(64) X(72) X(80) X(90) X(96) X(128)
 #define HFX_CT_DECLARE(NN) const CtFns* ct_fns_##NN();
 HFX_CT_SIZES(HFX_CT_DECLARE)
 #undef HFX_CT_DECLARE

@@ -228,7 +228,7 @@ def test_large_tile_sparse_block_pair():
         assert_v_close(V, V_ref, TOL[prec])
 
 
-@pytest.mark.parametrize("n", [48, 64])
+@pytest.mark.parametrize("n", [48, 64, 80, 90])
 @pytest.mark.parametrize("no_ct", ["0", "1"])
 def test_compile_time_and_runtime_kernels(n, no_ct, monkeypatch):
     """FP32 cubic grids with an instantiated edge use compile-time-geometry kernels; HFX_NO_CT=1
@@ -349,7 +349,7 @@ def test_compile_time_passes_with_sparse_pair_list():
 
 
 @pytest.mark.parametrize("dense_tma", ["1", "0"])
-@pytest.mark.parametrize("n,n_orb", [(32, 16), (48, 24)])
+@pytest.mark.parametrize("n,n_orb", [(32, 16), (48, 24), (80, 16), (90, 16)])
 def test_dense_pass_ignores_stale_transforms_of_empty_couples(dense_tma, n, n_orb, monkeypatch):
     """The compile-time dense accumulate pass reads whole couple tiles of the transform buffer (by
     TMA, or with HFX_DENSE_TMA=0 by per-thread copies).  Couples whose two pairs are both missing
