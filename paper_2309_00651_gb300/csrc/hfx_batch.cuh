@@ -56,15 +56,17 @@ struct BatchProblem {
 
 // forward / x item of an FP32 problem through the compile-time passes of its edge; false when the
 // problem has none (the runtime-geometry item runs instead)
+// (tw_ok: the twiddle table of edge N is already in shared memory from this block's previous item)
 template <typename T, int N>
 __device__ __forceinline__ bool ct_item_n(const BatchProblem<T>& P, int kind, int a0, long long local,
-                                          unsigned char* smem_raw, float (*redf)[32], int par) {
+                                          unsigned char* smem_raw, float (*redf)[32], int par, bool tw_ok) {
   if constexpr (std::is_same<T, float>::value) {
     if (P.ct_n != N) return false;
     constexpr StagePlan SP = ct::Plan<N>::p;
     float2* buf = reinterpret_cast<float2*>(smem_raw);
     float2* tw = buf + N * (N + 1);
-    for (int i = threadIdx.x; i < SP.twtotal; i += blockDim.x) tw[i] = P.twct[i];
+    if (!tw_ok)
+      for (int i = threadIdx.x; i < SP.twtotal; i += blockDim.x) tw[i] = P.twct[i];
     if (kind == kTaskFwd)
       ct::fwd_yz_ct_item<float, N>(P.orb, P.g.N, P.couples, a0, P.W, buf, tw, (int)local);
     else
@@ -78,13 +80,13 @@ __device__ __forceinline__ bool ct_item_n(const BatchProblem<T>& P, int kind, in
 
 template <typename T>
 __device__ __forceinline__ bool ct_item(const BatchProblem<T>& P, int kind, int a0, long long local,
-                                        unsigned char* smem_raw, float (*redf)[32], int par) {
-  return ct_item_n<T, 48>(P, kind, a0, local, smem_raw, redf, par) ||
-         ct_item_n<T, 64>(P, kind, a0, local, smem_raw, redf, par) ||
-         ct_item_n<T, 72>(P, kind, a0, local, smem_raw, redf, par) ||
-         ct_item_n<T, 80>(P, kind, a0, local, smem_raw, redf, par) ||
-         ct_item_n<T, 90>(P, kind, a0, local, smem_raw, redf, par) ||
-         ct_item_n<T, 96>(P, kind, a0, local, smem_raw, redf, par);
+                                        unsigned char* smem_raw, float (*redf)[32], int par, bool tw_ok) {
+  return ct_item_n<T, 48>(P, kind, a0, local, smem_raw, redf, par, tw_ok) ||
+         ct_item_n<T, 64>(P, kind, a0, local, smem_raw, redf, par, tw_ok) ||
+         ct_item_n<T, 72>(P, kind, a0, local, smem_raw, redf, par, tw_ok) ||
+         ct_item_n<T, 80>(P, kind, a0, local, smem_raw, redf, par, tw_ok) ||
+         ct_item_n<T, 90>(P, kind, a0, local, smem_raw, redf, par, tw_ok) ||
+         ct_item_n<T, 96>(P, kind, a0, local, smem_raw, redf, par, tw_ok);
 }
 
 struct BatchTask {
@@ -128,6 +130,8 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
   __shared__ float redf[2][32];  // warp partials of the compile-time x items, alternating
   int par = 0;
   int* done = reinterpret_cast<int*>(queue + 1);
+  int cur = 0;         // thread 0: the task of this block's previous item (items only increase)
+  int ct_loaded = 0;   // edge whose compile-time twiddle table this block's shared memory holds
   for (;;) {
     if (threadIdx.x == 0) {
       int task = -1;
@@ -135,12 +139,9 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
       if (!*(volatile int*)&queue->abort) {
         item = (long long)atomicAdd(&queue->next, 1ull);
         if (item < total_items) {
-          int lo = 0, hi = ntasks - 1;  // last task whose first item <= item
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tasks[mid].first <= item) lo = mid; else hi = mid - 1;
-          }
-          task = lo;
+          // the last task whose first item <= item, scanning on from the previous one
+          while (cur + 1 < ntasks && tasks[cur + 1].first <= item) ++cur;
+          task = cur;
           const BatchTask tk = tasks[task];
           if (tk.dep >= 0) {
             const int target = tasks[tk.dep].items + tk.extra;
@@ -169,9 +170,11 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
     const long long local = s_item - tk.first;
     const Geo& g = P.g;
     if ((tk.kind == kTaskFwd || tk.kind == kTaskX) && P.ct_n > 0 &&
-        ct_item(P, tk.kind, tk.a0, local, smem_raw, redf, par)) {
+        ct_item(P, tk.kind, tk.a0, local, smem_raw, redf, par, ct_loaded == P.ct_n)) {
       if (tk.kind == kTaskX) par ^= 1;
+      ct_loaded = P.ct_n;
     } else if (tk.kind == kTaskFwd) {
+      ct_loaded = 0;  // the items below reuse the shared memory that held a twiddle table
       C* buf = reinterpret_cast<C*>(smem_raw);
       C* tw2 = buf + g.n2 * g.S;
       C* tw3 = tw2 + g.n2;
@@ -179,6 +182,7 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
       for (int i = threadIdx.x; i < g.n3; i += blockDim.x) tw3[i] = P.tw3[i];
       fwd_yz_item(g, P.orb, P.couples, tk.a0, P.W, tw2, tw3, buf, local);
     } else if (tk.kind == kTaskX) {
+      ct_loaded = 0;
       C* buf = reinterpret_cast<C*>(smem_raw);
       C* tw1 = buf + g.n1 * g.S;
       C* tw3 = tw1 + g.n1;
@@ -186,6 +190,7 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
       for (int i = threadIdx.x; i < g.n3; i += blockDim.x) tw3[i] = P.tw3[i];
       x_coulomb_item(g, P.couples, tk.a0, P.W, P.vtab, tw1, tw3, P.epart, P.energy_only != 0, buf, red, local);
     } else if (tk.kind == kTaskAcc) {
+      ct_loaded = 0;
       constexpr int ZC = ZChunk<T>::value;
       const int nzc = (g.n3 + ZC - 1) / ZC;
       const int zi = int(local % nzc);
@@ -212,6 +217,7 @@ k_batch_persistent(const BatchProblem<T>* __restrict__ probs, const BatchTask* _
         d[1] = hi;
       }
     } else {  // energy: E_x = scale * sum_g w_g sum_y epart[g][y], in a fixed order
+      ct_loaded = 0;  // (block_sum below uses only static shared memory; kept simple)
       double sacc = 0.0;
       for (int c = threadIdx.x; c < P.total_couples; c += blockDim.x) {
         const int4 cp = P.couples[c];
