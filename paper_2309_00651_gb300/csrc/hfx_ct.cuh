@@ -182,6 +182,15 @@ __device__ __forceinline__ double widen_exact(float v) {
 
 constexpr int kUnroll = 4;
 
+// resident blocks per SM the plane kernels of edge N are built for: at most `cap`, and no more than
+// the padded plane (N (N+1) complex FP32 plus the twiddles, ~1 KB) lets fit in an SM's 228 KB of
+// shared memory (asking for more would only cap the registers a thread may use)
+template <int N, int cap> struct PlaneBlocks {
+  static constexpr int bytes = N * (N + 1) * 8 + 1024 + 1024;
+  static constexpr int fit = (228 * 1024) / bytes;
+  static constexpr int value = fit < 1 ? 1 : (fit < cap ? fit : cap);
+};
+
 // an asynchronous prefetch of `bytes` (a multiple of 16) at the 16-byte-aligned global address p
 // into L2; nothing is returned to the issuing thread
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
@@ -249,7 +258,7 @@ __device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long l
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreadsPlane, 3)
+__global__ void __launch_bounds__(kThreadsPlane, (PlaneBlocks<N, 3>::value))
 k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples, int c0, int c1,
             cx<T>* __restrict__ W, const cx<T>* __restrict__ twg, int prefetch) {
   using C = cx<T>;
@@ -359,7 +368,7 @@ __device__ __forceinline__ void x_coulomb_ct_item(const int4* __restrict__ coupl
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreadsPlane, 4)
+__global__ void __launch_bounds__(kThreadsPlane, (PlaneBlocks<N, 4>::value))
 k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
                const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only, int prefetch) {
   using C = cx<T>;

@@ -228,7 +228,7 @@ def test_large_tile_sparse_block_pair():
         assert_v_close(V, V_ref, TOL[prec])
 
 
-@pytest.mark.parametrize("n", [48, 64, 80, 90])
+@pytest.mark.parametrize("n", [48, 64, 80, 90, 96])
 @pytest.mark.parametrize("no_ct", ["0", "1"])
 def test_compile_time_and_runtime_kernels(n, no_ct, monkeypatch):
     """FP32 cubic grids with an instantiated edge use compile-time-geometry kernels; HFX_NO_CT=1
