@@ -67,8 +67,9 @@ typedef enum {
 
 typedef enum {
   HFX_PREC_FP64 = 0,     /* all arithmetic in FP64                                       */
-  HFX_PREC_FP32 = 1,     /* pair products and FFTs in FP32; energy sums and the V_x phi
-                            accumulation in FP64                                          */
+  HFX_PREC_FP32 = 1,     /* pair products and FFTs in FP32; energy sums in FP64; V_x phi
+                            summed per call in an FP32 workspace accumulator (a few dozen
+                            additions per element) and widened exactly into the FP64 output */
   HFX_PREC_MIXED_TC = 2  /* as HFX_PREC_FP32, but the forward DFTs of the plane pass (along
                             z and y) run on the tensor cores: each axis one complex DFT as a
                             dense GEMM with split TF32 operands (hi + lo, three products)
@@ -97,7 +98,14 @@ typedef struct {
  *   out    : receives the new context (owned by the caller; free with hfx_destroy).
  * Allocates the context's small device tables (twiddles, the Coulomb table v(G) of N values)
  * on the current device.  Returns HFX_ERR_INVALID_ARG, HFX_ERR_UNSUPPORTED_GRID, HFX_ERR_OOM
- * or HFX_ERR_CUDA on failure (and *out = NULL). */
+ * or HFX_ERR_CUDA on failure (and *out = NULL).
+ * Environment variables read here (schedule and kernel-form choices; results do not depend on
+ * them beyond rounding order): HFX_BLOCK (orbitals per block), HFX_BATCH_MB (transform budget),
+ * HFX_PIPELINE=0 (one stream), HFX_NO_CT=1 (runtime-geometry kernels on every grid),
+ * HFX_PENCIL=1 (pencil form of the plane passes), HFX_NO_TC=1 (ACE contractions off the
+ * tensor cores), HFX_DENSE_TMA=0 (dense accumulate pass with per-thread copies instead of TMA),
+ * HFX_PREFETCH=0 (no L2 prefetch of the next work item), HFX_GRID_WAVES (blocks per resident
+ * slot of the compile-time plane passes, default 16). */
 hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hfx_kernel kernel,
                       double alpha, hfx_precision prec, hfx_ctx** out);
 
