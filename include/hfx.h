@@ -176,9 +176,16 @@ typedef struct {
 hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
                              void* cuda_stream);
 
-/* flag for hfx_apply_args of hfx_apply_batched only -- a failure-detection test: the problem's
- * first dependent wait expects one more finished item than its predecessor task has, so it can
- * only end by running out of the wait budget (HFX_ERR_TIMEOUT); no GPU fault is involved. */
+/* flag for failure-detection tests (no GPU fault is involved; the call's result is void):
+ *   in hfx_apply_args of hfx_apply_batched: the problem's first dependent wait expects one more
+ *   finished item than its predecessor task has, so it can only end by running out of the wait
+ *   budget (HFX_ERR_TIMEOUT);
+ *   with hfx_apply on an FP32 context whose dense accumulate pass moves its tiles by TMA (cubic
+ *   compile-time edges that are multiples of 4): the first tile barrier of every dense block
+ *   expects 16 bytes more than its tensor copy brings, so its wait runs out (about 1 s per block
+ *   resident at the time; later blocks of the launch skip their work) and hfx_sync_status
+ *   reports HFX_ERR_TIMEOUT; on other contexts the flag has no effect.
+ * hfx_apply_sequential rejects it. */
 #define HFX_TEST_STALL    0x100u
 
 /* hfx_apply_sequential -- the same problems as separate hfx_apply calls, one after another on

@@ -1111,7 +1111,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       if (nd > 0 && ct && S.b == 8 && dense_tma)  // [dense block pairs]
         ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, tmV, g.N, couples,
                             S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
-                            (const float2*)c->d_twct, (float*)vacc, vscale, c->d_err);
+                            (const float2*)c->d_twct, (float*)vacc, vscale, c->d_err,
+                            (flags & HFX_TEST_STALL) ? 1 : 0);
       else if (nd > 0 && ct && S.b == 8)
         ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                         S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
@@ -1151,7 +1152,8 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
 static hfx_status check_apply_args(const hfx_ctx* c, const void* orbitals, int32_t n_orb, const int32_t* pairs,
                                    int64_t n_pairs, uint32_t flags, const double* ex_dev, const double* vxphi) {
   if (!c) return fail(HFX_ERR_INVALID_ARG, "ctx is NULL");
-  if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32)) return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
+  if (flags & ~(HFX_ENERGY_ONLY | HFX_ACCUMULATE | HFX_ORBITALS_F32 | HFX_TEST_STALL))
+    return fail(HFX_ERR_INVALID_ARG, "unknown flag bits");
   if (n_orb <= 0) return fail(HFX_ERR_INVALID_ARG, "n_orb must be > 0");
   if (n_pairs < 0 || n_pairs > (int64_t)1 << 31) return fail(HFX_ERR_INVALID_ARG, "n_pairs out of range");
   if (!orbitals || !ex_dev) return fail(HFX_ERR_INVALID_ARG, "orbitals or ex_dev is NULL");

@@ -591,7 +591,7 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
                   const __grid_constant__ CUtensorMap tmV, const int4* __restrict__ couples, const int* __restrict__ slot_list,
                   const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
                   const cx<T>* __restrict__ twg, T* __restrict__ V, long long Ntot, double vscale,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, int stall) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
   constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
@@ -630,16 +630,25 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   const int I0 = blk.x * B, J0 = blk.y * B;
   const int cs = slot_couple_base[slot];
   const long long rowoff = (long long)x * PLANE + z0;
-  // iteration k's couple tile -> ring slot k % RING (thread 0 only)
+  // thread 0's account of its copies: couple tiles issued, tiles it has seen land (in order), and
+  // whether the orbital tiles have landed; what it has not seen land is waited for before exit
+  int issued = 0, landed = 0;
+  bool orb_landed = false;
+  // iteration k's couple tile -> ring slot k % RING (thread 0 only).  stall (a failure-detection
+  // test): the first tile's mbarrier expects 16 bytes more than the copy brings, so its wait can
+  // only end by running out
   auto issue = [&](int k) {
     if (k >= ITERS) return;
     uint64_t* bar = &bars[k % RING];
-    tma::expect_tx(bar, kTileBytes);
+    tma::expect_tx(bar, kTileBytes + (stall && k == 0 ? 16u : 0u));
     tma::load4d(tiles + (k % RING) * N * LN, mapW, 2 * z0, cs - c0 + k * CPI, 0, x, bar);
+    issued = k + 1;
   };
   // thread 0 starts the copies at once: they do not depend on which couples hold pairs
   __shared__ int skip;
+  __shared__ int failed;  // set by any thread whose wait ran out; read after the next barrier
   if (threadIdx.x == 0) {
+    failed = 0;
     for (int i = 0; i <= RING; ++i) tc::mbar_init(&bars[i], 1);
     tc::mbar_init_fence();
     // a block of this launch whose copies never arrived: the result is void, start no more copies
@@ -665,15 +674,18 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   if (skip) return;  // the same for every thread of the block
   const unsigned live = live_mask;
 
-  // a wait that runs out is retried once (the copy may still land); after that the block reports
-  // the timeout and waits no more
+  // a wait that runs out is retried once (the copy may still land); after that this thread waits
+  // no more, and the block stops at its next vote
   bool waits_ok = true;
-  auto wait = [&](uint64_t* bar, uint32_t parity) {
-    if (waits_ok && !tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles) &&
-        !tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles))
-      waits_ok = false;
+  auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+    if (!waits_ok) return false;
+    if (tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles) || tc::mbar_wait_cycles(bar, parity, kTmaWaitCycles))
+      return true;
+    waits_ok = false;
+    failed = 1;
+    return false;
   };
-  wait(&bars[RING], 0);
+  orb_landed = wait(&bars[RING], 0);
 
   long long goff[NP];
   bool ok[NP];
@@ -692,10 +704,16 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   }
   // (a thread rewrites accI only at its own points, after it has read phi_J there)
 
+  // every thread's waits so far have ended with their copies landed: the same verdict for the block
+  __syncthreads();
+  bool block_ok = *(volatile int*)&failed == 0;
+  // (a constant trip count, so the loop unrolls; after a failed vote the iterations do nothing)
+#pragma unroll
   for (int kk = 0; kk < ITERS; ++kk) {
+    if (!block_ok) continue;
     if (threadIdx.x == 0) issue(kk + RING - 1);
     C* buf = tiles + (kk % RING) * N * LN;
-    wait(&bars[kk % RING], (uint32_t)((kk / RING) & 1));
+    if (wait(&bars[kk % RING], (uint32_t)((kk / RING) & 1))) landed = kk + 1;
     const unsigned dead = (~live >> (kk * CPI)) & ((1u << CPI) - 1u);
     if (dead) {  // the same for every thread of the block
       for (int i = threadIdx.x; i < N * LN; i += NT)
@@ -724,11 +742,24 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
         accI[r * PTS + p] = acci;
       }
     }
-    // this thread's writes of the slot are ordered before the tensor copy that refills it
+    // this thread's writes of the slot are ordered before the tensor copy that refills it; the
+    // barrier also takes the block's vote on its waits (a copy that never landed stops the block
+    // before it starts another)
     tc::fence_proxy_async();
     __syncthreads();
+    block_ok = *(volatile int*)&failed == 0;
   }
-  if (!waits_ok) atomicOr(err, kErrTimeout);
+  if (!block_ok) {
+    if (threadIdx.x == 0) {
+      atomicOr(err, kErrTimeout);
+      // the copies this block started and has not seen land: waited for, again with a limit, so
+      // that none is still writing into this block's shared memory when it exits
+      if (!orb_landed) tc::mbar_wait_cycles(&bars[RING], 0, kTmaWaitCycles);
+      for (int k = landed; k < issued; ++k)
+        tc::mbar_wait_cycles(&bars[k % RING], (uint32_t)((k / RING) & 1), kTmaWaitCycles);
+    }
+    return;  // the call's result is void; hfx_sync_status reports HFX_ERR_TIMEOUT
+  }
   // flush into the call's FP32 accumulator of V_x phi, every load before any store
   const T vs = (T)vscale;
   T old[NP][B];
