@@ -1109,10 +1109,9 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       const int nd = S.dense_begin[b + 1] - S.dense_begin[b];
       const int ng = S.generic_begin[b + 1] - S.generic_begin[b];
       if (nd > 0 && ct && S.b == 8 && dense_tma)  // [dense block pairs]
-        ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, tmV, g.N, couples,
+        ct->y_acc_dense_tma(dim3(nzc, g.n1, nd), smem_dense_tma_ct(g.n1), st, tmW[b & 1], tmOrb, tmV, couples,
                             S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
-                            (const float2*)c->d_twct, (float*)vacc, vscale, c->d_err,
-                            (flags & HFX_TEST_STALL) ? 1 : 0);
+                            (const float2*)c->d_twct, vscale, c->d_err, (flags & HFX_TEST_STALL) ? 1 : 0);
       else if (nd > 0 && ct && S.b == 8)
         ct->y_acc_dense(dim3(nzc, g.n1, nd), smem_dense_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
                         S.d_dense_slots + S.dense_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,

@@ -590,8 +590,7 @@ __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmOrb,
                   const __grid_constant__ CUtensorMap tmV, const int4* __restrict__ couples, const int* __restrict__ slot_list,
                   const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
-                  const cx<T>* __restrict__ twg, T* __restrict__ V, long long Ntot, double vscale,
-                  int* __restrict__ err, int stall) {
+                  const cx<T>* __restrict__ twg, double vscale, int* __restrict__ err, int stall) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
   constexpr int ZC = G::ZC, PTS = G::PTS, NP = G::NP, NT = G::NT;
@@ -603,7 +602,6 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   constexpr int ITERS = B / RPI;
   constexpr uint32_t kTileBytes = N * LN * sizeof(C);
   constexpr uint32_t kOrbTileBytes = B * PTS * sizeof(T);
-  constexpr int PLANE = N * N;
   constexpr StagePlan P = Plan<N>::p;
   static_assert(B % RPI == 0, "rows per iteration must divide the block");
   static_assert(B * HB <= 32, "one mask word per block pair");
@@ -629,7 +627,6 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   const int2 blk = slot_blocks[slot];
   const int I0 = blk.x * B, J0 = blk.y * B;
   const int cs = slot_couple_base[slot];
-  const long long rowoff = (long long)x * PLANE + z0;
   // thread 0's account of its copies: couple tiles issued, tiles it has seen land (in order), and
   // whether the orbital tiles have landed; what it has not seen land is waited for before exit
   int issued = 0, landed = 0;
@@ -687,15 +684,13 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   };
   orb_landed = wait(&bars[RING], 0);
 
-  long long goff[NP];
   bool ok[NP];
   T phiJ[NP][B], accJ[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int p = threadIdx.x + k * NT;
     const int y = p / ZC, zz = p - y * ZC;
-    ok[k] = p < PTS && zz < zcn;
-    goff[k] = rowoff + (long long)y * N + zz;
+    ok[k] = p < PTS && zz < zcn;  // (points past z = N lie outside tmV: the flush skips them)
 #pragma unroll
     for (int j = 0; j < B; ++j) {
       phiJ[k][j] = ok[k] ? accI[j * PTS + p] : T(0);
@@ -704,6 +699,7 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
   }
   // (a thread rewrites accI only at its own points, after it has read phi_J there)
 
+  const T vs = (T)vscale;
   // every thread's waits so far have ended with their copies landed: the same verdict for the block
   __syncthreads();
   bool block_ok = *(volatile int*)&failed == 0;
@@ -739,7 +735,7 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
           accJ[k][2 * t] += v.x * phii;
           accJ[k][2 * t + 1] += v.y * phii;
         }
-        accI[r * PTS + p] = acci;
+        accI[r * PTS + p] = vs * acci;
       }
     }
     // this thread's writes of the slot are ordered before the tensor copy that refills it; the
@@ -760,29 +756,23 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
     }
     return;  // the call's result is void; hfx_sync_status reports HFX_ERR_TIMEOUT
   }
-  // flush into the call's FP32 accumulator of V_x phi, every load before any store
-  const T vs = (T)vscale;
-  T old[NP][B];
-#pragma unroll
-  for (int k = 0; k < NP; ++k)
-#pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(J0 + j) * Ntot + goff[k]) : T(0);
+  // flush: V_J (registers, scaled) goes where phi_I was, V_I (scaled as stored) is in accI; both
+  // are added into the call's FP32 accumulator of V_x phi by two tensor reduce-adds, which run at
+  // L2 (no block of this launch touches the same elements: its block pairs are disjoint)
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    if (!ok[k]) continue;
-#pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(J0 + j) * Ntot + goff[k]] = old[k][j] + vs * accJ[k][j];
-  }
-#pragma unroll
-  for (int k = 0; k < NP; ++k)
-#pragma unroll
-    for (int j = 0; j < B; ++j) old[k][j] = ok[k] ? __ldcg(V + (long long)(I0 + j) * Ntot + goff[k]) : T(0);
-#pragma unroll
-  for (int k = 0; k < NP; ++k) {
-    if (!ok[k]) continue;
     const int p = threadIdx.x + k * NT;
+    if (p >= PTS) continue;
 #pragma unroll
-    for (int j = 0; j < B; ++j) V[(long long)(I0 + j) * Ntot + goff[k]] = old[k][j] + vs * accI[j * PTS + p];
+    for (int j = 0; j < B; ++j) phiI[j * PTS + p] = vs * accJ[k][j];
+  }
+  tma::fence_proxy_async_shared();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma::reduce_add4d(&tmV, z0, 0, J0, x, phiI);
+    tma::reduce_add4d(&tmV, z0, 0, I0, x, accI);
+    tma::bulk_commit();
+    tma::bulk_wait_read_all();  // the sources stay in place until the tensor unit has read them
   }
 }
 

@@ -46,11 +46,10 @@ void y_acc_dense(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long
 }
 
 void y_acc_dense_tma(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& tmW, const CUtensorMap& tmOrb,
-                     const CUtensorMap& tmV, long long Ntot, const int4* couples, const int* slot_list, const int* slot_couple_base,
-                     const int2* slot_blocks, int c0, const float2* tw, float* V, double vscale, int* err,
-                     int stall) {
+                     const CUtensorMap& tmV, const int4* couples, const int* slot_list, const int* slot_couple_base,
+                     const int2* slot_blocks, int c0, const float2* tw, double vscale, int* err, int stall) {
   ct::k_y_acc_dense_tma<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
-      tmW, tmOrb, tmV, couples, slot_list, slot_couple_base, slot_blocks, c0, tw, V, Ntot, vscale, err, stall);
+      tmW, tmOrb, tmV, couples, slot_list, slot_couple_base, slot_blocks, c0, tw, vscale, err, stall);
 }
 
 void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,

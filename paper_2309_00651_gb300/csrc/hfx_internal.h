@@ -69,12 +69,13 @@ struct CtFns {
                       const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale);
   // the same pass with its tiles moved by TMA: tmW maps the batch's transform buffer (dimensions
   // z reals, couple, y, x), tmOrb the FP32 orbitals and tmV the FP32 accumulator V (both z, y,
-  // orbital, x); boxes as k_y_acc_dense_tma reads them, shared memory smem_dense_ct + 128; stall:
+  // orbital, x), into which the pass adds by tensor reduce-adds; boxes as k_y_acc_dense_tma reads
+  // them, shared memory smem_dense_ct + 128; stall:
   // the HFX_TEST_STALL failure-detection test (each block's first wait runs out)
   void (*y_acc_dense_tma)(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap& tmW, const CUtensorMap& tmOrb,
-                          const CUtensorMap& tmV, long long Ntot, const int4* couples, const int* slot_list, const int* slot_couple_base,
-                          const int2* slot_blocks, int c0, const float2* tw, float* V, double vscale, int* err,
-                          int stall);
+                          const CUtensorMap& tmV, const int4* couples, const int* slot_list,
+                          const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* tw,
+                          double vscale, int* err, int stall);
   // full diagonal block pairs (B = 8), same arguments and threads as the dense pass
   void (*y_acc_diag)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                      const int4* couples, const int* slot_list, const int* slot_couple_base,

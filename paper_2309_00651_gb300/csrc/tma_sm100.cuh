@@ -37,5 +37,20 @@ __device__ __forceinline__ void prefetch4d(const CUtensorMap* map, int c0, int c
                : "memory");
 }
 
+// element-wise add of the FP32 box at `src` (shared memory, 128-byte aligned, laid out as a load of
+// the same box would land) into the tensor at coordinates (c0 .. c3), performed at L2; elements
+// outside the tensor are skipped.  Completes in this thread's bulk group.
+__device__ __forceinline__ void reduce_add4d(const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                             const void* src) {
+  asm volatile("cp.reduce.async.bulk.tensor.4d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(tc::smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// until the shared-memory sources of this thread's committed bulk operations have been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// generic-proxy writes of shared memory become visible to the tensor (async) proxy
+__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 }  // namespace tma
 }  // namespace hfx
