@@ -680,7 +680,7 @@ extern "C" hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], doub
   if (prec == HFX_PREC_FP32 && !c->pencil && grid[0] == grid[1] && grid[1] == grid[2] && !(no_ct && atoi(no_ct) != 0)) {
     const CtFns* f = ct_fns(grid[0]);
     const int n = grid[0];
-    if (f && std::max({smem_plane_ct(n), smem_dense_tma_ct(n), smem_diag_ct(n, 8)}) + 512 <= (size_t)c->max_smem) {
+    if (f && std::max({smem_plane_ct(n), smem_dense_tma_ct(n), smem_diag_ct(n, 8) + 128}) + 512 <= (size_t)c->max_smem) {
       e = f->prepare(c->max_smem - 512, smem_plane_ct(n), &c->blocks_fwd_ct, &c->blocks_x_ct);
       if (e != cudaSuccess) { free_ctx_tables(c.get()); return fail(HFX_ERR_CUDA, "kernel setup: %s", cudaGetErrorString(e)); }
       auto tw = to_real_vec<float>(stage_twiddles(n));
@@ -1031,7 +1031,7 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
   const int dense_threads = std::min(dense_np == 2 ? DenseBounds<2>::threads : DenseBounds<4>::threads,
                                      (((pts + dense_np - 1) / dense_np) + 31) / 32 * 32);
   // the tensor maps of the TMA dense accumulate pass (one per transform buffer)
-  CUtensorMap tmW[2], tmOrb, tmV;
+  CUtensorMap tmW[2] = {}, tmOrb = {}, tmV = {};
   bool dense_tma = false;
   // (tensor maps need 16-byte row strides: FP32 orbital rows of an edge that is a multiple of 4)
   if (std::is_same<T, float>::value && c->ct && S.b == 8 && c->dense_tma && !energy_only && g.n1 % 4 == 0) {
@@ -1124,9 +1124,10 @@ static hfx_status run_passes(hfx_ctx* c, Schedule& S, const Layout& L, const Cal
       const int ndg = S.diag_begin[b + 1] - S.diag_begin[b];
       e0 = mark(st);
       if (ndg > 0)  // [full diagonal block pairs]; the generic pass takes whatever is left
-        ct->y_acc_diag(dim3(nzc, g.n1, ndg), smem_diag_ct(g.n1, 8), st, (const float*)orb, g.N, couples,
+        ct->y_acc_diag(dim3(nzc, g.n1, ndg), smem_diag_ct(g.n1, 8) + 128, st, (const float*)orb, g.N, couples,
                        S.d_diag_slots + S.diag_begin[b], S.d_slot_couple_base, S.d_slot_blocks, c0,
-                       (const float2*)W, (const float2*)c->d_twct, (float*)vacc, vscale);
+                       (const float2*)W, (const float2*)c->d_twct, (float*)vacc, vscale, tmV,
+                       dense_tma ? 1 : 0);
       if (ndg > 0) close(kProfAccGeneric, e0, st);
       e0 = mark(st);
       if (ng > 0)

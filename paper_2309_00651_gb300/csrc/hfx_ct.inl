@@ -54,9 +54,9 @@ void y_acc_dense_tma(dim3 grid, size_t smem, cudaStream_t st, const CUtensorMap&
 
 void y_acc_diag(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples,
                 const int* slot_list, const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* W,
-                const float2* tw, float* V, double vscale) {
+                const float2* tw, float* V, double vscale, const CUtensorMap& tmV, int tma_flush) {
   ct::k_y_acc_diag_ct<float, kN, kB><<<grid, ct::DenseGeo<float, kN>::NT, smem, st>>>(
-      orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale);
+      orb, Ntot, couples, slot_list, slot_couple_base, slot_blocks, c0, W, tw, V, vscale, tmV, tma_flush);
 }
 
 const CtFns kFns = {kN, ct::DenseGeo<float, kN>::NT, &prepare, &fwd_yz, &x_coulomb, &y_acc_dense,

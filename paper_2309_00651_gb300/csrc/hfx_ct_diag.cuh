@@ -13,6 +13,7 @@
 // stages in shared memory, as in the off-diagonal dense pass.
 #pragma once
 #include "hfx_ct.cuh"
+#include "tma_sm100.cuh"
 #include "hfx_internal.h"
 
 namespace hfx {
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples,
                 const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base,
                 const int2* __restrict__ slot_blocks, int c0, const cx<T>* __restrict__ W,
-                const cx<T>* __restrict__ twg, T* __restrict__ V, double vscale) {
+                const cx<T>* __restrict__ twg, T* __restrict__ V, double vscale,
+                const __grid_constant__ CUtensorMap tmV, int tma_flush) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
   using D = DiagLayout<B>;
@@ -56,14 +58,17 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
   constexpr int PER = 16 / int(sizeof(C));
   constexpr int PLANE = N * N;
   constexpr StagePlan P = Plan<N>::p;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int z0 = blockIdx.x * ZC;
   const int zcn = min(ZC, N - z0);
   const int x = blockIdx.y;
   const int slot = slot_list[blockIdx.z];
-  C* tiles = reinterpret_cast<C*>(smem_raw);  // RING x [N][LN]
-  C* tw = tiles + RING * N * LN;
-  T* phis = reinterpret_cast<T*>(tw + P.twtotal);  // [B][PTS] staging of the block's orbitals
+  static_assert((RING * N * LN * sizeof(C)) % 128 == 0, "the staging tile starts on a 128-byte boundary");
+  unsigned char* base = smem_raw + ((128u - (tc::smem_u32(smem_raw) & 127u)) & 127u);
+  C* tiles = reinterpret_cast<C*>(base);  // RING x [N][LN]
+  // [B][PTS] staging of the block's orbitals; at the end, of the scaled V_x phi sums
+  T* phis = reinterpret_cast<T*>(tiles + RING * N * LN);
+  C* tw = reinterpret_cast<C*>(phis + B * PTS);
 
   const int I0 = slot_blocks[slot].x * B;
   const int cs = slot_couple_base[slot];
@@ -176,9 +181,29 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
     __syncthreads();
   });
 
+  const T vs = (T)vscale;
+  if (tma_flush) {
+    // the scaled sums go where the orbital tiles were (read into registers in the first
+    // iteration) and are added into the call's FP32 accumulator of V_x phi at L2 by one tensor
+    // reduce-add (tmV: the accumulator as (z, y, orbital, x), box 8 x N x 8)
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int p = threadIdx.x + k * NT;
+      if (p >= PTS) continue;
+#pragma unroll
+      for (int j = 0; j < B; ++j) phis[j * PTS + p] = vs * acc[k][j];
+    }
+    tma::fence_proxy_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tma::reduce_add4d(&tmV, z0, 0, I0, x, phis);
+      tma::bulk_commit();
+      tma::bulk_wait_read_all();
+    }
+    return;
+  }
   // read-modify-write of the block's rows of the call's FP32 accumulator of V_x phi: every load
   // before any store
-  const T vs = (T)vscale;
   T old[NP][B];
 #pragma unroll
   for (int k = 0; k < NP; ++k)

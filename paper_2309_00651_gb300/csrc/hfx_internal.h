@@ -76,10 +76,13 @@ struct CtFns {
                           const CUtensorMap& tmV, const int4* couples, const int* slot_list,
                           const int* slot_couple_base, const int2* slot_blocks, int c0, const float2* tw,
                           double vscale, int* err, int stall);
-  // full diagonal block pairs (B = 8), same arguments and threads as the dense pass
+  // full diagonal block pairs (B = 8), same arguments and threads as the dense pass; tma_flush:
+  // add the block's sums into V by one tensor reduce-add through tmV (else a read-modify-write);
+  // shared memory smem_diag_ct + 128
   void (*y_acc_diag)(dim3 grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot,
                      const int4* couples, const int* slot_list, const int* slot_couple_base,
-                     const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale);
+                     const int2* slot_blocks, int c0, const float2* W, const float2* tw, float* V, double vscale,
+                     const CUtensorMap& tmV, int tma_flush);
 };
 
 // Forward plane pass with the DFT stages on the tensor cores (hfx_dft_tc.cu): cubic FP32 grids of
