@@ -182,6 +182,13 @@ __device__ __forceinline__ double widen_exact(float v) {
 
 constexpr int kUnroll = 4;
 
+// threads per block of the compile-time plane kernels: 256, but 512 where the padded plane is so
+// large that one block fills an SM's shared memory (N = 128), so that 16 warps rather than 8 hide
+// the latency of each SM's single plane
+template <int N> struct PlaneThreads {
+  static constexpr int value = N * (N + 1) * 8 > 114 * 1024 ? 2 * kThreadsPlane : kThreadsPlane;
+};
+
 // resident blocks per SM the plane kernels of edge N are built for: at most `cap`, and no more than
 // the padded plane (N (N+1) complex FP32 plus the twiddles, ~1 KB) lets fit in an SM's 228 KB of
 // shared memory (asking for more would only cap the registers a thread may use)
@@ -208,7 +215,7 @@ __device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long l
                                                cx<T>* buf, const cx<T>* tw, int it) {
   using C = cx<T>;
   using T2 = typename Two<T>::type;
-  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane, NV = PLANE / 2;
+  constexpr int S = N + 1, PLANE = N * N, NT = PlaneThreads<N>::value, NV = PLANE / 2;
   constexpr StagePlan P = Plan<N>::p;
   const int cl = it / N;
   const int x = it - cl * N;
@@ -258,7 +265,7 @@ __device__ __forceinline__ void fwd_yz_ct_item(const T* __restrict__ orb, long l
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreadsPlane, (PlaneBlocks<N, 3>::value))
+__global__ void __launch_bounds__(PlaneThreads<N>::value, (PlaneBlocks<N, 3>::value))
 k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ couples, int c0, int c1,
             cx<T>* __restrict__ W, const cx<T>* __restrict__ twg, int prefetch) {
   using C = cx<T>;
@@ -267,7 +274,7 @@ k_fwd_yz_ct(const T* __restrict__ orb, long long Ntot, const int4* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
-  for (int i = threadIdx.x; i < P.twtotal; i += kThreadsPlane) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < P.twtotal; i += PlaneThreads<N>::value) tw[i] = twg[i];
   const int ncl = c1 - c0, items = ncl * N;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {
     // x-major order: the blocks in flight work on the same x-plane of many couples, whose orbital
@@ -296,7 +303,7 @@ __device__ __forceinline__ void x_coulomb_ct_item(const int4* __restrict__ coupl
                                                   int energy_only, cx<T>* buf, const cx<T>* tw, float (*red)[32],
                                                   int par, int it) {
   using C = cx<T>;
-  constexpr int S = N + 1, PLANE = N * N, NT = kThreadsPlane;
+  constexpr int S = N + 1, PLANE = N * N, NT = PlaneThreads<N>::value;
   constexpr StagePlan P = Plan<N>::p;
   constexpr int RL = P.r[P.ns - 1];  // last forward stage (m = 1)
   static_assert(P.ns >= 2, "compile-time x pass needs at least two stages");
@@ -368,7 +375,7 @@ __device__ __forceinline__ void x_coulomb_ct_item(const int4* __restrict__ coupl
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreadsPlane, (PlaneBlocks<N, 4>::value))
+__global__ void __launch_bounds__(PlaneThreads<N>::value, (PlaneBlocks<N, 4>::value))
 k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restrict__ W, const T* __restrict__ vtab,
                const cx<T>* __restrict__ twg, double* __restrict__ epart, int energy_only, int prefetch) {
   using C = cx<T>;
@@ -378,7 +385,7 @@ k_x_coulomb_ct(const int4* __restrict__ couples, int c0, int c1, cx<T>* __restri
   C* buf = reinterpret_cast<C*>(smem_raw);
   C* tw = buf + N * S;
   __shared__ float red[2][32];  // warp partials of the plane energy, double-buffered by item parity
-  for (int i = threadIdx.x; i < P.twtotal; i += kThreadsPlane) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < P.twtotal; i += PlaneThreads<N>::value) tw[i] = twg[i];
   int par = 0;
   const int items = (c1 - c0) * N;
   for (int it = blockIdx.x; it < items; it += gridDim.x) {

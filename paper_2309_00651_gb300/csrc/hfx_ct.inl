@@ -9,6 +9,7 @@ namespace {
 
 constexpr int kN = HFX_CT_N;
 constexpr int kB = 8;
+constexpr int kNT = ct::PlaneThreads<kN>::value;  // threads per block of the plane kernels
 
 cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, int* blocks_x) {
   const void* ks[] = {(const void*)ct::k_fwd_yz_ct<float, kN>, (const void*)ct::k_x_coulomb_ct<float, kN>,
@@ -21,20 +22,20 @@ cudaError_t prepare(int max_dynamic_smem, size_t smem_plane, int* blocks_fwd, in
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_fwd, ct::k_fwd_yz_ct<float, kN>,
-                                                                kThreadsPlane, smem_plane);
+                                                                kNT, smem_plane);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_x, ct::k_x_coulomb_ct<float, kN>, kThreadsPlane,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_x, ct::k_x_coulomb_ct<float, kN>, kNT,
                                                        smem_plane);
 }
 
 void fwd_yz(int grid, size_t smem, cudaStream_t st, const float* orb, long long Ntot, const int4* couples, int c0,
             int c1, float2* W, const float2* tw, int prefetch) {
-  ct::k_fwd_yz_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(orb, Ntot, couples, c0, c1, W, tw, prefetch);
+  ct::k_fwd_yz_ct<float, kN><<<grid, kNT, smem, st>>>(orb, Ntot, couples, c0, c1, W, tw, prefetch);
 }
 
 void x_coulomb(int grid, size_t smem, cudaStream_t st, const int4* couples, int c0, int c1, float2* W,
                const float* vtab, const float2* tw, double* epart, int energy_only, int prefetch) {
-  ct::k_x_coulomb_ct<float, kN><<<grid, kThreadsPlane, smem, st>>>(couples, c0, c1, W, vtab, tw, epart, energy_only,
+  ct::k_x_coulomb_ct<float, kN><<<grid, kNT, smem, st>>>(couples, c0, c1, W, vtab, tw, epart, energy_only,
                                                                     prefetch);
 }
 

@@ -396,3 +396,17 @@ def test_compile_time_passes_launch_shapes(prefetch, waves, monkeypatch):
     E, V = run_gpu(phi, pairs, lat, "fp32")
     assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
     assert_v_close(V, V_ref, TOL["fp32"])
+
+
+def test_compile_time_passes_128():
+    """128^3: the compile-time plane kernels run 512 threads per block (one block fills an SM's
+    shared memory), the dense accumulate pass one block of 512 per SM."""
+    n, n_orb = 128, 10
+    L = 0.4 * n
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=n + 3, frac=0.2)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, "fp32")
+    assert abs(E - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert_v_close(V, V_ref, TOL["fp32"])
