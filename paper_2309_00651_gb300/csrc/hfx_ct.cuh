@@ -587,16 +587,17 @@ k_y_acc_dense_ct(const T* __restrict__ orb, long long Ntot, const int4* __restri
 // RPI * HB couples x N rows of y at plane x, landing as [y][couple][zz]) and the two blocks'
 // orbital tiles as two more (box ZC x N x B, landing as [orbital][y][zz]); the copies complete on
 // mbarriers that every thread waits on with a time limit.  The same boxes of the FP32 V_x phi
-// accumulator (tmV, laid out like the orbitals) are prefetched into L2 for the final flush.  Couples without pairs are read
-// like the others (their slots of W hold stale values) and cleared in shared memory before the
-// transform.
+// accumulator (tmV, laid out like the orbitals) are prefetched into L2 at the start, and the
+// block's scaled sums are added into them at the end by two tensor reduce-adds.  Couples without
+// pairs are read like the others (their slots of W hold stale values) and cleared in shared
+// memory before the transform.
 constexpr long long kTmaWaitCycles = 1LL << 30;  // about half a second
 
 template <typename T, int N, int B>
 __global__ void __launch_bounds__(DenseGeo<T, N>::NT, DenseGeo<T, N>::MINB)
 k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant__ CUtensorMap tmOrb,
-                  const __grid_constant__ CUtensorMap tmV, const int4* __restrict__ couples, const int* __restrict__ slot_list,
-                  const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
+                  const __grid_constant__ CUtensorMap tmV, const int4* __restrict__ couples,
+                  const int* __restrict__ slot_list, const int* __restrict__ slot_couple_base, const int2* __restrict__ slot_blocks, int c0,
                   const cx<T>* __restrict__ twg, double vscale, int* __restrict__ err, int stall) {
   using C = cx<T>;
   using G = DenseGeo<T, N>;
@@ -773,7 +774,7 @@ k_y_acc_dense_tma(const __grid_constant__ CUtensorMap tmW, const __grid_constant
 #pragma unroll
     for (int j = 0; j < B; ++j) phiI[j * PTS + p] = vs * accJ[k][j];
   }
-  tma::fence_proxy_async_shared();
+  tc::fence_proxy_async();
   __syncthreads();
   if (threadIdx.x == 0) {
     tma::reduce_add4d(&tmV, z0, 0, J0, x, phiI);

@@ -193,7 +193,7 @@ k_y_acc_diag_ct(const T* __restrict__ orb, long long Ntot, const int4* __restric
 #pragma unroll
       for (int j = 0; j < B; ++j) phis[j * PTS + p] = vs * acc[k][j];
     }
-    tma::fence_proxy_async_shared();
+    tc::fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
       tma::reduce_add4d(&tmV, z0, 0, I0, x, phis);

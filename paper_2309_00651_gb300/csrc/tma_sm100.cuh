@@ -49,8 +49,6 @@ __device__ __forceinline__ void reduce_add4d(const CUtensorMap* map, int c0, int
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // until the shared-memory sources of this thread's committed bulk operations have been read
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// generic-proxy writes of shared memory become visible to the tensor (async) proxy
-__device__ __forceinline__ void fence_proxy_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 }  // namespace tma
 }  // namespace hfx
