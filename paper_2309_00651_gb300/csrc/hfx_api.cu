@@ -250,7 +250,8 @@ static bool encode_f32_4d(CUtensorMap* m, const void* base, const cuuint64_t dim
            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// the maps the TMA dense accumulate pass reads for a cubic grid of edge n: a transform buffer of
+// the maps of the TMA dense accumulate pass (tiles it reads; V also the tensor its reduce-adds
+// write) for a cubic grid of edge n: a transform buffer of
 // `cap` couples, W[couple][x][y][z] complex FP32, as (z reals, couple, y, x) with boxes of 8
 // complex x `cpi` couples x n rows; the FP32 orbitals orb[orbital][x][y][z] and the FP32
 // accumulator V (same layout) as (z, y, orbital, x) with boxes of 8 x n x 8
