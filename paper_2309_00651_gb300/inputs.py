@@ -251,6 +251,27 @@ def make_workload(w: Workload):
     return phi, pairs, info
 
 
+def save_workload(path: str, w: Workload, phi: np.ndarray, pairs: np.ndarray, info: Optional[dict] = None) -> None:
+    """Write a generated workload to one .npz file: the orbitals, the pair list and, as JSON, the
+    workload record (seed included) plus make_workload's info (cond(S), pair count).  A run can then
+    restart from exactly these inputs, or rebuild them from the record (make_workload(w) reproduces
+    the arrays bit for bit)."""
+    import json
+    meta = {"format": 1, "workload": dataclasses.asdict(w), "info": info or {}}
+    np.savez(path, phi=np.ascontiguousarray(phi, dtype=np.float64), pairs=np.ascontiguousarray(pairs, dtype=np.int32),
+             meta=np.array(json.dumps(meta)))
+
+
+def load_workload(path: str) -> Tuple[Workload, np.ndarray, np.ndarray, dict]:
+    """Read a file written by save_workload: (workload record, phi, pairs, info)."""
+    import json
+    with np.load(path, allow_pickle=False) as f:
+        meta = json.loads(str(f["meta"]))
+        if meta.get("format") != 1:
+            raise ValueError(f"{path}: unknown workload file format {meta.get('format')!r}")
+        return Workload(**meta["workload"]), f["phi"].copy(), f["pairs"].copy(), meta["info"]
+
+
 def random_pairs_subset(pairs: np.ndarray, k: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     idx = np.sort(rng.choice(len(pairs), size=min(k, len(pairs)), replace=False))

@@ -51,3 +51,28 @@ def test_screened_pairs_keep_diagonal():
     assert np.array_equal(p[:, 0], p[:, 1]) and len(p) == 12
     q = I.screened_pairs(phi, 12.0 ** 3, 0.0)
     assert len(q) == 12 * 13 // 2
+
+
+def test_save_and_load_workload_round_trip(tmp_path):
+    """Inputs saved with their record come back bit for bit, and the record alone rebuilds them."""
+    w = I.Workload("small_gauss", 10, 11.0, 20, 20.0, "gauss", seed=5, sigma=1.1, screen=1e-6)
+    phi, pairs, info = I.make_workload(w)
+    path = str(tmp_path / "small_gauss.npz")
+    I.save_workload(path, w, phi, pairs, info)
+    w2, phi2, pairs2, info2 = I.load_workload(path)
+    assert w2 == w
+    assert phi2.dtype == np.float64 and np.array_equal(phi2, phi)
+    assert pairs2.dtype == np.int32 and np.array_equal(pairs2, pairs)
+    assert info2 == info
+    phi3, pairs3, _ = I.make_workload(w2)
+    assert np.array_equal(phi3, phi) and np.array_equal(pairs3, pairs)
+
+
+def test_load_workload_rejects_unknown_format(tmp_path):
+    import json
+    path = str(tmp_path / "bad.npz")
+    np.savez(path, phi=np.zeros((1, 2, 2, 2)), pairs=np.zeros((1, 2), np.int32),
+             meta=np.array(json.dumps({"format": 99, "workload": {}, "info": {}})))
+    import pytest
+    with pytest.raises(ValueError, match="format"):
+        I.load_workload(path)
