@@ -273,6 +273,19 @@ hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]);
  * HFX_ERR_INVALID_ARG. */
 hfx_status hfx_debug_check_guards(hfx_ctx* c, void* cuda_stream);
 
+/* hfx_test_fail_allocation / hfx_test_live_allocations -- failure injection on the host, for
+ * tests of the error paths (the paper has no counterpart).  Every device allocation the library
+ * makes for itself (the context's tables in hfx_create, an n_orb's schedule tables on its first
+ * hfx_apply, the batch tables of hfx_apply_batched) goes through one allocator.  After
+ * hfx_test_fail_allocation(k), k >= 0, that allocator lets k allocations through and fails the
+ * next one as cudaMalloc does when the device is out of memory (cudaMalloc is not called for it);
+ * the call that needed it returns HFX_ERR_OOM and frees what it had allocated; later allocations
+ * succeed again.  k < 0 cancels a pending failure.  Process-wide, all devices and contexts.
+ * hfx_test_live_allocations returns the number of device allocations the library holds (all
+ * contexts): a failed call leaves it where it was before the call.  Neither touches the GPU. */
+void hfx_test_fail_allocation(int64_t k);
+int64_t hfx_test_live_allocations(void);
+
 /* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
  * thread's next libhfx call. */
 const char* hfx_last_error(void);

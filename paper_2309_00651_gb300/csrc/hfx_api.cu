@@ -447,6 +447,46 @@ static bool diag_available(const hfx_ctx* c) {
   return c->ct != nullptr && c->prec == HFX_PREC_FP32 && c->bsize == 8;
 }
 
+// Every device allocation the library makes for itself (context tables, schedules, batch tables)
+// goes through dev_alloc / dev_free: one place that counts what is held and that a test can make
+// fail (hfx_test_fail_allocation), so the error paths are exercised without exhausting a GPU.
+static std::mutex g_alloc_mu;
+static long long g_alloc_fail_in = -1;  // allocations to let through before one fails; -1: none fails
+static long long g_alloc_live = 0;      // device allocations held by the library, all contexts
+
+static cudaError_t dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_alloc_fail_in >= 0 && g_alloc_fail_in-- == 0) return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    ++g_alloc_live;
+  } else {
+    *p = nullptr;
+  }
+  return e;
+}
+
+static void dev_free(void* p) {
+  if (!p) return;
+  cudaFree(p);
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  --g_alloc_live;
+}
+
+extern "C" void hfx_test_fail_allocation(int64_t k) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  g_alloc_fail_in = k >= 0 ? (long long)k : -1;
+}
+
+extern "C" int64_t hfx_test_live_allocations(void) {
+  std::lock_guard<std::mutex> lk(g_alloc_mu);
+  return (int64_t)g_alloc_live;
+}
+
 static void free_ctx_tables(hfx_ctx* c) {
   for (cudaEvent_t* e : {&c->ev_fork, &c->ev_p2, &c->ev_p3[0], &c->ev_p3[1]}) {
     if (*e) cudaEventDestroy(*e);
@@ -454,27 +494,27 @@ static void free_ctx_tables(hfx_ctx* c) {
   }
   if (c->side) cudaStreamDestroy(c->side);
   c->side = nullptr;
-  if (c->d_twct) cudaFree(c->d_twct);
+  dev_free(c->d_twct);
   c->d_twct = nullptr;
-  if (c->d_batch) cudaFree(c->d_batch);
+  dev_free(c->d_batch);
   c->d_batch = nullptr;
-  if (c->d_dftb) cudaFree(c->d_dftb);
+  dev_free(c->d_dftb);
   c->d_dftb = nullptr;
   c->batch_bytes = 0;
   for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
   c->ev_pending.clear();
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
-  for (auto& p : c->d_tw) { if (p) cudaFree(p); p = nullptr; }
-  if (c->d_vtab) cudaFree(c->d_vtab);
-  if (c->d_err) cudaFree(c->d_err);
+  for (auto& p : c->d_tw) { dev_free(p); p = nullptr; }
+  dev_free(c->d_vtab);
+  dev_free(c->d_err);
   c->d_vtab = nullptr;
   c->d_err = nullptr;
   for (auto& kv : c->sched) {
     Schedule& S = *kv.second;
     for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
                     (void*)S.d_dense_slots, (void*)S.d_generic_slots, (void*)S.d_diag_slots})
-      if (p) cudaFree(p);
+      dev_free(p);
   }
   c->sched.clear();
 }
@@ -487,7 +527,7 @@ static std::vector<T> to_real_vec(const std::vector<double>& v) {
 }
 
 static hfx_status upload(void** dst, const void* src, size_t bytes) {
-  cudaError_t e = cudaMalloc(dst, bytes);
+  cudaError_t e = dev_alloc(dst, bytes);
   if (e != cudaSuccess) return fail(HFX_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
   e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(HFX_ERR_CUDA, "cudaMemcpy failed: %s", cudaGetErrorString(e));
@@ -550,7 +590,10 @@ static hfx_status build_tables(hfx_ctx* c) {
   if (c->prec == HFX_PREC_FP64) st = upload(&c->d_vtab, v.data(), v.size() * sizeof(double));
   else { auto f = to_real_vec<float>(v); st = upload(&c->d_vtab, f.data(), f.size() * sizeof(float)); }
   if (st != HFX_OK) return st;
-  HFX_CUDA_TRY(cudaMalloc(&c->d_err, sizeof(int)));
+  {
+    const cudaError_t e = dev_alloc((void**)&c->d_err, sizeof(int));
+    if (e != cudaSuccess) return fail(HFX_ERR_OOM, "cudaMalloc(%zu) failed: %s", sizeof(int), cudaGetErrorString(e));
+  }
   HFX_CUDA_TRY(cudaMemset(c->d_err, 0, sizeof(int)));
   return HFX_OK;
 }
@@ -785,7 +828,7 @@ static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
   std::unique_ptr<Schedule> S(new Schedule(make_host_schedule(c, n_orb)));
   auto up = [&](void** dst, const void* src, size_t bytes) -> hfx_status {
     if (bytes == 0) {  // an empty list still gets a valid (unused) device pointer
-      cudaError_t e = cudaMalloc(dst, 16);
+      cudaError_t e = dev_alloc(dst, 16);
       return e == cudaSuccess ? HFX_OK : fail(HFX_ERR_OOM, "cudaMalloc(16) failed: %s", cudaGetErrorString(e));
     }
     return upload(dst, src, bytes);
@@ -801,7 +844,7 @@ static hfx_status get_schedule(hfx_ctx* c, int n_orb, Schedule** out) {
   if (st != HFX_OK) {
     for (void* p : {(void*)S->d_slot_blocks, (void*)S->d_slot_of_bp, (void*)S->d_slot_couple_base,
                     (void*)S->d_dense_slots, (void*)S->d_generic_slots, (void*)S->d_diag_slots})
-      if (p) cudaFree(p);
+      dev_free(p);
     return st;
   }
   *out = S.get();
@@ -1452,10 +1495,10 @@ static hfx_status batched_persistent(hfx_ctx* const* ctxs, const hfx_apply_args*
     HFX_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone)
       return fail(HFX_ERR_INVALID_ARG, "the first batched call of this size on its lead context must come before stream capture");
-    if (lead->d_batch) { HFX_CUDA_TRY(cudaStreamSynchronize(st)); cudaFree(lead->d_batch); }
+    if (lead->d_batch) { HFX_CUDA_TRY(cudaStreamSynchronize(st)); dev_free(lead->d_batch); }
     lead->d_batch = nullptr;
     lead->batch_bytes = 0;
-    cudaError_t e = cudaMalloc(&lead->d_batch, off);
+    cudaError_t e = dev_alloc(&lead->d_batch, off);
     if (e != cudaSuccess) return fail(HFX_ERR_OOM, "cudaMalloc(%zu) for the batch tables failed: %s", off, cudaGetErrorString(e));
     lead->batch_bytes = off;
   }
@@ -1730,7 +1773,7 @@ extern "C" hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_byt
       Schedule& S = *kv.second;
       for (void* p : {(void*)S.d_slot_blocks, (void*)S.d_slot_of_bp, (void*)S.d_slot_couple_base,
                       (void*)S.d_dense_slots, (void*)S.d_generic_slots, (void*)S.d_diag_slots})
-        if (p) cudaFree(p);
+        dev_free(p);
     }
     c->sched.clear();
   }

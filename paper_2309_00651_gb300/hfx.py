@@ -36,7 +36,7 @@ EXPORTED = ("hfx_create", "hfx_workspace_bytes", "hfx_set_workspace", "hfx_apply
             "hfx_ace_workspace_bytes", "hfx_ace_build", "hfx_ace_apply", "hfx_screen_pairs", "hfx_ace_profile_read",
             "hfx_scdm_workspace_bytes", "hfx_scdm_localise",
             "hfx_sinr_update_n", "hfx_sinr_update_v", "hfx_sinr_update_x", "hfx_fma_peak",
-            "hfx_debug_check_guards")
+            "hfx_debug_check_guards", "hfx_test_fail_allocation", "hfx_test_live_allocations")
 HFX_NOALLOC_SCRATCH_BYTES = 32 << 20
 PASS_NAMES = ("stage", "fwd_yz", "x_coulomb", "y_acc_dense", "energy", "y_acc_generic")
 ACE_KERNEL_NAMES = ("ace_gram", "ace_lmul", "ace_small")
@@ -135,6 +135,10 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     L.hfx_fma_peak.restype = ctypes.c_int
     L.hfx_debug_check_guards.argtypes = [vp, vp]
     L.hfx_debug_check_guards.restype = ctypes.c_int
+    L.hfx_test_fail_allocation.argtypes = [i64]
+    L.hfx_test_fail_allocation.restype = None
+    L.hfx_test_live_allocations.argtypes = []
+    L.hfx_test_live_allocations.restype = i64
     _lib = L
     return L
 
@@ -487,3 +491,14 @@ def hfx_fma_peak(fp64: bool, iters: int = 20000, stream: Optional[torch.cuda.Str
 def hfx_debug_check_guards(ctx, stream: Optional[torch.cuda.Stream] = None) -> None:
     """HFX_DEBUG builds: enqueue the check of the workspace guard bands (see hfx_sync_status)."""
     _check(load_library().hfx_debug_check_guards(ctx, _stream_handle(stream)))
+
+
+def hfx_test_fail_allocation(k: int) -> None:
+    """Failure injection (tests): the library's device allocation after the next k fails as out of
+    memory; k < 0 cancels."""
+    load_library().hfx_test_fail_allocation(int(k))
+
+
+def hfx_test_live_allocations() -> int:
+    """Device allocations the library holds, all contexts."""
+    return int(load_library().hfx_test_live_allocations())

@@ -90,6 +90,26 @@ def test_host_side_argument_errors(lib):
     lib.hfx_destroy(None)
 
 
+def test_failure_injection_hook_on_the_host(lib):
+    """hfx_test_fail_allocation / hfx_test_live_allocations work without a GPU: argument errors are
+    found before any allocation, so a pending failure stays pending and nothing is held."""
+    from paper_2309_00651_gb300 import hfx
+    live0 = hfx.hfx_test_live_allocations()
+    assert live0 >= 0
+    box = hfx.HfxBox()
+    for a in range(3):
+        box.lattice[a][a] = 10.0
+    out = ctypes.c_void_p()
+    odd = (ctypes.c_int32 * 3)(15, 32, 32)
+    hfx.hfx_test_fail_allocation(0)
+    try:
+        assert lib.hfx_create(ctypes.byref(box), odd, 20.0, 0, 0.25, 1, ctypes.byref(out)) == -2
+        assert not out.value
+        assert hfx.hfx_test_live_allocations() == live0
+    finally:
+        hfx.hfx_test_fail_allocation(-1)
+
+
 def test_binding_fails_loudly_without_library(tmp_path):
     from paper_2309_00651_gb300 import hfx
     saved = hfx._lib
