@@ -398,11 +398,31 @@ def run_reference(args):
 PASS_KEYS = ("fwd_yz", "x_coulomb", "y_acc_dense", "y_acc_generic")
 
 
-def pass_rooflines(prof, steps, stats, N, csize, P, ms_step, peak):
+def measured_traffic(n, precision):
+    """DRAM bytes per couple of each pass from profiles/traffic.json (ncu counters of the bench
+    workload's own launches), for the grid edge and precision they were taken on and only while the
+    kernel sources are the ones they were taken on; {} otherwise."""
+    from paper_2309_00651_gb300 import build as B
+    prof_file = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(prof_file) as f:
+            tj = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    if tj.get("kernel_hash") != B.kernel_hash():
+        return {}
+    return {k: e["dram_bytes_per_couple"] for k, e in tj.get("kernels", {}).items()
+            if e.get("grid") == n and e.get("precision") == precision}
+
+
+def pass_rooflines(prof, steps, stats, N, csize, P, ms_step, peak, traffic=None):
     """Per pass: algorithmic bytes per step (per couple: forward pass writes the packed transform,
     8 N B in FP32; the x pass reads and writes it; the accumulate passes read it), device time per
     step from the library's per-launch CUDA events, and the fraction of the measured HBM peak;
-    plus the whole call at 16 N B per pair (FP32; 32 N B in FP64)."""
+    plus the whole call at 16 N B per pair (FP32; 32 N B in FP64).  Where `traffic` holds a pass's
+    measured DRAM bytes per couple, the pass also gets the DRAM bytes it moves per step and the
+    fraction of the HBM peak those bytes run at (`dram_frac`): how close the pass is to the DRAM
+    roofline in the bytes it really moves, compulsory re-reads included."""
     per_couple = {"fwd_yz": csize * N, "x_coulomb": 2 * csize * N, "y_acc_dense": csize * N,
                   "y_acc_generic": csize * N}
     couples_of = {"fwd_yz": stats["couples"], "x_coulomb": stats["couples"],
@@ -415,6 +435,10 @@ def pass_rooflines(prof, steps, stats, N, csize, P, ms_step, peak):
         b = per_couple[k] * couples_of[k]
         out[k] = {"ms_per_step": ms, "alg_bytes_per_step": b, "achieved_gbs": b / (ms / 1e3) / 1e9,
                   "frac": b / (ms / 1e3) / 1e9 / peak}
+        if traffic and k in traffic:
+            d = traffic[k] * couples_of[k]
+            out[k]["dram_bytes_per_step"] = d
+            out[k]["dram_frac"] = d / (ms / 1e3) / 1e9 / peak
     whole = 2 * csize * N * P
     out["whole_call"] = {"ms_per_step": ms_step, "alg_bytes_per_step": whole,
                          "achieved_gbs": whole / (ms_step / 1e3) / 1e9, "frac": whole / (ms_step / 1e3) / 1e9 / peak}
@@ -705,7 +729,8 @@ def main():
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "measured": "CUDA events around each launch, batches on one stream, K steps",
                 "pass_ms_per_step": {k: prof[k]["ms"] / args.steps for k in prof},
-                "passes": pass_rooflines(prof, args.steps, stats, N, csize, P, ms_step, peak)}
+                "passes": pass_rooflines(prof, args.steps, stats, N, csize, P, ms_step, peak,
+                                         measured_traffic(w.n, args.precision))}
 
     # end to end through the public API with host buffers: every step copies its orbitals and pair
     # list in from pinned host memory and its E_x and V_x phi back out.  Steps are pipelined the way
