@@ -60,6 +60,10 @@ typedef enum {
                                     canonical layout of its block pair                     */
 } hfx_status;
 
+/* Frequencies m_d in (-n_d/2, n_d/2], G = m1 b1 + m2 b2 + m3 b3.  On a Nyquist plane (m_d = n_d/2,
+ * even n_d) of a non-orthogonal cell the grid point and its mirror (-m mod n) have different |G|;
+ * the kernel used there is the mean of the two (its inversion-symmetric part), which keeps every
+ * pair potential real and equals the energy of v itself for real pair densities. */
 typedef enum {
   HFX_KERNEL_COULOMB = 0,        /* v = 4 pi/|G|^2 on the whole grid, v(0) = 0 (default)   */
   HFX_KERNEL_COULOMB_SPHERE = 1  /* also v = 0 where |G|^2/2 >= 4 ecut (pair-density sphere) */

@@ -575,16 +575,29 @@ static hfx_status build_tables(hfx_ctx* c) {
       mf[d][pos] = (f <= n / 2) ? f : f - n;
     }
   }
+  // v at the integer frequency m (each component in (-n/2, n/2])
+  auto kernel_at = [&](const int m[3]) {
+    double G[3];
+    for (int k = 0; k < 3; ++k) G[k] = m[0] * B[0][k] + m[1] * B[1][k] + m[2] * B[2][k];
+    const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    double val = (g2 > 0.0) ? 4.0 * kPi / g2 : 0.0;
+    if (c->kernel == HFX_KERNEL_COULOMB_SPHERE && 0.5 * g2 >= 4.0 * c->ecut) val = 0.0;
+    return val;
+  };
+  // The table holds the inversion-symmetric part of the kernel, (v(m) + v(m'))/2 with m' the
+  // frequency of grid index -k: m' = -m except on a Nyquist plane (m_d = n_d/2, its own mirror).
+  // In an orthogonal cell v(m') = v(m) bit for bit and nothing changes; in a non-orthogonal one
+  // the two differ on the Nyquist planes, and only the symmetric part keeps every v_ij real and
+  // the two-pairs-per-transform packing exact (for real pair densities it gives the same E_x as
+  // v itself, and V_x phi = the real part of the inverse transform of v F).
   std::vector<double> v((size_t)c->N);
   for (int a = 0; a < n1; ++a)
     for (int b = 0; b < n2; ++b)
       for (int e = 0; e < n3; ++e) {
-        double G[3];
-        for (int k = 0; k < 3; ++k) G[k] = mf[0][a] * B[0][k] + mf[1][b] * B[1][k] + mf[2][e] * B[2][k];
-        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
-        double val = (g2 > 0.0) ? 4.0 * kPi / g2 : 0.0;
-        if (c->kernel == HFX_KERNEL_COULOMB_SPHERE && 0.5 * g2 >= 4.0 * c->ecut) val = 0.0;
-        v[((size_t)a * n2 + b) * n3 + e] = val;
+        const int m[3] = {mf[0][a], mf[1][b], mf[2][e]};
+        int mm[3];
+        for (int d = 0; d < 3; ++d) mm[d] = (2 * m[d] == c->grid[d]) ? m[d] : -m[d];
+        v[((size_t)a * n2 + b) * n3 + e] = 0.5 * (kernel_at(m) + kernel_at(mm));
       }
   hfx_status st;
   if (c->prec == HFX_PREC_FP64) st = upload(&c->d_vtab, v.data(), v.size() * sizeof(double));

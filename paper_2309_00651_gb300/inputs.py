@@ -303,6 +303,27 @@ def complex_plane_wave_orbitals(kset: np.ndarray, L: float, n: int) -> np.ndarra
     return np.array(out)
 
 
+def skewed_basis_case(n: int = 24, L: float = 8.0, n_orb: int = 4, seed: int = 7):
+    """One cubic cell written in two bases: rows a1, a2, a3 and the skewed rows a1, a1 + a2, a3.
+
+    Grid point p of the skewed basis is r = ((p1 + p2)/n) a1 + (p2/n) a2 + (p3/n) a3, i.e. point
+    ((p1 + p2) mod n, p2, p3) of the cubic one, so phi_s[p1, p2] = phi[(p1 + p2) mod n, p2] is the
+    same periodic function.  The orbitals carry |m| <= 2 per axis, their pair densities |m| <= 4,
+    which in skewed indices is (m1, m1 + m2) with |m1 + m2| <= 8 < n/2: no Fourier coefficient of
+    a pair density lies where the two bases fold frequencies differently, so the discrete exchange
+    is the same in both.  Returns (phi, phi_s, lattice, skewed lattice, src) with
+    src[p1, p2] = (p1 + p2) mod n."""
+    ecut = 0.5 * (2 * math.pi * 2.5 / L) ** 2  # |m|^2 < 6.25
+    raw = random_pw_orbitals(n_orb, L, n, ecut=ecut, seed=seed)
+    phi, _ = loewdin(raw, L ** 3)
+    lat = np.diag([L, L, L])
+    lat_s = np.array([[L, 0.0, 0.0], [L, L, 0.0], [0.0, 0.0, L]])
+    p = np.arange(n)
+    src = (p[:, None] + p[None, :]) % n
+    phi_s = np.ascontiguousarray(phi[:, src, p[None, :], :])
+    return phi, phi_s, lat, lat_s, src
+
+
 def _make_workload_task(w: Workload):
     return make_workload(w)
 

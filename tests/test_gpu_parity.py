@@ -105,6 +105,40 @@ def test_orthorhombic_non_cubic_grid(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_triclinic_cell(prec):
+    """A general (non-orthogonal) cell: the reciprocal vectors and |G| of the Coulomb table come
+    from the full lattice matrix on both sides."""
+    lat = np.array([[9.0, 0.0, 0.0], [2.5, 8.0, 0.0], [1.0, -1.5, 10.0]])
+    grid = (20, 18, 24)
+    rng = np.random.default_rng(11)
+    raw = rng.standard_normal((6,) + grid)
+    phi, _ = I.loewdin(raw, abs(float(np.linalg.det(lat))))
+    pairs = I.all_pairs(6)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    E, V = run_gpu(phi, pairs, lat, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert_v_close(V, V_ref, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_skewed_basis_of_the_same_cell(prec):
+    """The cubic cell written in the skewed basis a1, a1 + a2, a3 with the grid data index-mapped
+    accordingly (band-limited orbitals, so no pair density reaches where the two bases fold
+    frequencies differently): against the oracle in the skewed basis, and against the GPU's own
+    result in the cubic basis mapped to the skewed grid."""
+    phi, phi_s, lat, lat_s, src = I.skewed_basis_case()
+    n = phi.shape[1]
+    pairs = I.all_pairs(phi.shape[0])
+    E_ref, V_ref = O.exchange(phi_s, pairs, lat_s)
+    E_s, V_s = run_gpu(phi_s, pairs, lat_s, prec)
+    assert abs(E_s - E_ref) <= TOL[prec] * abs(E_ref)
+    assert_v_close(V_s, V_ref, TOL[prec])
+    E, V = run_gpu(phi, pairs, lat, prec)
+    assert abs(E_s - E) <= TOL[prec] * abs(E)
+    assert_v_close(V_s, V[:, src, np.arange(n)[None, :], :], TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_pw16_n32_full(prec):
     """The 16-orbital random-PW workload: L = 10 bohr, 32^3, Ecut = 20 Ha, all 136 pairs."""
     w = I.WORKLOADS["pw16_n32"]

@@ -7,7 +7,8 @@
 * invariants: orthogonal rotation of the occupied set, v_ij = v_ji, Parseval (real-space
   energy), Euler homogeneity E = 1/2 sum_i <phi_i, V_x phi_i>, the gradient identity
   dE/dphi = 2 (Omega/N) V_x phi by a 5-point stencil (exact for a quartic), linearity in
-  the pair list, the two-pairs-per-complex-transform packing identity;
+  the pair list, the two-pairs-per-complex-transform packing identity, independence of the basis
+  a cell is written in (a skewed basis of the same cubic cell);
 * an independent pure-Python brute force of Eqs. vx/vij/HFX on a 4^3 grid.
 """
 import math
@@ -82,6 +83,59 @@ def test_coulomb_sphere_cut():
     assert np.all(v[0.5 * g2 >= 4 * ecut] == 0.0)
     inside = (0.5 * g2 < 4 * ecut) & (g2 > 0)
     assert np.allclose(v[inside], 4 * math.pi / g2[inside], rtol=1e-15)
+
+
+def test_skewed_basis_of_the_same_cell():
+    """E_x and V_x phi of a cell do not depend on the basis it is written in (pins the general-
+    lattice reciprocal vectors: a transposed or non-inverted lattice matrix fails)."""
+    phi, phi_s, lat, lat_s, src = I.skewed_basis_case()
+    n = phi.shape[1]
+    pairs = I.all_pairs(phi.shape[0])
+    E, V = O.exchange(phi, pairs, lat)
+    E_s, V_s = O.exchange(phi_s, pairs, lat_s)
+    assert abs(E_s - E) <= 1e-12 * abs(E)
+    assert rel(V_s, V[:, src, np.arange(n)[None, :], :]) <= 1e-12
+    # the skewed cell really is skewed: its reciprocal rows are not orthogonal
+    B = O.reciprocal_vectors(lat_s)
+    assert abs(B[0] @ B[1]) > 1e-3
+
+
+def test_symmetric_part_of_the_kernel_on_a_triclinic_cell(monkeypatch):
+    """On a non-orthogonal cell with even edges the kernel on the grid is not inversion-symmetric
+    (a Nyquist point and its mirror have different |G|), yet for real orbitals E_x = sum v |F|^2 and
+    V_x phi = Re ifft(v F) are the same with v replaced by its symmetric part (v(k) + v(-k))/2:
+    |F(k)| = |F(-k)| for real pair densities, and the real part keeps only the symmetric part."""
+    lat = np.array([[9.0, 0.0, 0.0], [2.5, 8.0, 0.0], [1.0, -1.5, 10.0]])
+    grid = (10, 8, 12)
+    v = O.coulomb_kernel(lat, grid)
+    mirror = tuple((-np.arange(n)) % n for n in grid)
+    v_m = v[mirror[0]][:, mirror[1]][:, :, mirror[2]]
+    assert np.max(np.abs(v - v_m)) > 1e-3 * np.max(v)  # the raw kernel is not symmetric here
+    rng = np.random.default_rng(12)
+    phi, _ = I.loewdin(rng.standard_normal((4,) + grid), abs(float(np.linalg.det(lat))))
+    pairs = I.all_pairs(4)
+    E, V = O.exchange(phi, pairs, lat)
+    kernel = O.coulomb_kernel
+
+    def symmetric(lattice, g, sphere_ecut=None):
+        w = kernel(lattice, g, sphere_ecut)
+        m = tuple((-np.arange(n)) % n for n in g)
+        return 0.5 * (w + w[m[0]][:, m[1]][:, :, m[2]])
+
+    monkeypatch.setattr(O, "coulomb_kernel", symmetric)
+    E_s, V_s = O.exchange(phi, pairs, lat)
+    assert abs(E_s - E) <= 1e-13 * abs(E)
+    assert rel(V_s, V) <= 1e-13
+
+
+def test_skewed_basis_catches_a_transposed_reciprocal_matrix(monkeypatch):
+    phi, phi_s, lat, lat_s, _ = I.skewed_basis_case()
+    pairs = I.all_pairs(phi.shape[0])
+    E, _ = O.exchange(phi, pairs, lat, want_v=False)
+    monkeypatch.setattr(O, "reciprocal_vectors",
+                        lambda A: 2.0 * np.pi * np.linalg.inv(np.asarray(A, dtype=np.float64)))
+    E_bad, _ = O.exchange(phi_s, pairs, lat_s, want_v=False)
+    assert abs(E_bad - E) > 1e-6 * abs(E)
 
 
 # ----------------------------------------------------------------------------- closed forms
