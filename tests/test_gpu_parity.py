@@ -138,6 +138,36 @@ def test_skewed_basis_of_the_same_cell(prec):
     assert_v_close(V_s, V[:, src, np.arange(n)[None, :], :], TOL[prec])
 
 
+@pytest.mark.parametrize("n,n_orb", [(32, 16), (24, 11)])
+def test_fp32_orbitals_flag(n, n_orb):
+    """HFX_ORBITALS_F32: FP32 orbitals taken straight from the caller give bit for bit what the FP64
+    orbitals give after the library's own round-to-nearest FP32 copy (a compile-time grid with the
+    TMA dense pass, and a runtime-geometry grid), in one call and in a batched call."""
+    from paper_2309_00651_gb300 import hfx
+    L = 0.6 * n
+    lat = np.diag([L] * 3)
+    phi = band_limited(n_orb, n, L, seed=21 + n)
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat)
+    ex = hfx.Exchange(lat, (n, n, n), alpha=0.25, precision="fp32")
+    phi64 = torch.from_numpy(phi).cuda()
+    phi32 = phi64.float().contiguous()
+    pairs_d = torch.from_numpy(pairs).cuda()
+    E1, V1 = ex.apply(phi64, pairs_d)
+    E2, V2 = ex.apply(phi32, pairs_d)
+    ex.sync_status()
+    assert E2.item() == E1.item() and torch.equal(V2, V1)
+    assert abs(E2.item() - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert_v_close(V2.cpu().numpy(), V_ref, TOL["fp32"])
+    E3 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    V3 = torch.empty_like(phi64)
+    hfx.hfx_apply_batched([ex.ctx], [(phi32, pairs_d, E3, V3, hfx.HFX_ORBITALS_F32)])
+    ex.sync_status()
+    assert abs(E3.item() - E_ref) <= TOL["fp32"] * abs(E_ref)
+    assert_v_close(V3.cpu().numpy(), V_ref, TOL["fp32"])
+    ex.close()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_pw16_n32_full(prec):
     """The 16-orbital random-PW workload: L = 10 bohr, 32^3, Ecut = 20 Ha, all 136 pairs."""
