@@ -138,6 +138,22 @@ def test_skewed_basis_of_the_same_cell(prec):
     assert_v_close(V_s, V[:, src, np.arange(n)[None, :], :], TOL[prec])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("grid,n_orb", [((4, 4, 4), 3), ((2, 4, 6), 2), ((6, 2, 4), 5), ((8, 8, 8), 1)])
+def test_degenerate_sizes(prec, grid, n_orb):
+    """The smallest grids (one radix per axis, an edge of 2, z rows shorter than a z-chunk) and a
+    single orbital (one diagonal pair), against the oracle's brute-force DFT."""
+    Ls = (5.0, 6.0, 7.0)
+    lat = np.diag(Ls)
+    rng = np.random.default_rng(sum(grid) + n_orb)
+    phi, _ = I.loewdin(rng.standard_normal((n_orb,) + grid), float(np.prod(Ls)))
+    pairs = I.all_pairs(n_orb)
+    E_ref, V_ref = O.exchange(phi, pairs, lat, direct=True)
+    E, V = run_gpu(phi, pairs, lat, prec)
+    assert abs(E - E_ref) <= TOL[prec] * abs(E_ref)
+    assert_v_close(V, V_ref, TOL[prec])
+
+
 @pytest.mark.parametrize("n,n_orb", [(32, 16), (24, 11)])
 def test_fp32_orbitals_flag(n, n_orb):
     """HFX_ORBITALS_F32: FP32 orbitals taken straight from the caller give bit for bit what the FP64
