@@ -8,6 +8,8 @@ HFX_ERR_OOM, hold no device allocation it did not hold before (hfx_test_live_all
 next call without a failure must give the same result as a context that never saw one.  Nothing
 here faults or exhausts the GPU: the failing allocation never reaches cudaMalloc.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -27,6 +29,17 @@ def _lib():
     yield
     from paper_2309_00651_gb300 import hfx
     hfx.hfx_test_fail_allocation(-1)
+
+
+@pytest.fixture(autouse=True)
+def _no_collection_during_counts():
+    """Contexts that earlier tests left in reference cycles are freed now, and the cyclic collector
+    is held off while a test compares allocation counts (a context it freed mid-test would lower
+    the count by its tables)."""
+    gc.collect()
+    gc.disable()
+    yield
+    gc.enable()
 
 
 def _workload(n_orb, seed):
