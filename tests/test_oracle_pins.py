@@ -128,6 +128,24 @@ def test_symmetric_part_of_the_kernel_on_a_triclinic_cell(monkeypatch):
     assert rel(V_s, V) <= 1e-13
 
 
+def test_result_does_not_depend_on_the_nyquist_tie_break(monkeypatch):
+    """Folding the Nyquist index to -n/2 instead of +n/2 swaps v between a Nyquist point and its
+    mirror on a triclinic cell; for real orbitals E_x and V_x phi stay the same."""
+    lat = np.array([[9.0, 0.0, 0.0], [2.5, 8.0, 0.0], [1.0, -1.5, 10.0]])
+    grid = (10, 8, 12)
+    rng = np.random.default_rng(13)
+    phi, _ = I.loewdin(rng.standard_normal((3,) + grid), abs(float(np.linalg.det(lat))))
+    pairs = I.all_pairs(3)
+    E, V = O.exchange(phi, pairs, lat)
+    v_plus = O.coulomb_kernel(lat, grid)
+    monkeypatch.setattr(O, "frequencies", lambda n: np.where(np.arange(n) < n // 2, np.arange(n),
+                                                             np.arange(n) - n))
+    assert not np.allclose(O.coulomb_kernel(lat, grid), v_plus)  # the tie-break matters to v
+    E_m, V_m = O.exchange(phi, pairs, lat)
+    assert abs(E_m - E) <= 1e-13 * abs(E)
+    assert rel(V_m, V) <= 1e-13
+
+
 def test_skewed_basis_catches_a_transposed_reciprocal_matrix(monkeypatch):
     phi, phi_s, lat, lat_s, _ = I.skewed_basis_case()
     pairs = I.all_pairs(phi.shape[0])
