@@ -7,6 +7,7 @@ flags and host machine skips the rebuild when nothing changed.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import hashlib
 import os
 import platform
@@ -78,9 +79,20 @@ def build(verbose: bool = False, force: bool = False, debug: bool = False) -> st
     """Compile (if needed) and return the path of libhfx.so, or of libhfx_debug.so with debug=True
     (HFX_DEBUG: workspace guard bands and the device-side couple-layout check)."""
     build_dir = BUILD + ("_debug" if debug else "")
+    os.makedirs(build_dir, exist_ok=True)
+    # one build at a time per folder: the ranks of a multi-process launch all call build(), and
+    # only the first compiles; the others wait here and then find the stamp up to date
+    with open(os.path.join(build_dir, "lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build(build_dir, verbose, force, debug)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build(build_dir: str, verbose: bool, force: bool, debug: bool) -> str:
     lib = LIB_DEBUG if debug else LIB
     flags = NVCC_FLAGS + (["-DHFX_DEBUG"] if debug else [])
-    os.makedirs(build_dir, exist_ok=True)
     stamp_file = os.path.join(build_dir, "stamp")
     stamp = _stamp() + ("-debug" if debug else "")
     if not force and os.path.exists(lib) and os.path.exists(stamp_file):
