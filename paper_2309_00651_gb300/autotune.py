@@ -44,7 +44,7 @@ def _load(path: str) -> Dict[str, dict]:
 def _store(path: str, table: Dict[str, dict]) -> None:
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
-        tmp = path + ".tmp"
+        tmp = f"{path}.{os.getpid()}.tmp"  # per process: concurrent writers never share it
         with open(tmp, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
         os.replace(tmp, path)
