@@ -116,13 +116,15 @@ hfx_status hfx_create(const hfx_box* box, const int32_t grid[3], double ecut, hf
 /* hfx_workspace_bytes -- device scratch that hfx_apply needs for n_orb orbitals and a list
  * of n_pairs pairs (pair staging, the per-batch transforms and the per-couple energy sums;
  * plus, on the FP32 paths, an FP32 copy of the orbitals and the FP32 accumulator of V_x phi that
- * is widened into the caller's FP64 array at the end of the call).  Returns 0 on bad arguments. */
+ * is widened into the caller's FP64 array at the end of the call).  Returns 0 on bad arguments.
+ * (Library plumbing; the paper has no counterpart.) */
 size_t hfx_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs);
 
 /* hfx_set_workspace -- hand the context a caller-owned device buffer (e.g. a torch tensor)
  * of `bytes` bytes, 256-byte aligned.  The context keeps the pointer until it is replaced
  * or the context is destroyed; it never frees it.  Calls that use the same context must
- * not overlap on the GPU. */
+ * not overlap on the GPU.
+ * (Library plumbing; the paper has no counterpart.) */
 hfx_status hfx_set_workspace(hfx_ctx* c, void* dev_ptr, size_t bytes);
 
 /* hfx_apply -- one exact-exchange evaluation (Eqs. vx, vij, HFX).
@@ -192,14 +194,16 @@ hfx_status hfx_apply_batched(hfx_ctx* const* ctxs, const hfx_apply_args* args, i
  * hfx_apply_sequential rejects it. */
 #define HFX_TEST_STALL    0x100u
 
-/* hfx_apply_sequential -- the same problems as separate hfx_apply calls, one after another on
- * the stream, each with the fastest passes its own context has (compile-time geometry where the
- * edge has it).  Same argument rules; HFX_TEST_STALL is rejected. */
+/* hfx_apply_sequential -- (Sec. 2.2, independent work, as for hfx_apply_batched) the same
+ * problems as separate hfx_apply calls, one after another on the stream, each with the fastest
+ * passes its own context has (compile-time geometry where the edge has it).  Same argument
+ * rules; HFX_TEST_STALL is rejected. */
 hfx_status hfx_apply_sequential(hfx_ctx* const* ctxs, const hfx_apply_args* args, int32_t n,
                                 void* cuda_stream);
 
 /* hfx_set_wait_budget -- clock cycles one device-side wait of hfx_apply_batched may last when
- * this context leads the batch (0: the default, 2^34 cycles, about 8 s at 2 GHz). */
+ * this context leads the batch (0: the default, 2^34 cycles, about 8 s at 2 GHz).
+ * (Library plumbing; the paper has no counterpart.) */
 hfx_status hfx_set_wait_budget(hfx_ctx* c, int64_t cycles);
 
 /* hfx_apply_noalloc -- hfx_apply for callers that cannot allocate device memory.
@@ -235,7 +239,8 @@ hfx_status hfx_apply_noalloc(hfx_ctx* c, const void* orbitals, int32_t n_orb, co
 
 /* hfx_sync_status -- wait for `cuda_stream` and return (then clear) the device-side error
  * word of the context: HFX_OK, HFX_ERR_BAD_PAIR_LIST, HFX_ERR_TIMEOUT,
- * HFX_ERR_NOT_POSITIVE_DEFINITE or HFX_ERR_RANK_DEFICIENT. */
+ * HFX_ERR_NOT_POSITIVE_DEFINITE or HFX_ERR_RANK_DEFICIENT.
+ * (Library plumbing; the paper has no counterpart.) */
 hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
 
 /* hfx_set_tuning -- schedule parameters of the context (what an autotuner varies; results do
@@ -246,7 +251,8 @@ hfx_status hfx_sync_status(hfx_ctx* c, void* cuda_stream);
  *   pipeline    : nonzero = the forward/x passes of the next batch run on a second stream beside
  *                 the accumulate pass of the current one (two transform buffers), 0 = one stream.
  * Synchronises the device when cached schedules have to be dropped; not during stream capture.
- * The workspace size (hfx_workspace_bytes) changes with these settings. */
+ * The workspace size (hfx_workspace_bytes) changes with these settings.
+ * (Library plumbing; the paper has no counterpart.) */
 hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_bytes, int32_t pipeline);
 
 /* hfx_plan_stats -- what hfx_apply(c, ..., n_orb, ..., n_pairs, flags, ...) will launch, from the
@@ -255,7 +261,8 @@ hfx_status hfx_set_tuning(hfx_ctx* c, int32_t block, size_t batch_bytes, int32_t
  *   out[3] = largest number of packed pair couples (two pairs per complex 3D transform) held
  *   by one batch, out[4] = couples of the whole call when every block pair is full (the
  *   exact count for the complete pair list), out[5] = the part of out[4] in full off-diagonal
- *   block pairs (handled by the register-accumulating inverse-y pass). */
+ *   block pairs (handled by the register-accumulating inverse-y pass).
+ * (Measurement support; the paper has no counterpart.) */
 hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint32_t flags, int64_t out[6]);
 
 /* hfx_profile_enable / hfx_profile_read -- per-pass device time.  While enabled, every
@@ -264,7 +271,8 @@ hfx_status hfx_plan_stats(const hfx_ctx* c, int32_t n_orb, int64_t n_pairs, uint
  * milliseconds and the number of launches since the last read, then resets them; index
  * 0 pair staging (and the FP32 orbital copy), 1 forward yz-plane pass, 2 x/Coulomb pass,
  * 3 inverse-y/accumulate pass for full off-diagonal block pairs, 4 energy sum,
- * 5 inverse-y/accumulate pass for the other block pairs.  Not for use inside stream capture. */
+ * 5 inverse-y/accumulate pass for the other block pairs.  Not for use inside stream capture.
+ * (Measurement support; the paper has no counterpart.) */
 hfx_status hfx_profile_enable(hfx_ctx* c, int on);
 hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]);
 
@@ -274,7 +282,8 @@ hfx_status hfx_profile_read(hfx_ctx* c, double ms[6], int64_t launches[6]);
  * band that lost its pattern sets the corruption bit of the error word (hfx_sync_status:
  * HFX_ERR_CORRUPTION).  Debug builds also check, after the pair placement of every call, that each
  * placed couple sits at its canonical place in its block pair.  Release builds return
- * HFX_ERR_INVALID_ARG. */
+ * HFX_ERR_INVALID_ARG.
+ * (A debugging aid; the paper has no counterpart.) */
 hfx_status hfx_debug_check_guards(hfx_ctx* c, void* cuda_stream);
 
 /* hfx_test_fail_allocation / hfx_test_live_allocations -- failure injection on the host, for
@@ -291,10 +300,12 @@ void hfx_test_fail_allocation(int64_t k);
 int64_t hfx_test_live_allocations(void);
 
 /* hfx_last_error -- the calling thread's last error message ("" if none); valid until the
- * thread's next libhfx call. */
+ * thread's next libhfx call.
+ * (Library plumbing; the paper has no counterpart.) */
 const char* hfx_last_error(void);
 
-/* hfx_destroy -- free the context and its tables (not the workspace).  NULL is a no-op. */
+/* hfx_destroy -- free the context and its tables (not the workspace).  NULL is a no-op.
+ * (Library plumbing; the paper has no counterpart.) */
 void hfx_destroy(hfx_ctx* c);
 
 #ifdef __cplusplus

@@ -37,10 +37,12 @@ extern "C" {
 
 /* hfx_ace_workspace_bytes -- device workspace that hfx_ace_build (n_psi = 0), hfx_ace_apply
  * and hfx_screen_pairs need for n_orb orbitals and n_psi functions: the split-contraction
- * partial sums plus the small matrices.  0 when the sizes are invalid. */
+ * partial sums plus the small matrices.  0 when the sizes are invalid.  (Library plumbing: the
+ * paper has no counterpart.) */
 size_t hfx_ace_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int32_t n_psi);
 
-/* hfx_ace_build -- ACE construction from the occupied orbitals and their exchange action.
+/* hfx_ace_build -- ACE construction from the occupied orbitals and their exchange action
+ * (Sec. 2.1, Eq. vx_ace and the definitions of M, L and P after it).
  *   orbitals : [n_orb][N] FP64, read only (psi).
  *   w        : [n_orb][N] FP64, read only (W = V_x psi, e.g. the output of hfx_apply).
  *   m        : [n_orb][n_orb] FP64 out, M_kl = <psi_k|W_l> as defined (not symmetrised); may be
@@ -53,7 +55,8 @@ size_t hfx_ace_workspace_bytes(const hfx_ctx* c, int32_t n_orb, int32_t n_psi);
 hfx_status hfx_ace_build(hfx_ctx* c, const double* orbitals, const double* w, int32_t n_orb, double* m,
                          double* l, double* p, void* workspace, size_t workspace_bytes, void* cuda_stream);
 
-/* hfx_ace_apply -- out_i = V_x^ACE psi_i = - sum_k P_k <P_k|psi_i> for i < n_psi.
+/* hfx_ace_apply -- out_i = V_x^ACE psi_i = - sum_k P_k <P_k|psi_i> for i < n_psi (Sec. 2.1,
+ * Eq. vx_ace: the compressed operator applied on the inner steps).
  *   p   : [n_orb][N] FP64 (from hfx_ace_build), read only.
  *   psi : [n_psi][N] FP64, read only.
  *   out : [n_psi][N] FP64; overwritten, or added to with HFX_ACCUMULATE in `flags`; must not
@@ -62,7 +65,8 @@ hfx_status hfx_ace_apply(hfx_ctx* c, const double* p, int32_t n_orb, const doubl
                          uint32_t flags, double* out, void* workspace, size_t workspace_bytes,
                          void* cuda_stream);
 
-/* hfx_screen_pairs -- the overlap screen of the pair list.
+/* hfx_screen_pairs -- the overlap screen of the pair list (Sec. 2.1, the overlap cut of the
+ * localised-orbital variant, s-MTACE).
  *   orbitals : [n_orb][N] FP64, read only.
  *   cut      : keep i < j when s_ij > cut (finite, >= 0).
  *   s        : [n_orb][n_orb] FP64 out (symmetric), or NULL.
@@ -75,7 +79,8 @@ hfx_status hfx_screen_pairs(hfx_ctx* c, const double* orbitals, int32_t n_orb, d
 
 /* hfx_scdm_workspace_bytes -- device workspace of hfx_scdm_localise for n_orb orbitals
  * (residual norms, per-block maxima, Q in the compute type; FP32 contexts also an FP32 copy of
- * the orbitals).  0 when the sizes are invalid. */
+ * the orbitals).  0 when the sizes are invalid.  (Library plumbing: the paper has no
+ * counterpart.) */
 size_t hfx_scdm_workspace_bytes(const hfx_ctx* c, int32_t n_orb);
 
 /* hfx_scdm_localise -- SCDM localisation (the selected-columns-of-the-density-matrix method the
@@ -95,7 +100,8 @@ size_t hfx_scdm_workspace_bytes(const hfx_ctx* c, int32_t n_orb);
 hfx_status hfx_scdm_localise(hfx_ctx* c, const double* orbitals, int32_t n_orb, int64_t* pivots, double* q,
                              double* phi_loc, void* workspace, size_t workspace_bytes, void* cuda_stream);
 
-/* hfx_ace_profile_read -- per-kernel device time of the calls above while hfx_profile_enable
+/* hfx_ace_profile_read -- (measurement; the paper has no counterpart) per-kernel device time of
+ * the calls above while hfx_profile_enable
  * is on (CUDA events around each launch on the call's stream): summed milliseconds and launch
  * counts since the last read, then reset; index 0 the split grid contractions (M, <psi|P>, s),
  * 1 the left multiplies (P, V_x^ACE psi, Phi = Psi Q), 2 the other steps (partial-sum

@@ -22,7 +22,7 @@ extern "C" {
  * is nonzero, else FP32), timed with CUDA events on cuda_stream; *tflops receives the rate.
  * Synchronises the stream.  Allocates a small device buffer for the chains' results (so the
  * compiler keeps them) and frees it.  Returns HFX_ERR_INVALID_ARG (iters < 1, NULL tflops) or
- * HFX_ERR_CUDA. */
+ * HFX_ERR_CUDA.  (Measurement support; the paper has no counterpart.) */
 hfx_status hfx_fma_peak(int32_t fp64, int32_t iters, double* tflops, void* cuda_stream);
 
 #ifdef __cplusplus

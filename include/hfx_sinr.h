@@ -30,21 +30,24 @@ typedef struct {
   int32_t L;     /* thermostat chain length, 1..16                   */
 } hfx_sinr_params;
 
-/* Update A: exp(iL_N dt/2) as n_res x n_sy factors (Suzuki-Yoshida order n_sy = 1, 3 or 5, the
- * standard weights w_k), each with Delta = w_k dt / n_res:
+/* Update A (the paper's appendix, update A; eq. eom): exp(iL_N dt/2) as n_res x n_sy factors
+ * (Suzuki-Yoshida order n_sy = 1, 3 or 5, the standard weights w_k), each with
+ * Delta = w_k dt / n_res:
  *   v2 += (Delta/4) G(v1)/Q2, G(v1) = Q1 v1^2 - kT;  V *= H;  v1 *= H exp(-v2 Delta/2);
  *   v2 += (Delta/4) G(v1)/Q2;  H = sqrt(Lambda/(M V^2 + L/(L+1) sum_j Q1 v1_j^2 exp(-v2_j Delta))). */
 hfx_status hfx_sinr_update_n(const hfx_sinr_params* p, int64_t n_dof, double dt, int32_t n_res, int32_t n_sy,
                              const double* mass, double* V, double* v1, double* v2, void* cuda_stream);
 
-/* Update B: exp(iL_V dt/2) with the force F = force + force_extra held constant (force_extra may
- * be NULL; the XI-RESPA steps pass n_MTS F_slow there at the ends of an outer step):
+/* Update B (the paper's appendix, update B): exp(iL_V dt/2) with the force F = force +
+ * force_extra held constant (force_extra may be NULL; the XI-RESPA steps pass n_MTS F_slow there
+ * at the ends of an outer step):
  *   V = (V + s F/M)/sdot, v1 /= sdot, with s, sdot of a = F V/Lambda, b = F^2/(M Lambda). */
 hfx_status hfx_sinr_update_v(const hfx_sinr_params* p, int64_t n_dof, double dt, const double* mass,
                              const double* force, const double* force_extra, double* V, double* v1,
                              void* cuda_stream);
 
-/* Update C: X += V dt and the exact Ornstein-Uhlenbeck step of v2 over dt,
+/* Update C (the paper's appendix, update C): X += V dt and the exact Ornstein-Uhlenbeck step of
+ * v2 over dt,
  *   v2 = v2 e^{-gamma dt} + sigma R sqrt((1 - e^{-2 gamma dt})/(2 gamma)), sigma = sqrt(2 kT gamma/Q2),
  * with R[I][j] standard normal draws supplied by the caller (read only). */
 hfx_status hfx_sinr_update_x(const hfx_sinr_params* p, int64_t n_dof, double dt, const double* V, double* X,

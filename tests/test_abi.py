@@ -35,6 +35,24 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """The comment in front of every entry point names the passage of the paper it computes
+    (Sec., Eq., the appendix) or states that the paper has no counterpart (plumbing, measurement,
+    testing hooks)."""
+    inc = os.path.join(ROOT, "include")
+    found = 0
+    for name in sorted(os.listdir(inc)):
+        if not name.endswith(".h"):
+            continue
+        with open(os.path.join(inc, name)) as f:
+            text = f.read()
+        for m in re.finditer(r"(/\*(?:(?!\*/).)*\*/)\s*((?:[a-z_0-9]+\s+\**)+?(hfx_[a-z_0-9]+)\s*\()", text, flags=re.S):
+            found += 1
+            comment = re.sub(r"\s*\n\s*\*\s*", " ", m.group(1))  # one line, without the leading stars
+            assert re.search(r"Sec\.|Eq\.|appendix|no counterpart", comment), f"{name}: {m.group(3)}"
+    assert found >= len(declared_symbols()) - 4  # (a few share one comment: profile_enable/read, ...)
+
+
 def test_library_exports_every_declared_symbol(lib):
     from paper_2309_00651_gb300 import hfx
     for name in declared_symbols():
